@@ -1,0 +1,253 @@
+"""FP64 CPU oracle of the SGML method (arXiv 1703.07206), Python side.
+
+TEST INFRASTRUCTURE ONLY: the test suite, the smoke check and the CPU-baseline leg of the benchmark
+load this module.  The CUDA library never calls it and shares no code with it.
+
+The arithmetic is in ``sgml_oracle.c`` (plain C, FP64, no fast-math).  This module compiles it with
+gcc on first use (or via :func:`build`), declares the ctypes signatures and converts NumPy arrays.
+Every field is a full single-grid array of shape ``(N, N)`` (2-D, indexed ``[y, x]``) or
+``(N, N, N)`` (3-D, ``[z, y, x]``) with ``N = 2**n + 1``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "sgml_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_BUILD, "liboracle.so")
+
+DIRICHLET = 0
+NEUMANN = 1
+
+
+class _Problem(ctypes.Structure):
+    _fields_ = [
+        ("dim", ctypes.c_int),
+        ("n", ctypes.c_int),
+        ("face_type", ctypes.c_int * 6),
+        ("face_value", ctypes.c_double * 6),
+        ("sigma", ctypes.POINTER(ctypes.c_double)),
+        ("a", ctypes.POINTER(ctypes.c_double)),
+        ("a_scalar", ctypes.c_double),
+        ("n_r", ctypes.c_int),
+        ("theta", ctypes.c_double),
+        ("stencil", ctypes.c_int),
+        ("dt_mode", ctypes.c_int),
+    ]
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle into ``oracle/_build/liboracle.so`` (plain -O2, no fast-math)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-fno-fast-math",
+                               "-ffp-contract=off", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+_lib = None
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        lib = ctypes.CDLL(build())
+        P = ctypes.POINTER(_Problem)
+        D = ctypes.POINTER(ctypes.c_double)
+        I = ctypes.c_int
+        lib.orc_apply_op.argtypes = [P, I, D, D, D, I, D]
+        lib.orc_restriction.argtypes = [P, I, D, D]
+        lib.orc_local_step.argtypes = [P, I, D, D, D]
+        lib.orc_interpolate_add.argtypes = [P, I, D, D]
+        lib.orc_visit.argtypes = [P, I, I, D, D, D, D]
+        lib.orc_cycle.argtypes = [P, D, D]
+        lib.orc_schedule.argtypes = [P, ctypes.POINTER(I), ctypes.POINTER(I), I]
+        lib.orc_schedule.restype = I
+        lib.orc_lift.argtypes = [P, D]
+        lib.orc_residual.argtypes = [P, D, D, D]
+        lib.orc_max_norm.argtypes = [P, D]
+        lib.orc_max_norm.restype = ctypes.c_double
+        lib.orc_solve.argtypes = [P, D, ctypes.c_double, I, D, D]
+        lib.orc_solve.restype = I
+        lib.orc_sigma_gradient.argtypes = [P, D, D, D]
+        _lib = lib
+    return _lib
+
+
+def _ptr(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if a is not None else None
+
+
+def _f64(a, shape):
+    if a is None:
+        return None
+    out = np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+    if out.shape != shape:
+        raise ValueError(f"expected shape {shape}, got {out.shape}")
+    return out
+
+
+class Problem:
+    """One boundary value problem L u = f with L = div(sigma grad) + a on the unit square/cube.
+
+    ``faces``: 2*dim face types in the order -x,+x,-y,+y(,-z,+z) (DIRICHLET or NEUMANN);
+    ``values``: per face Dirichlet value or outward normal derivative.
+    """
+
+    def __init__(self, dim, n, faces=None, values=None, sigma=None, a=None, a_scalar=0.0,
+                 n_r=2, theta=0.7, stencil=0, dt_mode=0):
+        if dim not in (2, 3):
+            raise ValueError("dim must be 2 or 3")
+        self.dim, self.n = dim, n
+        self.N = 2 ** n + 1
+        self.shape = (self.N,) * dim
+        faces = list(faces) if faces is not None else [DIRICHLET] * (2 * dim)
+        values = list(values) if values is not None else [0.0] * (2 * dim)
+        self.faces = faces + [DIRICHLET] * (6 - len(faces))
+        self.values = [float(v) for v in values] + [0.0] * (6 - len(values))
+        self.sigma = _f64(sigma, self.shape)
+        self.a = _f64(a, self.shape)
+        self.a_scalar = float(a_scalar)
+        self.n_r, self.theta, self.stencil, self.dt_mode = n_r, float(theta), stencil, dt_mode
+        self._c = _Problem()
+        self._c.dim, self._c.n = dim, n
+        for k in range(6):
+            self._c.face_type[k] = self.faces[k]
+            self._c.face_value[k] = self.values[k]
+        self._c.sigma = _ptr(self.sigma)
+        self._c.a = _ptr(self.a)
+        self._c.a_scalar = self.a_scalar
+        self._c.n_r, self._c.theta = n_r, self.theta
+        self._c.stencil, self._c.dt_mode = stencil, dt_mode
+
+    @property
+    def h(self):
+        return 1.0 / (self.N - 1)
+
+    def _arr(self, a):
+        return _f64(a, self.shape)
+
+    def _new(self):
+        return np.zeros(self.shape)
+
+    # --- operators ------------------------------------------------------------------------
+    def apply_op(self, u, nu=0, sig=None, a=None, with_flux=False):
+        """delta L_nu u at level-nu unknowns (Eq. 5 + a u), zero elsewhere."""
+        lib = _load()
+        u = self._arr(u)
+        sig = self._arr(sig) if sig is not None else self.sigma if nu == 0 else None
+        a = self._arr(a) if a is not None else self.a if nu == 0 else None
+        out = self._new()
+        lib.orc_apply_op(ctypes.byref(self._c), nu, _ptr(sig), _ptr(a), _ptr(u), int(with_flux), _ptr(out))
+        return out
+
+    def restriction(self, f, nu):
+        """restriction(nu) of Algorithm 1; valid at level-nu nodes."""
+        lib = _load()
+        f = self._arr(f)
+        g = self._new()
+        lib.orc_restriction(ctypes.byref(self._c), nu, _ptr(f), _ptr(g))
+        return g
+
+    def restricted_coeffs(self, nu):
+        sig = self.restriction(self.sigma, nu) if self.sigma is not None else None
+        a = self.restriction(self.a, nu) if self.a is not None else None
+        return sig, a
+
+    def local_step(self, nu):
+        lib = _load()
+        sig, a = self.restricted_coeffs(nu)
+        out = self._new()
+        lib.orc_local_step(ctypes.byref(self._c), nu, _ptr(sig), _ptr(a), _ptr(out))
+        return out
+
+    def interpolate_add(self, delta, e, nu):
+        """e + I_nu(delta) on the nodes outside the level-nu subset."""
+        lib = _load()
+        delta = self._arr(delta)
+        e = self._arr(e).copy()
+        lib.orc_interpolate_add(ctypes.byref(self._c), nu, _ptr(delta), _ptr(e))
+        return e
+
+    def visit(self, e, r, nu, k):
+        lib = _load()
+        e = self._arr(e).copy()
+        r_nu = self.restriction(r, nu)
+        sig, a = self.restricted_coeffs(nu)
+        lib.orc_visit(ctypes.byref(self._c), nu, k, _ptr(r_nu), _ptr(sig), _ptr(a), _ptr(e))
+        return e
+
+    def cycle(self, r):
+        lib = _load()
+        r = self._arr(r)
+        e = self._new()
+        lib.orc_cycle(ctypes.byref(self._c), _ptr(r), _ptr(e))
+        return e
+
+    def schedule(self):
+        lib = _load()
+        cap = 4 * self.n + 8
+        lv = (ctypes.c_int * cap)()
+        sw = (ctypes.c_int * cap)()
+        m = lib.orc_schedule(ctypes.byref(self._c), lv, sw, cap)
+        return [(lv[i], sw[i]) for i in range(m)]
+
+    def lift(self):
+        lib = _load()
+        u = self._new()
+        lib.orc_lift(ctypes.byref(self._c), _ptr(u))
+        return u
+
+    def residual(self, u, f):
+        lib = _load()
+        u, f = self._arr(u), self._arr(f)
+        r = self._new()
+        lib.orc_residual(ctypes.byref(self._c), _ptr(u), _ptr(f), _ptr(r))
+        return r
+
+    def max_norm(self, v):
+        return _load().orc_max_norm(ctypes.byref(self._c), _ptr(self._arr(v)))
+
+    def rel_residual(self, u, f):
+        """||f - delta L u||_inf / ||f||_inf over unknowns (Sec. 3.1)."""
+        fn = self.max_norm(f)
+        rn = self.max_norm(self.residual(u, f))
+        if fn == 0.0:
+            fn = self.max_norm(self.residual(self.lift(), f))
+        return rn / fn if fn > 0 else 0.0
+
+    def solve(self, f, tol=1e-12, max_cycles=200):
+        """Outer recurrence; returns (u, cycles or -1, history of relative residuals)."""
+        lib = _load()
+        f = self._arr(f)
+        u = self._new()
+        hist = np.zeros(max_cycles + 1)
+        c = lib.orc_solve(ctypes.byref(self._c), _ptr(f), float(tol), int(max_cycles), _ptr(u), _ptr(hist))
+        nh = (c if c >= 0 else max_cycles) + 1
+        return u, c, hist[:nh]
+
+    def sigma_gradient(self, lam, u):
+        lib = _load()
+        g = self._new()
+        lib.orc_sigma_gradient(ctypes.byref(self._c), _ptr(self._arr(lam)), _ptr(self._arr(u)), _ptr(g))
+        return g
+
+    def unknown_mask(self):
+        """Boolean mask of unknowns (nodes not on a Dirichlet face)."""
+        m = np.ones(self.shape, dtype=bool)
+        for k in range(self.dim):
+            ax = self.dim - 1 - k  # x is the last array axis
+            lo = [slice(None)] * self.dim
+            hi = [slice(None)] * self.dim
+            lo[ax], hi[ax] = 0, self.N - 1
+            if self.faces[2 * k] == DIRICHLET:
+                m[tuple(lo)] = False
+            if self.faces[2 * k + 1] == DIRICHLET:
+                m[tuple(hi)] = False
+        return m

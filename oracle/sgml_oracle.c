@@ -1,0 +1,553 @@
+/*
+ * sgml_oracle.c -- plain, slow FP64 CPU oracle of the single-grid multi-level (SGML) method of
+ * Becerra-Sagredo, Mandujano and Malaga, "A GPU-based Multi-level Algorithm for Boundary Value
+ * Problems" (arXiv 1703.07206).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the reference against which the CUDA library is checked.
+ * Only the test suite, the smoke check and the CPU-baseline leg of the benchmark may load it.  It
+ * shares no code, header, table or constant with the CUDA path, and the CUDA path never calls it.
+ *
+ * Everything lives on ONE grid, exactly as the paper describes (Sec. 2): every field is a full
+ * array of N^d doubles (N = 2^n + 1 per dimension, row-major [z][y][x], x fastest), and the level-nu
+ * subset is the set of nodes whose indices are all multiples of 2^nu.  Level-nu work reads and writes
+ * that subset in place.  No blocking, fusion or compact per-level storage is used: the loops follow
+ * the paper's routines in the paper's order so that they can be checked against it by eye.
+ *
+ * Readings of the paper where it is silent or garbled (each also listed in the design notes):
+ *   - Algorithm 1 runs its passes m = 0 .. nu-1 (restriction(0) is the identity), evaluated at the
+ *     level-(m+1) nodes only; values there are those of the every-node evaluation.
+ *   - Algorithm 3 line 3 is read as the zig-zag "visit nu1, then nu1-1", followed by lines 6-8's
+ *     second visit to nu1; a level below 0 is skipped.
+ *   - The stencil of Eq. 5 is normalised with kappa_d = 2 / sum_o w_o o_1^2 so that it is exact on
+ *     quadratics ("consistent"); the printed 3/(13h) (and the 2-D analogue 1/(2h)) is kept as the
+ *     "literal" option.
+ *   - The pseudo-time step is theta * (kappa_d S_d / 2) / D_i, D_i the diagonal of delta L at the
+ *     node (Jacobi-scaled); for constant sigma and a = 0 this is theta * H^2 / (2 sigma), the bound
+ *     of Sec. 2 and Sec. 3.4 times theta.  The node-local form theta * H^2 / (2 sigma_i) of Sec. 3.4
+ *     is kept as an option.
+ *   - The interpolation of Algorithm 2 is applied to the whole change of a visit once its sweeps
+ *     end (the variation of the last sweep is not dropped).
+ *   - Dirichlet values are lifted into u before the first cycle; every cycle is homogeneous.
+ *   - Images: indices that leave [0, N-1] are reflected (-k -> k, N-1+k -> N-1-k).  On a Neumann
+ *     face the image of u carries the prescribed outward derivative g: u_ghost = u_mirror + 2 k h g.
+ *     Coefficients (sigma, a) are reflected on every face.
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_DIRICHLET 0
+#define ORC_NEUMANN 1
+
+/* Problem description.  The Python wrapper mirrors this layout with ctypes. */
+typedef struct {
+  int dim;               /* 2 or 3 */
+  int n;                 /* N = 2^n + 1 nodes per dimension */
+  int face_type[6];      /* -x,+x,-y,+y,-z,+z : ORC_DIRICHLET or ORC_NEUMANN */
+  double face_value[6];  /* Dirichlet value, or outward normal derivative g on a Neumann face */
+  const double* sigma;   /* N^d node values of sigma, or NULL for sigma = 1 */
+  const double* a;       /* N^d node values of a, or NULL for a = a_scalar everywhere */
+  double a_scalar;
+  int n_r;               /* maximum relaxation-interpolations per visit (Algorithm 3) */
+  double theta;          /* fraction of the maximum stable pseudo-time step */
+  int stencil;           /* 0 consistent kappa_d, 1 literal Eq. 5 constant */
+  int dt_mode;           /* 0 Jacobi-scaled step, 1 node-local sigma step (Sec. 3.4) */
+} orc_problem;
+
+/* ------------------------------------------------------------------------------------------ */
+/* Grid helpers                                                                                 */
+/* ------------------------------------------------------------------------------------------ */
+
+static int npts(const orc_problem* p) { return (1 << p->n) + 1; }
+
+static long nnodes(const orc_problem* p) {
+  long N = npts(p);
+  return p->dim == 3 ? N * N * N : N * N;
+}
+
+static long at(const orc_problem* p, const int c[3]) {
+  long N = npts(p);
+  return ((long)c[2] * N + c[1]) * N + c[0];
+}
+
+static double grid_h(const orc_problem* p) { return 1.0 / (double)(npts(p) - 1); }
+
+static void coords(const orc_problem* p, long idx, int c[3]) {
+  long N = npts(p);
+  c[0] = (int)(idx % N);
+  c[1] = (int)((idx / N) % N);
+  c[2] = p->dim == 3 ? (int)(idx / (N * N)) : 0;
+}
+
+/* A node on a Dirichlet face is fixed; every other node is an unknown (Dirichlet wins at a corner
+ * shared with a Neumann face). */
+static int is_dirichlet(const orc_problem* p, const int c[3]) {
+  int N = npts(p);
+  for (int k = 0; k < p->dim; ++k) {
+    if (c[k] == 0 && p->face_type[2 * k] == ORC_DIRICHLET) return 1;
+    if (c[k] == N - 1 && p->face_type[2 * k + 1] == ORC_DIRICHLET) return 1;
+  }
+  return 0;
+}
+
+static int on_level(const int c[3], int dim, int nu) {
+  int s = 1 << nu;
+  for (int k = 0; k < dim; ++k)
+    if (c[k] % s != 0) return 0;
+  return 1;
+}
+
+/* Even image of an index outside [0, N-1]; *out_by gets how many fine nodes it lay outside and
+ * *face the face it crossed (-1 if inside). */
+static int reflect(int i, int N, int k, int* out_by, int* face) {
+  *out_by = 0;
+  *face = -1;
+  if (i < 0) {
+    *out_by = -i;
+    *face = 2 * k;
+    return -i;
+  }
+  if (i > N - 1) {
+    *out_by = i - (N - 1);
+    *face = 2 * k + 1;
+    return 2 * (N - 1) - i;
+  }
+  return i;
+}
+
+/* Offsets o in {-1,0,1}^d \ {0}: the 8 (2-D) or 26 (3-D) neighbours of the radial stencil. */
+static int offsets(int dim, int o[26][3]) {
+  int m = 0;
+  for (int z = (dim == 3 ? -1 : 0); z <= (dim == 3 ? 1 : 0); ++z)
+    for (int y = -1; y <= 1; ++y)
+      for (int x = -1; x <= 1; ++x) {
+        if (x == 0 && y == 0 && z == 0) continue;
+        o[m][0] = x;
+        o[m][1] = y;
+        o[m][2] = z;
+        ++m;
+      }
+  return m;
+}
+
+/* Eq. 5: the radial difference to a neighbour at distance h*l is divided by l, with l = 1, sqrt(2),
+ * sqrt(3) for face, edge and corner neighbours: w_o = 1 / l_o = 1 / sqrt(#non-zero components). */
+static double weight(const int o[3]) {
+  int nz = (o[0] != 0) + (o[1] != 0) + (o[2] != 0);
+  return 1.0 / sqrt((double)nz);
+}
+
+/* Constant in front of Eq. 5.  Consistent: kappa_d = 2 / sum_o w_o o_1^2, which makes the stencil
+ * exact on quadratics.  Literal: 3/13 in 3-D as printed, and the same construction in 2-D (the
+ * perimeter/area ratio 4/h of the disc of radius h/2 spread over 8 directions) gives 1/2. */
+static double kappa(const orc_problem* p) {
+  if (p->stencil == 1) return p->dim == 3 ? 3.0 / 13.0 : 0.5;
+  int o[26][3];
+  int m = offsets(p->dim, o);
+  double s = 0.0;
+  for (int q = 0; q < m; ++q) s += weight(o[q]) * (double)(o[q][0] * o[q][0]);
+  return 2.0 / s;
+}
+
+/* kappa_d S_d / 2 with the consistent kappa_d and S_d = sum_o w_o: the product delta_tau * D_i of
+ * the Jacobi-scaled step for theta = 1 (sqrt(2) in 2-D). */
+static double jacobi_gain(const orc_problem* p) {
+  int o[26][3];
+  int m = offsets(p->dim, o);
+  double s = 0.0, s1 = 0.0;
+  for (int q = 0; q < m; ++q) {
+    s += weight(o[q]);
+    s1 += weight(o[q]) * (double)(o[q][0] * o[q][0]);
+  }
+  return (2.0 / s1) * s / 2.0;
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* Radial finite-difference operator delta L at level nu (Eq. 5, Sec. 3 L = div(sigma grad) + a) */
+/* ------------------------------------------------------------------------------------------ */
+
+/* (delta L_nu u) at the level-nu unknown c.  sig and a hold the level-nu (restricted) coefficients
+ * at level-nu nodes (NULL: 1 and a_scalar).  Neighbours are level-nu nodes at distance 2^nu h.
+ * With with_flux set, a Neumann image carries the prescribed outward derivative (used for the
+ * outer residual only; inside a cycle the images are homogeneous). */
+static double op_at(const orc_problem* p, int nu, const double* sig, const double* a, const double* u,
+                    const int c[3], int with_flux) {
+  int N = npts(p);
+  int s = 1 << nu;
+  double H = s * grid_h(p);
+  int o[26][3];
+  int m = offsets(p->dim, o);
+  long ic = at(p, c);
+  double sc = sig ? sig[ic] : 1.0;
+  double uc = u[ic];
+  double sum = 0.0;
+  for (int q = 0; q < m; ++q) {
+    int nb[3] = {0, 0, 0};
+    double ghost = 0.0;
+    for (int k = 0; k < p->dim; ++k) {
+      int by, face;
+      nb[k] = reflect(c[k] + s * o[q][k], N, k, &by, &face);
+      if (face >= 0 && with_flux && p->face_type[face] == ORC_NEUMANN)
+        ghost += 2.0 * (double)by * grid_h(p) * p->face_value[face];
+    }
+    long in = at(p, nb);
+    double sn = sig ? sig[in] : 1.0;
+    double un = u[in] + ghost;
+    sum += weight(o[q]) * 0.5 * (sc + sn) * (un - uc);
+  }
+  double ac = a ? a[ic] : p->a_scalar;
+  return kappa(p) / (H * H) * sum + ac * uc;
+}
+
+/* delta L_nu applied at every level-nu unknown; 0 at every other node. */
+void orc_apply_op(const orc_problem* p, int nu, const double* sig, const double* a, const double* u,
+                  int with_flux, double* out) {
+  long M = nnodes(p);
+  for (long i = 0; i < M; ++i) {
+    int c[3];
+    coords(p, i, c);
+    out[i] = (on_level(c, p->dim, nu) && !is_dirichlet(p, c)) ? op_at(p, nu, sig, a, u, c, with_flux) : 0.0;
+  }
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* Restriction (Algorithm 1, Eqs. 3-4)                                                          */
+/* ------------------------------------------------------------------------------------------ */
+
+/* Hat function of Sec. 2: 1 at 0, 1/2 at +-1/2, support [-1, 1]. */
+static double hat(double x) {
+  double t = 1.0 - fabs(x);
+  return t > 0.0 ? t : 0.0;
+}
+
+/* One pass of Algorithm 1 with lambda = 2^m: at every level-(m+1) node,
+ * out = 2^-d sum_{p in {-1,0,1}^d} prod_k hat(-p_k/2) in(i + lambda p)   (Eq. 3 in 2-D, Eq. 4 in 3-D).
+ * Indices leaving the domain take the even image. */
+static void restrict_pass(const orc_problem* p, int m, const double* in, double* out) {
+  int N = npts(p);
+  int lam = 1 << m;
+  long M = nnodes(p);
+  double norm = p->dim == 3 ? 1.0 / 8.0 : 1.0 / 4.0;
+  for (long i = 0; i < M; ++i) {
+    int c[3];
+    coords(p, i, c);
+    if (!on_level(c, p->dim, m + 1)) continue;
+    double acc = 0.0;
+    for (int pz = (p->dim == 3 ? -1 : 0); pz <= (p->dim == 3 ? 1 : 0); ++pz)
+      for (int py = -1; py <= 1; ++py)
+        for (int px = -1; px <= 1; ++px) {
+          int pp[3] = {px, py, pz};
+          int nb[3] = {0, 0, 0};
+          double w = 1.0;
+          for (int k = 0; k < p->dim; ++k) {
+            int by, face;
+            nb[k] = reflect(c[k] + lam * pp[k], N, k, &by, &face);
+            w *= hat(-0.5 * pp[k]);
+          }
+          acc += w * in[at(p, nb)];
+        }
+    out[i] = norm * acc;
+  }
+}
+
+/* restriction(nu) of Algorithm 1: g = f, then passes m = 0 .. nu-1.  The result is valid at the
+ * level-nu nodes of g (other entries are left as scratch). */
+void orc_restriction(const orc_problem* p, int nu, const double* f, double* g) {
+  long M = nnodes(p);
+  memcpy(g, f, sizeof(double) * M);
+  if (nu == 0) return;
+  double* t = (double*)malloc(sizeof(double) * M);
+  for (int m = 0; m < nu; ++m) {
+    memcpy(t, g, sizeof(double) * M);
+    restrict_pass(p, m, t, g);
+  }
+  free(t);
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* Pseudo-time step (Sec. 2 stability bound, Sec. 3.4 local step)                              */
+/* ------------------------------------------------------------------------------------------ */
+
+/* D_i = kappa/H^2 sum_o w_o (sigma_i + sigma_o)/2 - a_i: minus the diagonal of delta L_nu. */
+static double diag_at(const orc_problem* p, int nu, const double* sig, const double* a, const int c[3]) {
+  int N = npts(p);
+  int s = 1 << nu;
+  double H = s * grid_h(p);
+  int o[26][3];
+  int m = offsets(p->dim, o);
+  long ic = at(p, c);
+  double sc = sig ? sig[ic] : 1.0;
+  double sum = 0.0;
+  for (int q = 0; q < m; ++q) {
+    int nb[3] = {0, 0, 0};
+    for (int k = 0; k < p->dim; ++k) {
+      int by, face;
+      nb[k] = reflect(c[k] + s * o[q][k], N, k, &by, &face);
+    }
+    double sn = sig ? sig[at(p, nb)] : 1.0;
+    sum += weight(o[q]) * 0.5 * (sc + sn);
+  }
+  double ac = a ? a[ic] : p->a_scalar;
+  return kappa(p) / (H * H) * sum - ac;
+}
+
+static double step_at(const orc_problem* p, int nu, const double* sig, const double* a, const int c[3]) {
+  if (p->dt_mode == 1) {
+    double H = (1 << nu) * grid_h(p);
+    double sc = sig ? sig[at(p, c)] : 1.0;
+    return p->theta * H * H / (2.0 * sc);
+  }
+  return p->theta * jacobi_gain(p) / diag_at(p, nu, sig, a, c);
+}
+
+/* Local pseudo-time step at every level-nu unknown (0 elsewhere). */
+void orc_local_step(const orc_problem* p, int nu, const double* sig, const double* a, double* out) {
+  long M = nnodes(p);
+  for (long i = 0; i < M; ++i) {
+    int c[3];
+    coords(p, i, c);
+    out[i] = (on_level(c, p->dim, nu) && !is_dirichlet(p, c)) ? step_at(p, nu, sig, a, c) : 0.0;
+  }
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* Interpolation I_lambda (Sec. 2, Algorithm 2 line 6)                                          */
+/* ------------------------------------------------------------------------------------------ */
+
+/* For every node x NOT in the level-nu subset: e_x += sum over the corners c of x's level-nu cell of
+ * prod_k hat((x_k - c_k) / 2^nu) * delta_c, with delta given at level-nu nodes. */
+void orc_interpolate_add(const orc_problem* p, int nu, const double* delta, double* e) {
+  int N = npts(p);
+  int s = 1 << nu;
+  long M = nnodes(p);
+  for (long i = 0; i < M; ++i) {
+    int x[3];
+    coords(p, i, x);
+    if (on_level(x, p->dim, nu)) continue;
+    int lo[3] = {0, 0, 0};
+    for (int k = 0; k < p->dim; ++k) lo[k] = (x[k] / s) * s;
+    double acc = 0.0;
+    for (int cz = 0; cz <= (p->dim == 3 ? 1 : 0); ++cz)
+      for (int cy = 0; cy <= 1; ++cy)
+        for (int cx = 0; cx <= 1; ++cx) {
+          int cc[3] = {lo[0] + cx * s, lo[1] + cy * s, lo[2] + cz * s};
+          double w = 1.0;
+          int inside = 1;
+          for (int k = 0; k < p->dim; ++k) {
+            if (cc[k] > N - 1) inside = 0;
+            w *= hat((double)(x[k] - cc[k]) / (double)s);
+          }
+          if (inside && w != 0.0) acc += w * delta[at(p, cc)];
+        }
+    e[i] += acc;
+  }
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* Relaxation-interpolation visit (Algorithm 2) and the single cycle (Algorithm 3)               */
+/* ------------------------------------------------------------------------------------------ */
+
+/* One visit of level nu: k forward-Euler (Jacobi) steps of Eq. 2 on the level-nu unknowns with the
+ * restricted source r_nu and coefficients, then the change of the visit is interpolated to every
+ * node outside the level-nu subset.  e holds the level-nu values in place on the single grid. */
+void orc_visit(const orc_problem* p, int nu, int k, const double* r_nu, const double* sig_nu,
+               const double* a_nu, double* e) {
+  long M = nnodes(p);
+  double* saved = (double*)malloc(sizeof(double) * M);
+  double* next = (double*)malloc(sizeof(double) * M);
+  memcpy(saved, e, sizeof(double) * M);
+  for (int sweep = 0; sweep < k; ++sweep) {
+    memcpy(next, e, sizeof(double) * M);
+    for (long i = 0; i < M; ++i) {
+      int c[3];
+      coords(p, i, c);
+      if (!on_level(c, p->dim, nu) || is_dirichlet(p, c)) continue;
+      double dtau = step_at(p, nu, sig_nu, a_nu, c);
+      next[i] = e[i] + dtau * (op_at(p, nu, sig_nu, a_nu, e, c, 0) - r_nu[i]);
+    }
+    memcpy(e, next, sizeof(double) * M);
+  }
+  if (nu > 0) {
+    for (long i = 0; i < M; ++i) {
+      int c[3];
+      coords(p, i, c);
+      next[i] = on_level(c, p->dim, nu) ? e[i] - saved[i] : 0.0;
+    }
+    orc_interpolate_add(p, nu, next, e);
+  }
+  free(saved);
+  free(next);
+}
+
+static int min_int(int a, int b) { return a < b ? a : b; }
+
+/* Number of relaxation-interpolations of a visit in tooth nu1 (Algorithm 3 lines 5, 8, 10). */
+static int sweeps_for(const orc_problem* p, int nu1_exp) {
+  long full = 1L << (nu1_exp > 30 ? 30 : nu1_exp);
+  return (long)p->n_r < full ? p->n_r : (int)full;
+}
+
+/* One visit of Algorithm 3: restriction(nu) of the cycle's source and of the coefficients
+ * (lines 4, 7), then k relaxation-interpolations (lines 5, 8, 10). */
+static void restrict_and_visit(const orc_problem* p, int nu, int k, const double* r, double* e,
+                               double* r_nu, double* sig_nu, double* a_nu) {
+  orc_restriction(p, nu, r, r_nu);
+  if (p->sigma) orc_restriction(p, nu, p->sigma, sig_nu);
+  if (p->a) orc_restriction(p, nu, p->a, a_nu);
+  orc_visit(p, nu, k, r_nu, p->sigma ? sig_nu : NULL, p->a ? a_nu : NULL, e);
+}
+
+/* The single cycle (Algorithm 3) solving delta L e = r from e = 0.  Teeth nu1 = n-1 .. 0 each visit
+ * nu1, nu1-1 (skipped when negative) and nu1 again with min(n_r, 2^(n-nu1)) sweeps per visit; the
+ * cycle ends with min(n_r, 2^n) sweeps on level 0. */
+void orc_cycle(const orc_problem* p, const double* r, double* e) {
+  long M = nnodes(p);
+  double* r_nu = (double*)malloc(sizeof(double) * M);
+  double* sig_nu = (double*)malloc(sizeof(double) * M);
+  double* a_nu = (double*)malloc(sizeof(double) * M);
+  memset(e, 0, sizeof(double) * M);
+  for (int nu1 = p->n - 1; nu1 >= 0; --nu1) {
+    int k = sweeps_for(p, p->n - nu1);
+    for (int nu = nu1; nu >= nu1 - 1; --nu) {
+      if (nu < 0) continue;
+      restrict_and_visit(p, nu, k, r, e, r_nu, sig_nu, a_nu);
+    }
+    restrict_and_visit(p, nu1, k, r, e, r_nu, sig_nu, a_nu);
+  }
+  restrict_and_visit(p, 0, sweeps_for(p, p->n), r, e, r_nu, sig_nu, a_nu);
+  free(r_nu);
+  free(sig_nu);
+  free(a_nu);
+}
+
+/* Visit sequence of one cycle (levels, in order); returns the count.  Used to check the schedule. */
+int orc_schedule(const orc_problem* p, int* levels, int* sweeps, int cap) {
+  int m = 0;
+  for (int nu1 = p->n - 1; nu1 >= 0; --nu1) {
+    int k = sweeps_for(p, p->n - nu1);
+    for (int nu = nu1; nu >= nu1 - 1; --nu) {
+      if (nu < 0) continue;
+      if (m < cap) { levels[m] = nu; sweeps[m] = k; }
+      ++m;
+    }
+    if (m < cap) { levels[m] = nu1; sweeps[m] = k; }
+    ++m;
+  }
+  if (m < cap) { levels[m] = 0; sweeps[m] = sweeps_for(p, p->n); }
+  ++m;
+  return m;
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* Outer recurrence on accumulated residuals (Sec. 2, last paragraphs; Sec. 3.1 residual norm)   */
+/* ------------------------------------------------------------------------------------------ */
+
+/* Dirichlet value of a fixed node: the first Dirichlet face (order -x,+x,-y,+y,-z,+z) holding it. */
+static double dirichlet_value(const orc_problem* p, const int c[3]) {
+  int N = npts(p);
+  for (int k = 0; k < p->dim; ++k) {
+    if (c[k] == 0 && p->face_type[2 * k] == ORC_DIRICHLET) return p->face_value[2 * k];
+    if (c[k] == N - 1 && p->face_type[2 * k + 1] == ORC_DIRICHLET) return p->face_value[2 * k + 1];
+  }
+  return 0.0;
+}
+
+/* u = Dirichlet values on fixed nodes, 0 on unknowns. */
+void orc_lift(const orc_problem* p, double* u) {
+  long M = nnodes(p);
+  for (long i = 0; i < M; ++i) {
+    int c[3];
+    coords(p, i, c);
+    u[i] = is_dirichlet(p, c) ? dirichlet_value(p, c) : 0.0;
+  }
+}
+
+/* r = f - delta L_0 u at unknowns (Neumann images carry the prescribed derivative), 0 at fixed
+ * nodes. */
+void orc_residual(const orc_problem* p, const double* u, const double* f, double* r) {
+  long M = nnodes(p);
+  for (long i = 0; i < M; ++i) {
+    int c[3];
+    coords(p, i, c);
+    r[i] = is_dirichlet(p, c) ? 0.0 : f[i] - op_at(p, 0, p->sigma, p->a, u, c, 1);
+  }
+}
+
+/* Maximum norm over the unknowns. */
+double orc_max_norm(const orc_problem* p, const double* v) {
+  long M = nnodes(p);
+  double m = 0.0;
+  for (long i = 0; i < M; ++i) {
+    int c[3];
+    coords(p, i, c);
+    if (!is_dirichlet(p, c) && fabs(v[i]) > m) m = fabs(v[i]);
+  }
+  return m;
+}
+
+/* Repeat the cycle on the residual of the accumulated solution until ||r||_inf / ||f||_inf <= tol
+ * (Sec. 3.1; when f vanishes on the unknowns the initial residual is the scale).  The residual is
+ * recomputed from u each time (equal to the recurrence r_i = r_{i-1} - delta L e_{i-1} in exact
+ * arithmetic).  u is lifted first.  Returns the number of cycles run, or -1 if max_cycles cycles did
+ * not reach tol.  hist (may be NULL) receives the relative residual before each cycle and after the
+ * last (max_cycles + 1 entries). */
+int orc_solve(const orc_problem* p, const double* f, double tol, int max_cycles, double* u, double* hist) {
+  long M = nnodes(p);
+  double* r = (double*)malloc(sizeof(double) * M);
+  double* e = (double*)malloc(sizeof(double) * M);
+  orc_lift(p, u);
+  double scale = orc_max_norm(p, f);
+  int cycles = -1;
+  for (int c = 0;; ++c) {
+    orc_residual(p, u, f, r);
+    double rn = orc_max_norm(p, r);
+    if (c == 0 && scale == 0.0) scale = rn;
+    double rel = scale > 0.0 ? rn / scale : 0.0;
+    if (hist) hist[c] = rel;
+    if (rel <= tol) {
+      cycles = c;
+      break;
+    }
+    if (c == max_cycles) break;
+    orc_cycle(p, r, e);
+    for (long i = 0; i < M; ++i) u[i] += e[i];
+  }
+  free(r);
+  free(e);
+  return cycles;
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* Adjoint gradient for J(u(sigma, f)) with delta L_0(sigma) u = f, all faces Dirichlet           */
+/* ------------------------------------------------------------------------------------------ */
+
+/* Given the forward solution u and the adjoint lambda (delta L_0^T lambda = dJ/du on the unknowns,
+ * lambda = 0 on fixed nodes), dJ/dsigma_m = kappa/(2h^2) sum_{o: m+o inside} w_o
+ * (lambda_{m+o} - lambda_m)(u_{m+o} - u_m): the derivative of Eq. 5's link coefficient
+ * (sigma_i + sigma_j)/2 with respect to sigma_m, contracted with -lambda^T (d delta L/d sigma_m) u.
+ * dJ/df = lambda. */
+void orc_sigma_gradient(const orc_problem* p, const double* lambda, const double* u, double* g) {
+  int N = npts(p);
+  long M = nnodes(p);
+  double h = grid_h(p);
+  int o[26][3];
+  int m = offsets(p->dim, o);
+  double c0 = kappa(p) / (2.0 * h * h);
+  for (long i = 0; i < M; ++i) {
+    int c[3];
+    coords(p, i, c);
+    double acc = 0.0;
+    for (int q = 0; q < m; ++q) {
+      int nb[3] = {0, 0, 0};
+      int inside = 1;
+      for (int k = 0; k < p->dim; ++k) {
+        nb[k] = c[k] + o[q][k];
+        if (nb[k] < 0 || nb[k] > N - 1) inside = 0;
+      }
+      if (!inside) continue;
+      long j = at(p, nb);
+      acc += weight(o[q]) * (lambda[j] - lambda[i]) * (u[j] - u[i]);
+    }
+    g[i] = c0 * acc;
+  }
+}
