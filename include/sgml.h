@@ -1,0 +1,150 @@
+/*
+ * sgml.h -- C ABI of libsgml, a GB300 (sm_103a) implementation of the single-grid multi-level
+ * (SGML) method of Becerra-Sagredo, Mandujano and Malaga, "A GPU-based Multi-level Algorithm for
+ * Boundary Value Problems" (arXiv 1703.07206).
+ *
+ * The library solves, for a batch of independent problems on the unit square (dim = 2) or cube
+ * (dim = 3) with N = 2^n + 1 nodes per side,
+ *
+ *     L u = f,   L = div(sigma grad) + a                                  (Sec. 2 Eq. 1, Sec. 3)
+ *
+ * discretised with the radial 9-point (2-D) / 27-point (3-D) stencil of Eq. 5, by repeating the
+ * saw-like single cycle of Algorithm 3 (restriction, Algorithm 1 / Eqs. 3-4, and relaxation-
+ * interpolation, Algorithm 2) on the residual of the accumulated solution (Sec. 2, last
+ * paragraphs) until ||f - delta L u||_inf / ||f||_inf <= tol (Sec. 3.1).
+ *
+ * Conventions shared by every entry point:
+ *   - Every call returns an int status (sgml_status); no exception crosses the ABI.  On failure
+ *     sgml_last_error() returns a message for the calling thread.
+ *   - Node arrays hold N^dim doubles, row-major [z][y][x] with x fastest, boundary nodes included;
+ *     node i sits at x_i = i / (N - 1).
+ *   - Array pointers may be host or device pointers (unified addressing decides); the library
+ *     copies from / to them and never keeps them.  The grid owns all of its device memory.
+ *   - Work is issued on the CUDA stream given to sgml_create_grid.  Calls documented as
+ *     synchronising wait for that stream; the others are stream-ordered and return at once.
+ *   - Faces are ordered -x, +x, -y, +y, -z, +z (the last two ignored in 2-D).
+ */
+#ifndef SGML_H
+#define SGML_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sgml_grid* sgml_grid_t;
+
+typedef enum {
+  SGML_OK = 0,
+  SGML_ERR_ARG = -1,             /* invalid argument; nothing was changed */
+  SGML_ERR_CUDA = -2,            /* a CUDA call failed; the grid should be destroyed */
+  SGML_ERR_NOT_CONVERGED = -3,   /* solve_to_tol: max_cycles cycles did not reach the tolerance */
+  SGML_ERR_DIVERGED = -4,        /* the residual grew for several cycles above its start value */
+  SGML_ERR_BARRIER_TIMEOUT = -5, /* a grid-wide barrier of the cycle kernel gave up waiting */
+  SGML_ERR_NONFINITE = -6        /* a residual norm was NaN or infinite */
+} sgml_status;
+
+enum { SGML_FP64 = 0, SGML_MIXED = 1 };        /* cycle precision; the outer step is always FP64 */
+enum { SGML_DIRICHLET = 0, SGML_NEUMANN = 1 }; /* face types */
+enum { SGML_NORM_MAX = 0, SGML_NORM_L2 = 1 };
+enum { SGML_STENCIL_CONSISTENT = 0, SGML_STENCIL_LITERAL = 1 };
+
+/* Create a batch of `batch` problems of dimension `dim` (2 or 3); problem b has
+ * N_b = 2^n_levels[b] + 1 nodes per side (1 <= n_levels[b] <= 12 in 2-D, <= 10 in 3-D).
+ * `precision`: SGML_FP64 runs the whole cycle in FP64; SGML_MIXED runs restriction, relaxation and
+ * interpolation in FP32 on a scaled residual, keeping the outer residual and the solution sum in FP64.
+ * `cuda_stream` is a cudaStream_t (NULL = the legacy default stream).  Initially every face is
+ * Dirichlet 0, sigma = 1, a = 0 and f = 0; parameters are those of sgml_set_params' defaults.
+ * Allocates device memory; *out receives the handle. */
+int sgml_create_grid(int dim, int batch, const int* n_levels, int precision, void* cuda_stream,
+                     sgml_grid_t* out);
+
+/* Method parameters (Algorithm 3, Sec. 2): n_r = maximum relaxation-interpolations per visit
+ * (default 2, as in Fig. 3); theta in (0, 1] = fraction of the maximum stable pseudo-time step
+ * (default 0.7; the step at a node is theta * (kappa_d S_d / 2) / D_i with D_i minus the diagonal of
+ * delta L there, equal to theta (2^nu h)^2 / (2 sigma) for constant sigma, the bound of Sec. 2 and
+ * Sec. 3.4); schedule must be 0 (the zig-zag reading of Algorithm 3); stencil selects the constant
+ * of Eq. 5 (SGML_STENCIL_CONSISTENT: exact on quadratics; SGML_STENCIL_LITERAL: the printed
+ * 3/(13h) and its 2-D analogue); dt_mode must be 0 (Jacobi-scaled local step); max_cycles bounds
+ * sgml_solve_to_tol (default 200).  Stream-ordered. */
+int sgml_set_params(sgml_grid_t g, int n_r, double theta, int schedule, int stencil, int dt_mode,
+                    int max_cycles);
+
+/* Coefficients of L = div(sigma grad) + a for one problem (problem >= 0) or for all (problem = -1,
+ * arrays concatenated problem after problem).  sigma: N^dim positive node values, or NULL for
+ * sigma = 1.  a: N^dim node values, or NULL for the constant a_scalar.  a <= 0 is required (the
+ * pseudo-time step needs D_i > 0); a < 0 everywhere makes an all-Neumann problem well posed.
+ * Copies the arrays; the coefficient pyramid is rebuilt before the next cycle. */
+int sgml_set_coeffs(sgml_grid_t g, int problem, const double* sigma, const double* a, double a_scalar);
+
+/* Source f of L u = f (the paper's sign: a problem -Lap u = q passes f = -q).  N^dim values for one
+ * problem, or all problems concatenated when problem = -1.  Values on Dirichlet nodes are ignored.
+ * Copies the array and resets the solution (the next cycle starts from the lifted boundary values). */
+int sgml_set_source(sgml_grid_t g, int problem, const double* f);
+
+/* Boundary conditions of one problem (or all, problem = -1): face_type[2*dim] of SGML_DIRICHLET /
+ * SGML_NEUMANN and face_value[2*dim] (NULL = 0): the Dirichlet value of the face, or the prescribed
+ * outward normal derivative of a Neumann face (Sec. 2, boundary conditions).  A node on a Dirichlet
+ * face is fixed (Dirichlet wins where faces of both kinds meet; the first Dirichlet face in face
+ * order gives the value).  Neumann faces use even images (-k -> k) with u_image = u_mirror + 2 k h g.
+ * Resets the solution. */
+int sgml_set_bc(sgml_grid_t g, int problem, const int* face_type, const double* face_value);
+
+/* Run exactly ncycles cycles of Algorithm 3 for every problem from the current solution (the
+ * lifted boundary values after create/set_*), each followed by the FP64 outer step u += e,
+ * r = f - delta L u.  One persistent cooperative kernel launch.  Stream-ordered (asynchronous). */
+int sgml_run_cycle(sgml_grid_t g, int ncycles);
+
+/* Solve every problem from its lifted boundary values: repeat cycles until
+ * ||r||_inf / ||f||_inf <= rtol (Sec. 3.1; when f vanishes on the unknowns the initial residual is
+ * the scale) or max_cycles cycles.  One persistent cooperative kernel launch; synchronises.
+ * cycles_out[batch] and rel_res_out[batch] (either may be NULL) receive per problem the cycles run
+ * and the final relative residual.  Returns SGML_OK when every problem converged,
+ * SGML_ERR_NOT_CONVERGED / SGML_ERR_DIVERGED / SGML_ERR_NONFINITE otherwise (worst status). */
+int sgml_solve_to_tol(sgml_grid_t g, double rtol, int* cycles_out, double* rel_res_out);
+
+/* Relative residual of the current solution for every problem: ||f - delta L u|| / ||f|| over the
+ * unknowns in the max norm (SGML_NORM_MAX) or the Euclidean norm (SGML_NORM_L2).  rel_out[batch].
+ * Synchronises. */
+int sgml_residual_norm(sgml_grid_t g, int norm, double* rel_out);
+
+/* Copy the FP64 solution of one problem (N^dim values) into u.  Synchronises. */
+int sgml_get_solution(sgml_grid_t g, int problem, double* u);
+
+/* Per-problem statistics of the last run: cycles run (cumulative since the last reset), final
+ * relative residual (max norm), and the status (sgml_status) of the problem.  Synchronises. */
+int sgml_get_stats(sgml_grid_t g, int problem, int* cycles, double* rel_max, int* status);
+
+/* Relative max-norm residual before each cycle of the last sgml_solve_to_tol / sgml_run_cycle call
+ * and after its last cycle (cycles + 1 values, at most cap).  Synchronises.  Returns the count
+ * written through *count. */
+int sgml_get_history(sgml_grid_t g, int problem, double* hist, int cap, int* count);
+
+/* r = f - delta L_0 u for one problem, with u given (N^dim values; the grid's own solution is not
+ * touched), the grid's source, coefficients and boundary conditions (Neumann images carry the
+ * prescribed derivative); r = 0 on fixed nodes.  FP64.  Synchronises. */
+int sgml_residual(sgml_grid_t g, int problem, const double* u, double* r);
+
+/* Adjoint gradient of J(u) with respect to sigma for one all-Dirichlet problem: given the forward
+ * solution u and the adjoint lambda (the solution of delta L^T lambda = dJ/du on the unknowns,
+ * lambda = 0 on fixed nodes; delta L is symmetric there), writes
+ * dJ/dsigma_m = kappa/(2h^2) sum_{o, m+o inside} w_o (lambda_{m+o} - lambda_m)(u_{m+o} - u_m)
+ * (the derivative of Eq. 5's link coefficient (sigma_i + sigma_j)/2).  dJ/df = lambda.  FP64.
+ * Returns SGML_ERR_ARG for a problem with a Neumann face.  Synchronises. */
+int sgml_sigma_gradient(sgml_grid_t g, int problem, const double* lambda, const double* u, double* grad);
+
+/* Launch shape of the cycle kernel: threads per CTA (multiple of 32, 64..1024) and CTAs per SM
+ * (0 = as many as fit).  The cooperative launch needs all CTAs resident; the library clamps to the
+ * occupancy limit.  Used by the autotuner. */
+int sgml_set_launch(sgml_grid_t g, int threads, int ctas_per_sm);
+
+/* Number of kernel launches the library issued on this grid since creation (every kernel,
+ * setup included). */
+int sgml_launch_count(sgml_grid_t g, long long* count);
+
+int sgml_destroy(sgml_grid_t g);
+const char* sgml_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SGML_H */

@@ -1,0 +1,605 @@
+// sgml_api.cu -- host side of libsgml: the C ABI declared in include/sgml.h.
+//
+// The grid object owns every device buffer (layout in sgml_internal.cuh), the schedule of one
+// cycle (Algorithm 3) as a table of phases, and the launch shape of the persistent cooperative
+// cycle kernel.  Solves run as one kernel launch each; coefficient pyramids (restricted sigma and a,
+// Algorithm 1 applied to coefficients, and the local pseudo-time steps, Sec. 2 and Sec. 3.4) are
+// rebuilt by small setup kernels when the coefficients change.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "sgml.h"
+#include "sgml_internal.cuh"
+
+using namespace sgml;
+
+static thread_local std::string g_last_error;
+
+static int fail(int code, const std::string& msg) {
+  g_last_error = msg;
+  return code;
+}
+
+#define SGML_CUDA(call)                                                                   \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess) return fail(SGML_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+struct sgml_grid {
+  int dim = 2, batch = 0, mixed = 0, elem = 8;
+  cudaStream_t stream = nullptr;
+  int device = 0, sms = 0;
+  std::vector<ProblemDesc> P;
+  std::vector<long long> M0;
+  int n_max = 0;
+  // device state
+  ProblemDesc* d_probs = nullptr;
+  ProblemState* d_state = nullptr;
+  Accum* d_accum = nullptr;
+  GridSync* d_sync = nullptr;
+  Phase* d_phases = nullptr;
+  int nphases = 0;
+  long long* d_tiles = nullptr;
+  double* d_hist = nullptr;
+  int hist_cap = 0;
+  double *U = nullptr, *F = nullptr, *SIG64 = nullptr, *A64 = nullptr;
+  void *E = nullptr, *E2 = nullptr, *B = nullptr, *R = nullptr, *SIG = nullptr, *Q = nullptr;
+  long long full_total = 0, lvl_total = 0;
+  // parameters
+  int n_r = 2;
+  double theta = 0.7;
+  int stencil = SGML_STENCIL_CONSISTENT;
+  int max_cycles = 200;
+  int threads = 256, ctas_per_sm = 0, blocks = 0;
+  bool dirty_coeffs = true, dirty_desc = true, dirty_phases = true, dirty_tiles = true, fresh = true;
+  long long launches = 0;
+  ProblemState* h_state = nullptr;  // pinned
+};
+
+// ------------------------------------------------------------------------------------------------
+// Constants of the radial stencil (Eq. 5)
+// ------------------------------------------------------------------------------------------------
+static double w_edge() { return 1.0 / std::sqrt(2.0); }
+static double w_corner() { return 1.0 / std::sqrt(3.0); }
+
+// sum_o w_o over the 8 / 26 neighbours
+static double weight_sum(int dim) {
+  return dim == 3 ? 6.0 + 12.0 * w_edge() + 8.0 * w_corner() : 4.0 + 4.0 * w_edge();
+}
+
+// sum_o w_o o_1^2
+static double weight_moment(int dim) {
+  return dim == 3 ? 2.0 + 8.0 * w_edge() + 8.0 * w_corner() : 2.0 + 4.0 * w_edge();
+}
+
+static double kappa_of(int dim, int stencil) {
+  if (stencil == SGML_STENCIL_LITERAL) return dim == 3 ? 3.0 / 13.0 : 0.5;
+  return 2.0 / weight_moment(dim);
+}
+
+// delta_tau * D_i of the Jacobi-scaled step for theta = 1: kappa_consistent * S / 2.
+static double jacobi_gain(int dim) { return (2.0 / weight_moment(dim)) * weight_sum(dim) / 2.0; }
+
+static long long side(int n, int l) { return (1LL << (n - l)) + 1; }
+static long long nodes(int dim, int n, int l) {
+  long long N = side(n, l);
+  return dim == 3 ? N * N * N : N * N;
+}
+static long long round_up(long long x, long long a) { return (x + a - 1) / a * a; }
+
+// ------------------------------------------------------------------------------------------------
+// Schedule of one cycle (Algorithm 3) for the deepest problem of the batch; shallower problems
+// follow its suffix.
+// ------------------------------------------------------------------------------------------------
+static std::vector<Phase> build_phases(int n_max, int n_r) {
+  std::vector<Phase> ph;
+  for (int l = 1; l <= n_max - 1; ++l) ph.push_back(Phase{OP_RESTRICT, l, l - 1, 0, 0, 0});
+  struct Visit {
+    int level, tooth, first, final_visit;
+  };
+  std::vector<Visit> vs;
+  for (int nu1 = n_max - 1; nu1 >= 1; --nu1) {
+    vs.push_back({nu1, nu1, 1, 0});
+    vs.push_back({nu1 - 1, nu1, 0, 0});
+    vs.push_back({nu1, nu1, 0, 0});
+  }
+  vs.push_back({0, 0, 1, 1});  // tooth 0 (two level-0 visits) merged with the final level-0 visit
+  for (size_t q = 0; q < vs.size(); ++q) {
+    const Visit& v = vs[q];
+    if (q > 0) {
+      const Visit& u = vs[q - 1];
+      if (v.level == u.level - 1) {
+        const bool init = v.tooth == u.tooth;
+        ph.push_back(Phase{OP_PROLONG, v.level, u.tooth, 0, init ? kInit : 0, v.level + 1});
+      } else if (v.level == u.level + 1) {
+        ph.push_back(Phase{OP_INJECT, v.level, u.tooth, 0, 0, 0});
+      }
+    }
+    const int e = n_max - v.tooth;
+    const int k = std::min<long long>(n_r, 1LL << std::min(e, 30));
+    const int kk = v.final_visit ? 3 * k : k;
+    for (int s = 0; s < kk; ++s)
+      ph.push_back(Phase{OP_SWEEP, v.level, v.tooth, s,
+                         (v.final_visit ? kFinalVisit : 0) | (v.first ? kFirstOfTooth : 0), 0});
+  }
+  return ph;
+}
+
+static int upload_phases(sgml_grid* g) {
+  std::vector<Phase> ph = build_phases(g->n_max, g->n_r);
+  if (g->d_phases) SGML_CUDA(cudaFree(g->d_phases));
+  g->d_phases = nullptr;
+  g->nphases = (int)ph.size();
+  SGML_CUDA(cudaMalloc(&g->d_phases, sizeof(Phase) * std::max<size_t>(ph.size(), 1)));
+  SGML_CUDA(cudaMemcpyAsync(g->d_phases, ph.data(), sizeof(Phase) * ph.size(), cudaMemcpyHostToDevice, g->stream));
+  SGML_CUDA(cudaStreamSynchronize(g->stream));
+  g->dirty_phases = false;
+  return SGML_OK;
+}
+
+static int upload_tiles(sgml_grid* g) {
+  int bps = 0;
+  if (cycle_kernel_occupancy(g->mixed, g->dim, g->threads, &bps) != 0 || bps < 1)
+    return fail(SGML_ERR_CUDA, "occupancy query failed for the cycle kernel");
+  if (g->ctas_per_sm > 0) bps = std::min(bps, g->ctas_per_sm);
+  g->blocks = g->sms * bps;
+  std::vector<long long> tp((size_t)kMaxLevels * (g->batch + 1), 0);
+  for (int l = 0; l < kMaxLevels; ++l)
+    for (int b = 0; b < g->batch; ++b) {
+      long long t = (l <= g->P[b].n - 1) ? (nodes(g->dim, g->P[b].n, l) + g->threads - 1) / g->threads : 0;
+      tp[(size_t)l * (g->batch + 1) + b + 1] = tp[(size_t)l * (g->batch + 1) + b] + t;
+    }
+  if (!g->d_tiles) SGML_CUDA(cudaMalloc(&g->d_tiles, sizeof(long long) * tp.size()));
+  SGML_CUDA(cudaMemcpyAsync(g->d_tiles, tp.data(), sizeof(long long) * tp.size(), cudaMemcpyHostToDevice, g->stream));
+  SGML_CUDA(cudaStreamSynchronize(g->stream));
+  g->dirty_tiles = false;
+  return SGML_OK;
+}
+
+static int ensure_hetero_pools(sgml_grid* g, bool need_a) {
+  if (!g->SIG64) {
+    SGML_CUDA(cudaMalloc(&g->SIG64, sizeof(double) * g->full_total));
+    SGML_CUDA(cudaMalloc(&g->SIG, (size_t)g->elem * g->lvl_total));
+    SGML_CUDA(cudaMalloc(&g->Q, (size_t)g->elem * g->lvl_total));
+    SGML_CUDA(cudaMemsetAsync(g->SIG, 0, (size_t)g->elem * g->lvl_total, g->stream));
+    SGML_CUDA(cudaMemsetAsync(g->Q, 0, (size_t)g->elem * g->lvl_total, g->stream));
+  }
+  if (need_a && !g->A64) {
+    SGML_CUDA(cudaMalloc(&g->A64, sizeof(double) * g->full_total));
+    SGML_CUDA(cudaMemsetAsync(g->A64, 0, sizeof(double) * g->full_total, g->stream));
+  }
+  return SGML_OK;
+}
+
+// Coefficient pyramid: restricted sigma / a and the local steps of every level (setup, excluded
+// from the solve).  Homogeneous problems get one constant per level computed here.
+static int build_coeffs(sgml_grid* g) {
+  const double kap = kappa_of(g->dim, g->stencil);
+  const double tg = g->theta * jacobi_gain(g->dim);
+  std::vector<double*> tmp;
+  for (int b = 0; b < g->batch; ++b) {
+    ProblemDesc& P = g->P[b];
+    for (int l = 0; l < kMaxLevels; ++l) P.q_const[l] = 0.0;
+    for (int l = 0; l <= P.n - 1; ++l) {
+      const double H = P.h * (double)(1LL << l);
+      const double c = kap / (2.0 * H * H);
+      const double D = c * 2.0 * weight_sum(g->dim) - P.a_scalar;
+      P.q_const[l] = tg / D * c;
+    }
+    if (!P.hetero) continue;
+    // level pyramid of sigma (and a) in FP64 temporaries
+    std::vector<double*> sig(P.n, nullptr), av(P.n, nullptr);
+    sig[0] = g->SIG64 + P.off_full;
+    av[0] = P.a_per_node ? g->A64 + P.off_full : nullptr;
+    for (int l = 1; l <= P.n - 1; ++l) {
+      const long long M = nodes(g->dim, P.n, l);
+      SGML_CUDA(cudaMalloc(&sig[l], sizeof(double) * M));
+      tmp.push_back(sig[l]);
+      SGML_CUDA(launch_restrict64(g->dim, sig[l - 1], (int)side(P.n, l - 1), sig[l], (int)side(P.n, l), g->stream));
+      g->launches++;
+      if (P.a_per_node) {
+        SGML_CUDA(cudaMalloc(&av[l], sizeof(double) * M));
+        tmp.push_back(av[l]);
+        SGML_CUDA(launch_restrict64(g->dim, av[l - 1], (int)side(P.n, l - 1), av[l], (int)side(P.n, l), g->stream));
+        g->launches++;
+      }
+    }
+    for (int l = 0; l <= P.n - 1; ++l) {
+      SGML_CUDA(launch_setup_level(g->mixed, g->dim, P, l, sig[l], av[l], kap, w_edge(), w_corner(), tg, g->SIG, g->Q,
+                                   g->stream));
+      g->launches++;
+    }
+  }
+  SGML_CUDA(cudaStreamSynchronize(g->stream));
+  for (double* t : tmp) SGML_CUDA(cudaFree(t));
+  g->dirty_coeffs = false;
+  g->dirty_desc = true;
+  return SGML_OK;
+}
+
+static int upload_desc(sgml_grid* g) {
+  SGML_CUDA(cudaMemcpyAsync(g->d_probs, g->P.data(), sizeof(ProblemDesc) * g->batch, cudaMemcpyHostToDevice, g->stream));
+  SGML_CUDA(cudaStreamSynchronize(g->stream));
+  g->dirty_desc = false;
+  return SGML_OK;
+}
+
+static int prepare(sgml_grid* g) {
+  int st;
+  if (g->dirty_coeffs && (st = build_coeffs(g)) != SGML_OK) return st;
+  if (g->dirty_desc && (st = upload_desc(g)) != SGML_OK) return st;
+  if (g->dirty_phases && (st = upload_phases(g)) != SGML_OK) return st;
+  if (g->dirty_tiles && (st = upload_tiles(g)) != SGML_OK) return st;
+  return SGML_OK;
+}
+
+static int ensure_hist(sgml_grid* g, int cap) {
+  if (cap <= g->hist_cap) return SGML_OK;
+  SGML_CUDA(cudaStreamSynchronize(g->stream));
+  if (g->d_hist) SGML_CUDA(cudaFree(g->d_hist));
+  g->hist_cap = std::max(cap, 256);
+  SGML_CUDA(cudaMalloc(&g->d_hist, sizeof(double) * (size_t)g->hist_cap * g->batch));
+  SGML_CUDA(cudaMemsetAsync(g->d_hist, 0, sizeof(double) * (size_t)g->hist_cap * g->batch, g->stream));
+  return SGML_OK;
+}
+
+// One launch of the persistent cycle kernel: up to max_cycles cycles per problem, stopping a
+// problem when its relative residual reaches tol (tol < 0: never).
+static int launch(sgml_grid* g, int max_cycles, double tol) {
+  int st;
+  if ((st = prepare(g)) != SGML_OK) return st;
+  if ((st = ensure_hist(g, max_cycles + 1)) != SGML_OK) return st;
+  const bool fresh = g->fresh;
+  SGML_CUDA(cudaMemsetAsync(g->d_accum, 0, sizeof(Accum) * g->batch, g->stream));
+  SGML_CUDA(cudaMemsetAsync(g->d_sync, 0, sizeof(GridSync), g->stream));
+  if (fresh) SGML_CUDA(cudaMemsetAsync(g->d_state, 0, sizeof(ProblemState) * g->batch, g->stream));
+  KernelParams p;
+  std::memset(&p, 0, sizeof(p));
+  p.dim = g->dim;
+  p.batch = g->batch;
+  p.n_max = g->n_max;
+  p.mixed = g->mixed;
+  p.probs = g->d_probs;
+  p.state = g->d_state;
+  p.accum = g->d_accum;
+  p.phases = g->d_phases;
+  p.nphases = g->nphases;
+  p.tile_prefix = g->d_tiles;
+  p.tile = g->threads;
+  p.fresh = fresh ? 1 : 0;
+  p.max_cycles = max_cycles;
+  p.tol = tol;
+  p.kappa = kappa_of(g->dim, g->stencil);
+  p.w_edge = w_edge();
+  p.w_corner = w_corner();
+  p.omega = g->theta * jacobi_gain(g->dim);
+  p.n_r = g->n_r;
+  p.sync = g->d_sync;
+  p.timeout_ns = 2000000000ull;  // 2 s per barrier wait
+  p.hist = g->d_hist;
+  p.hist_cap = g->hist_cap;
+  p.U = g->U;
+  p.F = g->F;
+  p.SIG64 = g->SIG64;
+  p.A64 = g->A64;
+  p.E = g->E;
+  p.E2 = g->E2;
+  p.B = g->B;
+  p.R = g->R;
+  p.SIG = g->SIG;
+  p.Q = g->Q;
+  SGML_CUDA(launch_cycle_kernel(p, g->mixed, g->dim, g->blocks, g->threads, g->stream));
+  g->launches++;
+  g->fresh = false;
+  return SGML_OK;
+}
+
+static int sync_and_check(sgml_grid* g) {
+  SGML_CUDA(cudaStreamSynchronize(g->stream));
+  GridSync s;
+  SGML_CUDA(cudaMemcpy(&s, g->d_sync, sizeof(GridSync), cudaMemcpyDeviceToHost));
+  if (s.error) return fail(SGML_ERR_BARRIER_TIMEOUT, "a grid barrier of the cycle kernel timed out");
+  SGML_CUDA(cudaMemcpy(g->h_state, g->d_state, sizeof(ProblemState) * g->batch, cudaMemcpyDeviceToHost));
+  return SGML_OK;
+}
+
+static bool valid(sgml_grid* g) { return g != nullptr && g->batch > 0; }
+
+// ------------------------------------------------------------------------------------------------
+// C ABI
+// ------------------------------------------------------------------------------------------------
+extern "C" {
+
+int sgml_create_grid(int dim, int batch, const int* n_levels, int precision, void* cuda_stream, sgml_grid_t* out) {
+  if (!out) return fail(SGML_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (dim != 2 && dim != 3) return fail(SGML_ERR_ARG, "dim must be 2 or 3");
+  if (batch < 1 || batch > 65536 || !n_levels) return fail(SGML_ERR_ARG, "batch must be in 1..65536 with n_levels given");
+  if (precision != SGML_FP64 && precision != SGML_MIXED) return fail(SGML_ERR_ARG, "precision must be SGML_FP64 or SGML_MIXED");
+  const int nmax_allowed = dim == 3 ? 10 : 12;
+  for (int b = 0; b < batch; ++b)
+    if (n_levels[b] < 1 || n_levels[b] > nmax_allowed)
+      return fail(SGML_ERR_ARG, "n_levels[b] out of range (1..12 in 2-D, 1..10 in 3-D)");
+  sgml_grid* g = new sgml_grid();
+  g->dim = dim;
+  g->batch = batch;
+  g->mixed = precision == SGML_MIXED;
+  g->elem = g->mixed ? 4 : 8;
+  g->stream = (cudaStream_t)cuda_stream;
+  g->P.resize(batch);
+  long long full = 0, lvl = 0;
+  for (int b = 0; b < batch; ++b) {
+    ProblemDesc& P = g->P[b];
+    std::memset(&P, 0, sizeof(P));
+    P.n = n_levels[b];
+    P.h = 1.0 / (double)((1LL << P.n));
+    P.off_full = full;
+    full += round_up(nodes(dim, P.n, 0), 32);
+    for (int l = 0; l <= P.n - 1; ++l) {
+      P.off_lvl[l] = lvl;
+      lvl += round_up(nodes(dim, P.n, l), 64);
+    }
+    g->n_max = std::max(g->n_max, P.n);
+  }
+  g->full_total = full;
+  g->lvl_total = lvl;
+  auto cleanup = [&](int code, const std::string& m) {
+    sgml_destroy(g);
+    return fail(code, m);
+  };
+  cudaError_t e;
+#define ALLOC(ptr, bytes)                                                      \
+  if ((e = cudaMalloc((void**)&(ptr), (bytes))) != cudaSuccess) return cleanup(SGML_ERR_CUDA, std::string("cudaMalloc: ") + cudaGetErrorString(e)); \
+  if ((e = cudaMemsetAsync((ptr), 0, (bytes), g->stream)) != cudaSuccess) return cleanup(SGML_ERR_CUDA, cudaGetErrorString(e));
+  if ((e = cudaGetDevice(&g->device)) != cudaSuccess) return cleanup(SGML_ERR_CUDA, cudaGetErrorString(e));
+  if ((e = cudaDeviceGetAttribute(&g->sms, cudaDevAttrMultiProcessorCount, g->device)) != cudaSuccess)
+    return cleanup(SGML_ERR_CUDA, cudaGetErrorString(e));
+  ALLOC(g->U, sizeof(double) * full);
+  ALLOC(g->F, sizeof(double) * full);
+  ALLOC(g->E, (size_t)g->elem * lvl);
+  ALLOC(g->E2, (size_t)g->elem * lvl);
+  ALLOC(g->B, (size_t)g->elem * lvl);
+  ALLOC(g->R, (size_t)g->elem * lvl);
+  ALLOC(g->d_probs, sizeof(ProblemDesc) * batch);
+  ALLOC(g->d_state, sizeof(ProblemState) * batch);
+  ALLOC(g->d_accum, sizeof(Accum) * batch);
+  ALLOC(g->d_sync, sizeof(GridSync));
+#undef ALLOC
+  if ((e = cudaMallocHost(&g->h_state, sizeof(ProblemState) * batch)) != cudaSuccess)
+    return cleanup(SGML_ERR_CUDA, cudaGetErrorString(e));
+  std::memset(g->h_state, 0, sizeof(ProblemState) * batch);
+  if ((e = cudaStreamSynchronize(g->stream)) != cudaSuccess) return cleanup(SGML_ERR_CUDA, cudaGetErrorString(e));
+  *out = g;
+  return SGML_OK;
+}
+
+int sgml_set_params(sgml_grid_t g, int n_r, double theta, int schedule, int stencil, int dt_mode, int max_cycles) {
+  if (!valid(g)) return fail(SGML_ERR_ARG, "invalid grid");
+  if (n_r < 1 || n_r > 64) return fail(SGML_ERR_ARG, "n_r must be in 1..64");
+  if (!(theta > 0.0 && theta <= 2.0)) return fail(SGML_ERR_ARG, "theta must be in (0, 2]");
+  if (schedule != 0) return fail(SGML_ERR_ARG, "only schedule 0 (zig-zag reading of Algorithm 3) is implemented");
+  if (stencil != SGML_STENCIL_CONSISTENT && stencil != SGML_STENCIL_LITERAL) return fail(SGML_ERR_ARG, "bad stencil");
+  if (dt_mode != 0) return fail(SGML_ERR_ARG, "only dt_mode 0 (Jacobi-scaled local step) is implemented");
+  if (max_cycles < 0) return fail(SGML_ERR_ARG, "max_cycles must be >= 0");
+  if (n_r != g->n_r) g->dirty_phases = true;
+  if (theta != g->theta || stencil != g->stencil) g->dirty_coeffs = true;
+  g->n_r = n_r;
+  g->theta = theta;
+  g->stencil = stencil;
+  g->max_cycles = max_cycles;
+  g->fresh = true;
+  return SGML_OK;
+}
+
+int sgml_set_coeffs(sgml_grid_t g, int problem, const double* sigma, const double* a, double a_scalar) {
+  if (!valid(g)) return fail(SGML_ERR_ARG, "invalid grid");
+  if (problem < -1 || problem >= g->batch) return fail(SGML_ERR_ARG, "problem out of range");
+  if (!(a_scalar <= 0.0)) return fail(SGML_ERR_ARG, "a_scalar must be <= 0");
+  int st;
+  if ((sigma || a) && (st = ensure_hetero_pools(g, a != nullptr)) != SGML_OK) return st;
+  long long src = 0;
+  for (int b = (problem < 0 ? 0 : problem); b < (problem < 0 ? g->batch : problem + 1); ++b) {
+    ProblemDesc& P = g->P[b];
+    const long long M = nodes(g->dim, P.n, 0);
+    P.hetero = (sigma || a) ? 1 : 0;
+    P.a_per_node = a ? 1 : 0;
+    P.a_scalar = a ? 0.0 : a_scalar;
+    if (sigma) SGML_CUDA(cudaMemcpyAsync(g->SIG64 + P.off_full, sigma + src, sizeof(double) * M, cudaMemcpyDefault, g->stream));
+    else if (a) {
+      SGML_CUDA(launch_fill(g->SIG64 + P.off_full, M, 1.0, g->stream));
+      g->launches++;
+    }
+    if (a) SGML_CUDA(cudaMemcpyAsync(g->A64 + P.off_full, a + src, sizeof(double) * M, cudaMemcpyDefault, g->stream));
+    src += M;
+  }
+  g->dirty_coeffs = true;
+  g->dirty_desc = true;
+  g->fresh = true;
+  return SGML_OK;
+}
+
+int sgml_set_source(sgml_grid_t g, int problem, const double* f) {
+  if (!valid(g)) return fail(SGML_ERR_ARG, "invalid grid");
+  if (problem < -1 || problem >= g->batch || !f) return fail(SGML_ERR_ARG, "problem out of range or f NULL");
+  long long src = 0;
+  for (int b = (problem < 0 ? 0 : problem); b < (problem < 0 ? g->batch : problem + 1); ++b) {
+    const long long M = nodes(g->dim, g->P[b].n, 0);
+    SGML_CUDA(cudaMemcpyAsync(g->F + g->P[b].off_full, f + src, sizeof(double) * M, cudaMemcpyDefault, g->stream));
+    src += M;
+  }
+  g->fresh = true;
+  return SGML_OK;
+}
+
+int sgml_set_bc(sgml_grid_t g, int problem, const int* face_type, const double* face_value) {
+  if (!valid(g)) return fail(SGML_ERR_ARG, "invalid grid");
+  if (problem < -1 || problem >= g->batch || !face_type) return fail(SGML_ERR_ARG, "problem out of range or face_type NULL");
+  const int nf = 2 * g->dim;
+  for (int k = 0; k < nf; ++k)
+    if (face_type[k] != SGML_DIRICHLET && face_type[k] != SGML_NEUMANN) return fail(SGML_ERR_ARG, "bad face type");
+  for (int b = (problem < 0 ? 0 : problem); b < (problem < 0 ? g->batch : problem + 1); ++b) {
+    ProblemDesc& P = g->P[b];
+    for (int k = 0; k < 6; ++k) {
+      P.face_type[k] = k < nf ? face_type[k] : SGML_DIRICHLET;
+      P.face_value[k] = (k < nf && face_value) ? face_value[k] : 0.0;
+    }
+  }
+  g->dirty_desc = true;
+  g->fresh = true;
+  return SGML_OK;
+}
+
+int sgml_run_cycle(sgml_grid_t g, int ncycles) {
+  if (!valid(g)) return fail(SGML_ERR_ARG, "invalid grid");
+  if (ncycles < 0) return fail(SGML_ERR_ARG, "ncycles must be >= 0");
+  return launch(g, ncycles, -1.0);
+}
+
+int sgml_solve_to_tol(sgml_grid_t g, double rtol, int* cycles_out, double* rel_res_out) {
+  if (!valid(g)) return fail(SGML_ERR_ARG, "invalid grid");
+  if (!(rtol >= 0.0)) return fail(SGML_ERR_ARG, "rtol must be >= 0");
+  g->fresh = true;
+  int st = launch(g, g->max_cycles, rtol);
+  if (st != SGML_OK) return st;
+  if ((st = sync_and_check(g)) != SGML_OK) return st;
+  int worst = SGML_OK;
+  for (int b = 0; b < g->batch; ++b) {
+    if (cycles_out) cycles_out[b] = g->h_state[b].cycles;
+    if (rel_res_out) rel_res_out[b] = g->h_state[b].rel;
+    if (g->h_state[b].status < worst) worst = g->h_state[b].status;
+  }
+  if (worst != SGML_OK) {
+    char buf[128];
+    std::snprintf(buf, sizeof(buf), "solve ended with status %d for at least one problem", worst);
+    g_last_error = buf;
+  }
+  return worst;
+}
+
+int sgml_residual_norm(sgml_grid_t g, int norm, double* rel_out) {
+  if (!valid(g)) return fail(SGML_ERR_ARG, "invalid grid");
+  if ((norm != SGML_NORM_MAX && norm != SGML_NORM_L2) || !rel_out) return fail(SGML_ERR_ARG, "bad norm or rel_out NULL");
+  int st = launch(g, 0, -1.0);
+  if (st != SGML_OK) return st;
+  if ((st = sync_and_check(g)) != SGML_OK) return st;
+  for (int b = 0; b < g->batch; ++b) rel_out[b] = norm == SGML_NORM_MAX ? g->h_state[b].rel : g->h_state[b].rel_l2;
+  return SGML_OK;
+}
+
+int sgml_get_solution(sgml_grid_t g, int problem, double* u) {
+  if (!valid(g)) return fail(SGML_ERR_ARG, "invalid grid");
+  if (problem < 0 || problem >= g->batch || !u) return fail(SGML_ERR_ARG, "problem out of range or u NULL");
+  const ProblemDesc& P = g->P[problem];
+  SGML_CUDA(cudaMemcpyAsync(u, g->U + P.off_full, sizeof(double) * nodes(g->dim, P.n, 0), cudaMemcpyDefault, g->stream));
+  SGML_CUDA(cudaStreamSynchronize(g->stream));
+  return SGML_OK;
+}
+
+int sgml_get_stats(sgml_grid_t g, int problem, int* cycles, double* rel_max, int* status) {
+  if (!valid(g)) return fail(SGML_ERR_ARG, "invalid grid");
+  if (problem < 0 || problem >= g->batch) return fail(SGML_ERR_ARG, "problem out of range");
+  int st = sync_and_check(g);
+  if (st != SGML_OK) return st;
+  if (cycles) *cycles = g->h_state[problem].cycles;
+  if (rel_max) *rel_max = g->h_state[problem].rel;
+  if (status) *status = g->h_state[problem].status;
+  return SGML_OK;
+}
+
+int sgml_get_history(sgml_grid_t g, int problem, double* hist, int cap, int* count) {
+  if (!valid(g)) return fail(SGML_ERR_ARG, "invalid grid");
+  if (problem < 0 || problem >= g->batch || !hist || cap < 0) return fail(SGML_ERR_ARG, "bad arguments");
+  int st = sync_and_check(g);
+  if (st != SGML_OK) return st;
+  // the row holds the relative residual before each cycle of the last launch and after its last
+  int n = std::min(std::min(cap, g->hist_cap), g->h_state[problem].hist_len);
+  std::vector<double> row(g->hist_cap);
+  SGML_CUDA(cudaMemcpy(row.data(), g->d_hist + (size_t)problem * g->hist_cap, sizeof(double) * g->hist_cap, cudaMemcpyDeviceToHost));
+  for (int i = 0; i < n; ++i) hist[i] = row[i];
+  if (count) *count = n;
+  return SGML_OK;
+}
+
+int sgml_residual(sgml_grid_t g, int problem, const double* u, double* r) {
+  if (!valid(g)) return fail(SGML_ERR_ARG, "invalid grid");
+  if (problem < 0 || problem >= g->batch || !u || !r) return fail(SGML_ERR_ARG, "bad arguments");
+  int st;
+  if (g->dirty_desc && (st = upload_desc(g)) != SGML_OK) return st;
+  const ProblemDesc& P = g->P[problem];
+  const long long M = nodes(g->dim, P.n, 0);
+  double *du = nullptr, *dr = nullptr;
+  SGML_CUDA(cudaMalloc(&du, sizeof(double) * M));
+  SGML_CUDA(cudaMalloc(&dr, sizeof(double) * M));
+  SGML_CUDA(cudaMemcpyAsync(du, u, sizeof(double) * M, cudaMemcpyDefault, g->stream));
+  SGML_CUDA(launch_residual64(g->dim, P, du, g->F + P.off_full, g->SIG64 ? g->SIG64 + P.off_full : nullptr,
+                              g->A64 ? g->A64 + P.off_full : nullptr, kappa_of(g->dim, g->stencil), w_edge(),
+                              w_corner(), dr, g->stream));
+  g->launches++;
+  SGML_CUDA(cudaMemcpyAsync(r, dr, sizeof(double) * M, cudaMemcpyDefault, g->stream));
+  SGML_CUDA(cudaStreamSynchronize(g->stream));
+  SGML_CUDA(cudaFree(du));
+  SGML_CUDA(cudaFree(dr));
+  return SGML_OK;
+}
+
+int sgml_sigma_gradient(sgml_grid_t g, int problem, const double* lambda, const double* u, double* grad) {
+  if (!valid(g)) return fail(SGML_ERR_ARG, "invalid grid");
+  if (problem < 0 || problem >= g->batch || !lambda || !u || !grad) return fail(SGML_ERR_ARG, "bad arguments");
+  const ProblemDesc& P = g->P[problem];
+  for (int k = 0; k < 2 * g->dim; ++k)
+    if (P.face_type[k] != SGML_DIRICHLET) return fail(SGML_ERR_ARG, "the sigma gradient needs all faces Dirichlet");
+  const long long M = nodes(g->dim, P.n, 0);
+  double *dl = nullptr, *du = nullptr, *dg = nullptr;
+  SGML_CUDA(cudaMalloc(&dl, sizeof(double) * M));
+  SGML_CUDA(cudaMalloc(&du, sizeof(double) * M));
+  SGML_CUDA(cudaMalloc(&dg, sizeof(double) * M));
+  SGML_CUDA(cudaMemcpyAsync(dl, lambda, sizeof(double) * M, cudaMemcpyDefault, g->stream));
+  SGML_CUDA(cudaMemcpyAsync(du, u, sizeof(double) * M, cudaMemcpyDefault, g->stream));
+  SGML_CUDA(launch_sigma_gradient(g->dim, P, dl, du, kappa_of(g->dim, g->stencil), w_edge(), w_corner(), dg, g->stream));
+  g->launches++;
+  SGML_CUDA(cudaMemcpyAsync(grad, dg, sizeof(double) * M, cudaMemcpyDefault, g->stream));
+  SGML_CUDA(cudaStreamSynchronize(g->stream));
+  SGML_CUDA(cudaFree(dl));
+  SGML_CUDA(cudaFree(du));
+  SGML_CUDA(cudaFree(dg));
+  return SGML_OK;
+}
+
+int sgml_set_launch(sgml_grid_t g, int threads, int ctas_per_sm) {
+  if (!valid(g)) return fail(SGML_ERR_ARG, "invalid grid");
+  if (threads < 64 || threads > 1024 || threads % 32 != 0 || ctas_per_sm < 0)
+    return fail(SGML_ERR_ARG, "threads must be a multiple of 32 in 64..1024, ctas_per_sm >= 0");
+  g->threads = threads;
+  g->ctas_per_sm = ctas_per_sm;
+  g->dirty_tiles = true;
+  return SGML_OK;
+}
+
+int sgml_launch_count(sgml_grid_t g, long long* count) {
+  if (!valid(g) || !count) return fail(SGML_ERR_ARG, "invalid grid or count NULL");
+  *count = g->launches;
+  return SGML_OK;
+}
+
+int sgml_destroy(sgml_grid_t g) {
+  if (!g) return SGML_OK;
+  cudaStreamSynchronize(g->stream);
+  void* ptrs[] = {g->U, g->F, g->SIG64, g->A64, g->E, g->E2, g->B, g->R, g->SIG, g->Q,
+                  g->d_probs, g->d_state, g->d_accum, g->d_sync, g->d_phases, g->d_tiles, g->d_hist};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  if (g->h_state) cudaFreeHost(g->h_state);
+  delete g;
+  return SGML_OK;
+}
+
+const char* sgml_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"

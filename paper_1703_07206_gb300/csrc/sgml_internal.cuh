@@ -1,0 +1,123 @@
+// sgml_internal.cuh -- data layout shared by the host side (sgml_api.cu) and the device side
+// (sgml_kernels.cu) of libsgml.  Not part of the public ABI.
+//
+// Memory layout in HBM (one allocation per pool, all problems of the batch back to back):
+//   FP64 full-grid pools, N^d doubles per problem at ProblemDesc::off_full:
+//     U (solution), F (source), SIG64 (sigma), A64 (per-node a)
+//   cycle-precision level pools (T = double or float), per problem levels 0..n-1 back to back at
+//   ProblemDesc::off_lvl[l], level l holding (2^(n-l)+1)^d nodes (the level-l subset of the single
+//   grid stored compactly, row-major [z][y][x]):
+//     E, E2 (Jacobi ping-pong of the correction e), B (value of E when last injected from below),
+//     R (restricted residual pyramid), SIG (restricted sigma), Q (local step times kappa/(2H^2)).
+// Every level array starts on a 256-byte boundary.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace sgml {
+
+constexpr int kMaxLevels = 13;  // n <= 12
+
+enum Op : int { OP_RESTRICT = 0, OP_SWEEP = 1, OP_PROLONG = 2, OP_INJECT = 3 };
+
+// Phase flags
+constexpr int kFinalVisit = 1;   // SWEEP: merged last level-0 visit (tooth 0 and the final visit)
+constexpr int kFirstOfTooth = 2; // SWEEP: first visit of its tooth
+constexpr int kInit = 4;         // PROLONG: first arrival at the target level in this cycle
+
+// One step of the cycle's schedule; a grid-wide barrier follows each phase.
+struct Phase {
+  int op;
+  int level;       // level whose nodes the phase writes
+  int tooth;       // SWEEP: tooth nu1 of the visit; PROLONG / INJECT: tooth of the visit just ended
+  int sweep;       // SWEEP: sweep index inside the visit
+  int flags;
+  int prev_tooth;  // PROLONG (not kInit): tooth of the last visit at the target level
+};
+
+struct ProblemDesc {
+  int n;                // N = 2^n + 1 nodes per side at level 0
+  int hetero;           // per-node SIG / Q arrays are used
+  int a_per_node;       // A64 holds per-node a
+  int face_type[6];     // 0 Dirichlet, 1 Neumann (-x,+x,-y,+y,-z,+z)
+  double face_value[6]; // Dirichlet value or outward derivative
+  double h;
+  double a_scalar;
+  long long off_full;              // element offset in the FP64 full-grid pools
+  long long off_lvl[kMaxLevels];   // element offset of level l in the level pools
+  double q_const[kMaxLevels];      // homogeneous problems: delta_tau * kappa / (2 H^2) per level
+};
+
+// Per-problem running state, written by CTA 0 of the cycle kernel between barriers.
+struct ProblemState {
+  double fnorm;           // max-norm normaliser of the residual
+  double fnorm2;          // L2 normaliser
+  double rmax_prev;       // max-norm of the latest residual (sets the next cast scale)
+  double scale_used[2];   // scale of the residual cast in cycle c (slot c & 1)
+  double rel, rel_l2;     // latest relative residuals
+  double rel_prev;
+  int cycles;             // cycles completed since the last reset
+  int status;             // sgml_status of the problem
+  int grow;               // consecutive cycles with a growing residual
+  int hist_len;           // entries of the history row written by the last launch
+};
+
+// Norm accumulators and the per-launch stop flag (zeroed by the host before every launch).
+struct Accum {
+  unsigned long long rmax_bits[2];
+  double rsum2[2];
+  unsigned long long fmax_bits;
+  double fsum2;
+  int done;               // the problem stopped in the current launch
+  int pad;
+};
+
+struct GridSync {
+  unsigned int count;
+  unsigned int gen;
+  int error;       // 1: a barrier timed out
+  int active[2];   // any problem still active after the check of cycle c (slot c & 1)
+  int pad[3];
+};
+
+struct KernelParams {
+  int dim, batch, n_max;
+  int mixed;
+  const ProblemDesc* probs;
+  ProblemState* state;
+  Accum* accum;
+  const Phase* phases;
+  int nphases;
+  const long long* tile_prefix;  // [kMaxLevels][batch + 1] cumulative tile counts per level
+  int tile;                      // nodes per tile (= blockDim.x)
+  int fresh;                     // lift u and measure f first
+  int max_cycles;
+  double tol;
+  double kappa;                  // stencil constant (consistent or literal)
+  double w_edge, w_corner;       // 1/sqrt(2), 1/sqrt(3)
+  double omega;                  // delta_tau * D_i of the Jacobi-scaled step
+  int n_r;
+  GridSync* sync;
+  unsigned long long timeout_ns;
+  double* hist;
+  int hist_cap;
+  double *U, *F, *SIG64, *A64;
+  void *E, *E2, *B, *R, *SIG, *Q;
+};
+
+// Host-side launchers (sgml_kernels.cu)
+cudaError_t launch_cycle_kernel(const KernelParams& p, int precision_mixed, int dim, int blocks,
+                                int threads, cudaStream_t s);
+int cycle_kernel_occupancy(int precision_mixed, int dim, int threads, int* blocks_per_sm);
+cudaError_t launch_setup_level(int mixed, int dim, const ProblemDesc& P, int level, const double* sig_l,
+                               const double* a_l, double kappa, double w_edge, double w_corner,
+                               double theta_gain, void* SIG_T, void* Q_T, cudaStream_t s);
+cudaError_t launch_restrict64(int dim, const double* src, int Ns, double* dst, int Nt, cudaStream_t s);
+cudaError_t launch_residual64(int dim, const ProblemDesc& P, const double* U, const double* F,
+                              const double* SIG64, const double* A64, double kappa, double w_edge,
+                              double w_corner, double* r, cudaStream_t s);
+cudaError_t launch_sigma_gradient(int dim, const ProblemDesc& P, const double* lam, const double* U,
+                                  double kappa, double w_edge, double w_corner, double* g, cudaStream_t s);
+cudaError_t launch_fill(double* dst, long long n, double v, cudaStream_t s);
+
+}  // namespace sgml

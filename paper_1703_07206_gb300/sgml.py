@@ -1,0 +1,230 @@
+"""Python binding of libsgml (ctypes): the C entry points of include/sgml.h under the same names,
+plus a small ``Grid`` class.  Argument marshalling only -- every step of the solver runs in the CUDA
+library; if the library is missing this module raises instead of falling back to anything else.
+
+Arrays may be NumPy arrays (host memory) or CUDA tensors (``torch.Tensor`` on a GPU); both must be
+C-contiguous float64 with N^dim elements per problem, indexed [y, x] (2-D) or [z, y, x] (3-D).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_build", "libsgml.so")
+
+FP64 = 0
+MIXED = 1
+DIRICHLET = 0
+NEUMANN = 1
+NORM_MAX = 0
+NORM_L2 = 1
+STENCIL_CONSISTENT = 0
+STENCIL_LITERAL = 1
+
+OK = 0
+ERR_ARG = -1
+ERR_CUDA = -2
+ERR_NOT_CONVERGED = -3
+ERR_DIVERGED = -4
+ERR_BARRIER_TIMEOUT = -5
+ERR_NONFINITE = -6
+
+_lib = None
+
+_SIGNATURES = {
+    "sgml_create_grid": [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.c_void_p,
+                         ctypes.POINTER(ctypes.c_void_p)],
+    "sgml_set_params": [ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                        ctypes.c_int],
+    "sgml_set_coeffs": [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double],
+    "sgml_set_source": [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p],
+    "sgml_set_bc": [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)],
+    "sgml_run_cycle": [ctypes.c_void_p, ctypes.c_int],
+    "sgml_solve_to_tol": [ctypes.c_void_p, ctypes.c_double, ctypes.POINTER(ctypes.c_int),
+                          ctypes.POINTER(ctypes.c_double)],
+    "sgml_residual_norm": [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double)],
+    "sgml_get_solution": [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p],
+    "sgml_get_stats": [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double),
+                       ctypes.POINTER(ctypes.c_int)],
+    "sgml_get_history": [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.c_int,
+                         ctypes.POINTER(ctypes.c_int)],
+    "sgml_residual": [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p],
+    "sgml_sigma_gradient": [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
+    "sgml_set_launch": [ctypes.c_void_p, ctypes.c_int, ctypes.c_int],
+    "sgml_launch_count": [ctypes.c_void_p, ctypes.POINTER(ctypes.c_longlong)],
+    "sgml_destroy": [ctypes.c_void_p],
+    "sgml_last_error": [],
+}
+
+
+def load(path: str | None = None):
+    """Load libsgml.so (built by paper_1703_07206_gb300.build).  Raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise RuntimeError(f"libsgml.so not found at {path}: build it with paper_1703_07206_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    for name, args in _SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = ctypes.c_char_p if name == "sgml_last_error" else ctypes.c_int
+    _lib = lib
+    return lib
+
+
+class SGMLError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"sgml error {code}: {msg}")
+        self.code = code
+
+
+def _check(code, allow=()):
+    if code != OK and code not in allow:
+        raise SGMLError(code, load().sgml_last_error().decode())
+    return code
+
+
+def _addr(x, count=None):
+    """Address of a float64 C-contiguous host (NumPy) or device (torch) array."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        if x.dtype != np.float64 or not x.flags["C_CONTIGUOUS"]:
+            raise TypeError("arrays must be C-contiguous float64")
+        if count is not None and x.size < count:
+            raise ValueError(f"array has {x.size} elements, {count} needed")
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):
+        import torch
+        if x.dtype != torch.float64 or not x.is_contiguous():
+            raise TypeError("tensors must be contiguous float64")
+        if count is not None and x.numel() < count:
+            raise ValueError(f"tensor has {x.numel()} elements, {count} needed")
+        return x.data_ptr()
+    raise TypeError("expected a NumPy array or a torch tensor")
+
+
+class Grid:
+    """A batch of problems L u = f on the unit square/cube, solved on the GPU by libsgml."""
+
+    def __init__(self, dim, n_levels, precision=MIXED, stream=None):
+        lib = load()
+        if isinstance(n_levels, int):
+            n_levels = [n_levels]
+        self.dim = dim
+        self.n_levels = [int(n) for n in n_levels]
+        self.batch = len(self.n_levels)
+        self.shapes = [((2 ** n + 1),) * dim for n in self.n_levels]
+        self.sizes = [int(np.prod(s)) for s in self.shapes]
+        arr = (ctypes.c_int * self.batch)(*self.n_levels)
+        handle = ctypes.c_void_p()
+        sptr = None
+        if stream is not None:
+            sptr = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+        _check(lib.sgml_create_grid(dim, self.batch, arr, precision, sptr, ctypes.byref(handle)))
+        self._h = handle
+        self.precision = precision
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().sgml_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def _count(self, problem):
+        return sum(self.sizes) if problem < 0 else self.sizes[problem]
+
+    def set_params(self, n_r=2, theta=0.7, schedule=0, stencil=STENCIL_CONSISTENT, dt_mode=0, max_cycles=200):
+        _check(load().sgml_set_params(self._h, n_r, float(theta), schedule, stencil, dt_mode, max_cycles))
+
+    def set_coeffs(self, problem, sigma=None, a=None, a_scalar=0.0):
+        c = self._count(problem)
+        _check(load().sgml_set_coeffs(self._h, problem, _addr(sigma, c), _addr(a, c), float(a_scalar)))
+
+    def set_source(self, problem, f):
+        _check(load().sgml_set_source(self._h, problem, _addr(f, self._count(problem))))
+
+    def set_bc(self, problem, faces, values=None):
+        ft = (ctypes.c_int * 6)(*(list(faces) + [0] * (6 - len(faces))))
+        fv = None
+        if values is not None:
+            fv = (ctypes.c_double * 6)(*([float(v) for v in values] + [0.0] * (6 - len(values))))
+        _check(load().sgml_set_bc(self._h, problem, ft, fv))
+
+    def run_cycle(self, ncycles=1):
+        _check(load().sgml_run_cycle(self._h, ncycles))
+
+    def solve_to_tol(self, rtol, raise_on_failure=False):
+        """Returns (status, cycles per problem, relative residual per problem)."""
+        cyc = (ctypes.c_int * self.batch)()
+        rel = (ctypes.c_double * self.batch)()
+        st = load().sgml_solve_to_tol(self._h, float(rtol), cyc, rel)
+        if raise_on_failure or st in (ERR_ARG, ERR_CUDA, ERR_BARRIER_TIMEOUT):
+            _check(st)
+        return st, np.array(cyc[:]), np.array(rel[:])
+
+    def residual_norm(self, norm=NORM_MAX):
+        out = (ctypes.c_double * self.batch)()
+        _check(load().sgml_residual_norm(self._h, norm, out))
+        return np.array(out[:])
+
+    def get_solution(self, problem=0, out=None):
+        if out is None:
+            out = np.empty(self.shapes[problem])
+        _check(load().sgml_get_solution(self._h, problem, _addr(out, self.sizes[problem])))
+        return out
+
+    def get_stats(self, problem=0):
+        c, r, s = ctypes.c_int(), ctypes.c_double(), ctypes.c_int()
+        _check(load().sgml_get_stats(self._h, problem, ctypes.byref(c), ctypes.byref(r), ctypes.byref(s)))
+        return c.value, r.value, s.value
+
+    def get_history(self, problem=0, cap=1024):
+        buf = (ctypes.c_double * cap)()
+        n = ctypes.c_int()
+        _check(load().sgml_get_history(self._h, problem, buf, cap, ctypes.byref(n)))
+        return np.array(buf[: n.value])
+
+    def residual(self, problem, u, out=None):
+        if out is None:
+            out = np.empty(self.shapes[problem])
+        _check(load().sgml_residual(self._h, problem, _addr(u, self.sizes[problem]), _addr(out, self.sizes[problem])))
+        return out
+
+    def sigma_gradient(self, problem, lam, u, out=None):
+        if out is None:
+            out = np.empty(self.shapes[problem])
+        m = self.sizes[problem]
+        _check(load().sgml_sigma_gradient(self._h, problem, _addr(lam, m), _addr(u, m), _addr(out, m)))
+        return out
+
+    def set_launch(self, threads=256, ctas_per_sm=0):
+        _check(load().sgml_set_launch(self._h, threads, ctas_per_sm))
+
+    def launch_count(self):
+        c = ctypes.c_longlong()
+        _check(load().sgml_launch_count(self._h, ctypes.byref(c)))
+        return c.value
+
+
+def problem_into_grid(grid, b, prob):
+    """Copy one problem dictionary (paper_1703_07206_gb300.inputs format) into problem slot b."""
+    grid.set_bc(b, prob["faces"], prob["values"])
+    grid.set_coeffs(b, prob.get("sigma"), prob.get("a"), prob.get("a_scalar", 0.0))
+    grid.set_source(b, np.ascontiguousarray(prob["f"], dtype=np.float64))

@@ -1,0 +1,168 @@
+"""GPU parity: libsgml (through its C ABI) against the FP64 CPU oracle on the same seeded inputs.
+
+Tolerances:
+  - FP64 form, after the same number of cycles: relative L2 <= 1e-12 (rounding order only: the GPU
+    sums the stencil in a different order and uses the factored Jacobi update).
+  - converged solutions (FP64 and mixed forms): relative L2 <= 1e-10 against the oracle's converged
+    solution (the discrete solution is unique; both are driven to a residual far below that).
+  - mixed form after the same number of cycles: relative L2 <= 2e-5 (the cycle runs in FP32: about
+    1e-7 relative per operation, amplified by the ~30 sweeps and interpolations of a cycle).
+"""
+import numpy as np
+import pytest
+
+from paper_1703_07206_gb300 import inputs, sgml
+from tests.gpu_helpers import gpu_grid, oracle_cycles, oracle_problem, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+CASES = [
+    ("poisson2d_n4", lambda: inputs.poisson_sine_2d(4)),
+    ("poisson2d_n5", lambda: inputs.poisson_sine_2d(5)),
+    ("rand2d_n5", lambda: inputs.random_problem(2, 5, seed=101)),
+    ("rand2d_n5_flux", lambda: inputs.random_problem(2, 5, seed=102, flux=True)),
+    ("rand2d_n3_const", lambda: inputs.random_problem(2, 3, seed=103, hetero=False, helmholtz=False)),
+    ("rand3d_n3", lambda: inputs.random_problem(3, 3, seed=104)),
+    ("rand3d_n4_flux", lambda: inputs.random_problem(3, 4, seed=105, flux=True)),
+    ("poisson3d_n4", lambda: inputs.random_problem(3, 4, seed=106, hetero=False, helmholtz=False, mixed_bc=False)),
+    ("single_node_2d", lambda: inputs.random_problem(2, 1, seed=107)),
+    ("single_node_3d", lambda: inputs.random_problem(3, 1, seed=108, mixed_bc=False)),
+]
+
+
+def with_dirichlet_values(d):
+    vals = list(d["values"])
+    for k in range(2 * d["dim"]):
+        if d["faces"][k] == inputs.DIRICHLET:
+            vals[k] = 0.25 * (k + 1)
+    d = dict(d)
+    d["values"] = vals
+    return d
+
+
+@pytest.mark.parametrize("name,make", CASES, ids=[c[0] for c in CASES])
+@pytest.mark.parametrize("k", [1, 3])
+def test_fp64_cycles_match_oracle(name, make, k):
+    d = with_dirichlet_values(make())
+    p = oracle_problem(d)
+    u_ref = oracle_cycles(p, d["f"], k)
+    g = gpu_grid([d], sgml.FP64)
+    g.run_cycle(k)
+    u = g.get_solution(0)
+    assert rel_l2(u, u_ref) <= 1e-12, rel_l2(u, u_ref)
+
+
+@pytest.mark.parametrize("name,make", CASES[:6], ids=[c[0] for c in CASES[:6]])
+def test_mixed_cycles_close_to_oracle(name, make):
+    d = with_dirichlet_values(make())
+    p = oracle_problem(d)
+    u_ref = oracle_cycles(p, d["f"], 2)
+    g = gpu_grid([d], sgml.MIXED)
+    g.run_cycle(2)
+    assert rel_l2(g.get_solution(0), u_ref) <= 2e-5
+
+
+@pytest.mark.parametrize("precision", [sgml.FP64, sgml.MIXED])
+def test_poisson_129_converged(precision):
+    """129 x 129 Poisson, sin(pi x) sin(pi y), Dirichlet 0, relative residual 1e-12."""
+    d = inputs.poisson_sine_2d(7)
+    p = oracle_problem(d)
+    u_ref, c_ref, hist_ref = p.solve(d["f"], tol=1e-12, max_cycles=100)
+    g = gpu_grid([d], precision)
+    st, cyc, rel = g.solve_to_tol(1e-12)
+    assert st == sgml.OK
+    u = g.get_solution(0)
+    assert rel_l2(u, u_ref) <= 1e-10
+    assert rel[0] <= 1e-12
+    if precision == sgml.FP64:
+        assert cyc[0] == c_ref
+        h = g.get_history(0)
+        assert len(h) == len(hist_ref)
+        big = hist_ref > 1e-10  # below that the residual is at its rounding floor
+        assert np.allclose(h[big], hist_ref[big], rtol=1e-6)
+    # the oracle's residual of the GPU solution
+    assert p.rel_residual(u, d["f"]) <= 1.5e-12
+
+
+@pytest.mark.parametrize("precision", [sgml.FP64, sgml.MIXED])
+@pytest.mark.parametrize("name,make", CASES, ids=[c[0] for c in CASES])
+def test_converged_solution_matches_oracle(precision, name, make):
+    d = with_dirichlet_values(make())
+    p = oracle_problem(d)
+    u_ref, c_ref, _ = p.solve(d["f"], tol=1e-12, max_cycles=400)
+    assert c_ref >= 0
+    g = gpu_grid([d], precision, max_cycles=400)
+    st, cyc, rel = g.solve_to_tol(1e-12)
+    assert st == sgml.OK, (st, cyc, rel)
+    assert rel_l2(g.get_solution(0), u_ref) <= 1e-10
+
+
+def test_batch_of_uneven_problems_matches_individual_oracle_solves():
+    probs = [inputs.random_problem(2, n, seed=200 + n, flux=(n % 2 == 0)) for n in (2, 5, 3, 6, 4, 1)]
+    for precision in (sgml.FP64, sgml.MIXED):
+        g = gpu_grid(probs, precision, max_cycles=400)
+        st, cyc, rel = g.solve_to_tol(1e-12)
+        assert st == sgml.OK
+        for b, d in enumerate(probs):
+            u_ref, c_ref, _ = oracle_problem(d).solve(d["f"], tol=1e-12, max_cycles=400)
+            assert rel_l2(g.get_solution(b), u_ref) <= 1e-10, b
+    # FP64 batch after a fixed number of cycles equals the oracle cycle by cycle
+    g = gpu_grid(probs, sgml.FP64)
+    g.run_cycle(2)
+    for b, d in enumerate(probs):
+        u_ref = oracle_cycles(oracle_problem(d), d["f"], 2)
+        assert rel_l2(g.get_solution(b), u_ref) <= 1e-12, b
+
+
+def test_residual_entry_point_matches_oracle():
+    d = inputs.random_problem(3, 4, seed=301, flux=True)
+    p = oracle_problem(d)
+    u = np.random.default_rng(3).standard_normal(p.shape)
+    g = gpu_grid([d], sgml.FP64)
+    r = g.residual(0, u)
+    r_ref = p.residual(u, d["f"])
+    assert np.abs(r - r_ref).max() <= 1e-12 * np.abs(r_ref).max()
+
+
+def test_sigma_gradient_entry_point_matches_oracle():
+    d = inputs.random_problem(3, 4, seed=302, mixed_bc=False, helmholtz=False)
+    p = oracle_problem(d)
+    rng = np.random.default_rng(4)
+    lam, u = rng.standard_normal(p.shape), rng.standard_normal(p.shape)
+    g = gpu_grid([d], sgml.FP64)
+    gr = g.sigma_gradient(0, lam, u)
+    ref = p.sigma_gradient(lam, u)
+    assert np.abs(gr - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+def test_literal_stencil_option_matches_oracle():
+    d = inputs.random_problem(2, 5, seed=303)
+    p = oracle_problem(d, stencil=1)
+    u_ref = oracle_cycles(p, d["f"], 2)
+    g = gpu_grid([d], sgml.FP64, stencil=sgml.STENCIL_LITERAL)
+    g.run_cycle(2)
+    assert rel_l2(g.get_solution(0), u_ref) <= 1e-12
+
+
+def test_n_r_option_matches_oracle():
+    for n_r in (1, 3):
+        d = inputs.random_problem(2, 5, seed=304 + n_r)
+        p = oracle_problem(d, n_r=n_r)
+        u_ref = oracle_cycles(p, d["f"], 2)
+        g = gpu_grid([d], sgml.FP64, n_r=n_r)
+        g.run_cycle(2)
+        assert rel_l2(g.get_solution(0), u_ref) <= 1e-12, n_r
+
+
+def test_run_cycle_continues_and_residual_norm():
+    d = inputs.random_problem(2, 5, seed=310)
+    p = oracle_problem(d)
+    g = gpu_grid([d], sgml.FP64)
+    g.run_cycle(1)
+    g.run_cycle(2)
+    u_ref = oracle_cycles(p, d["f"], 3)
+    u = g.get_solution(0)
+    assert rel_l2(u, u_ref) <= 1e-12
+    rel = g.residual_norm(sgml.NORM_MAX)[0]
+    assert rel == pytest.approx(p.rel_residual(u, d["f"]), rel=1e-9)
+    assert g.get_stats(0)[0] == 3
