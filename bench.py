@@ -1,0 +1,396 @@
+"""Benchmark: solved nodes/s to relative residual 1e-10 on the 3-D heterogeneous dielectric workload.
+
+Workload (one "step" = one full solve from the lifted boundary values, inputs resident in HBM):
+div(eps grad u) = f on the unit cube, 257^3 nodes, eps = 1 with 32 seeded spheres of eps = 80,
+f = 8 seeded unit Gaussian charges (std 2h), u = 0 on the boundary, solved by the SGML cycle until
+||r||_inf / ||f||_inf <= 1e-10.  The mixed form (FP32 cycle, FP64 outer step) gives `value`; the FP64
+form is measured in the same run and reported beside it.  With --gpus N > 1 (torchrun, one rank per
+GPU) every rank solves its own seeded instance: independent replicas, weak scaling.
+
+Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle instead (host cores).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "solved nodes/s to rel. residual 1e-10 (mixed vs FP64 form), % of HBM roofline"
+TOL = 1e-10
+# Algorithmic HBM bytes per fine node per cycle of the schedule (3-D, heterogeneous eps): one DRAM
+# pass per phase, n_r = 2, zig-zag, 8 level-0 sweeps (outer step 24 + 2b + 8, level-0 sweeps
+# 8 (3b + b), coarse levels (18b + 6b) / 7, b = bytes of the cycle precision).
+BYTES_PER_NODE_CYCLE = {"mixed": 182.0, "fp64": 331.0}
+KERNEL_SOURCES = ["paper_1703_07206_gb300/csrc/sgml_kernels.cu", "paper_1703_07206_gb300/csrc/sgml_internal.cuh"]
+
+
+def workload_name(n):
+    N = 2 ** n + 1
+    return (f"3-D heterogeneous dielectric div(eps grad u)=f, {N}^3 nodes, eps 1 / 80 in 32 seeded spheres, "
+            f"8 Gaussian charges (std 2h), Dirichlet 0, solve to rel. residual 1e-10")
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def load_traffic():
+    """DRAM bytes per node per cycle of the cycle kernel from the committed ncu summary, if the
+    kernel sources are unchanged since the capture (else None)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+    except Exception:
+        return {}
+    if d.get("kernel_hash") != kernel_hash():
+        return {}
+    return d.get("bytes_per_node_cycle", {})
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+# ------------------------------------------------------------------------------------------------
+# CPU oracle sample (the cpu_baseline leg and the reference arm)
+# ------------------------------------------------------------------------------------------------
+def oracle_seconds_per_node_cycle(n_sample, cycles):
+    """Time `cycles` outer steps + cycles of the FP64 CPU oracle on the n_sample instance of the
+    workload recipe (single thread).  Returns seconds per node per cycle."""
+    from oracle.oracle import Problem
+    from paper_1703_07206_gb300 import inputs
+    d = inputs.dielectric_spheres_3d(n=n_sample, seed=2000)
+    p = Problem(3, n_sample, sigma=d["sigma"])
+    u = p.lift()
+    t0 = time.perf_counter()
+    for _ in range(cycles):
+        r = p.residual(u, d["f"])
+        u = u + p.cycle(r)
+    dt = time.perf_counter() - t0
+    return dt / (cycles * (2 ** n_sample + 1) ** 3), dt
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    K_cycles = args.ref_cycles
+    n_s = 6
+    M_s = (2 ** n_s + 1) ** 3
+    for _ in range(args.warmup):
+        oracle_seconds_per_node_cycle(n_s, 1)
+    per, total = [], 0.0
+    for _ in range(args.steps):
+        s, dt = oracle_seconds_per_node_cycle(n_s, 1)
+        per.append(s)
+        total += dt
+    s = float(np.median(per))
+    value = 1.0 / (s * K_cycles)
+    line = {"metric": METRIC, "value": value, "unit": "nodes/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": workload_name(args.n), "form": "fp64 CPU oracle"},
+            "cpu_baseline": {"value": value, "unit": "nodes/s", "cores": 1, "kind": "oracle",
+                             "sample": f"each step: one outer step + one cycle of the oracle on the "
+                                       f"{2 ** n_s + 1}^3 instance of the recipe ({M_s} nodes), scaled by "
+                                       f"{K_cycles} cycles to tolerance (the cycle count of the {2 ** args.n + 1}^3 "
+                                       f"FP64 solve)"},
+            "e2e": {"value": value, "unit": "nodes/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------------------------------------
+# GPU arm
+# ------------------------------------------------------------------------------------------------
+def make_grid(d, precision, stream):
+    from paper_1703_07206_gb300 import sgml
+    g = sgml.Grid(3, [d["n"]], precision=precision, stream=stream)
+    g.set_params(max_cycles=args_global.max_cycles)
+    return g
+
+
+def time_solves(torch, g, stream, steps, warmup):
+    """Warm-up, then time `steps` solves with CUDA events on the grid's stream."""
+    from paper_1703_07206_gb300 import sgml
+    for _ in range(warmup):
+        st, cyc, rel = g.solve_to_tol(TOL)
+        if st != sgml.OK:
+            raise RuntimeError(f"solve failed: status {st}, cycles {cyc}, rel {rel}")
+    launches0 = g.launch_count()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    per = []
+    e0.record(stream)
+    for _ in range(steps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        st, cyc, rel = g.solve_to_tol(TOL)
+        b.record(stream)
+        per.append((a, b))
+        if st != sgml.OK:
+            raise RuntimeError(f"solve failed: status {st}")
+    e1.record(stream)
+    torch.cuda.synchronize()
+    total_ms = e0.elapsed_time(e1)
+    kernel_ms = float(np.mean([a.elapsed_time(b) for a, b in per]))
+    return total_ms, kernel_ms, int(cyc[0]), float(rel[0]), g.launch_count() - launches0
+
+
+def run_gpu(args):
+    import torch
+    from paper_1703_07206_gb300 import build, inputs, sgml
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    build.build()
+    stream = torch.cuda.Stream()
+    n = args.n
+    N = 2 ** n + 1
+    M = N ** 3
+    d = inputs.dielectric_spheres_3d(n=n, seed=2000 + rank)
+    f = np.ascontiguousarray(d["f"])
+    sig = np.ascontiguousarray(d["sigma"])
+    f_dev = torch.from_numpy(f).to(f"cuda:{local}")
+    s_dev = torch.from_numpy(sig).to(f"cuda:{local}")
+    results = {}
+    forms = ["mixed", "fp64"] if args.form == "both" else [args.form]
+    grids = {}
+    for form in forms:
+        prec = sgml.MIXED if form == "mixed" else sgml.FP64
+        g = make_grid(d, prec, stream)
+        g.set_coeffs(0, s_dev)
+        g.set_source(0, f_dev)
+        g.set_bc(0, [sgml.DIRICHLET] * 6)
+        grids[form] = g
+    peak, peak_kind = load_peaks()
+    traffic = load_traffic()
+    for form in forms:
+        g = grids[form]
+        steps = args.steps if form == forms[0] else max(1, min(args.steps, args.fp64_steps))
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        with ClockSampler(local) as clk:
+            total_ms, kernel_ms, cycles, rel, launches = time_solves(torch, g, stream, steps, args.warmup)
+        if world > 1:
+            t = torch.tensor([total_ms], device=f"cuda:{local}")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            total_ms = float(t.item())
+        ms = total_ms / steps
+        value = world * M / (ms / 1e3)
+        achieved = BYTES_PER_NODE_CYCLE[form] * M * cycles / (kernel_ms / 1e3) / 1e9
+        tr = traffic.get(form)
+        results[form] = {"value": value, "ms_per_step": ms, "kernel_ms": kernel_ms, "cycles": cycles, "rel": rel,
+                         "launches_per_step": launches / steps, "steps": steps, "clocks": clk.summary(),
+                         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                                      "frac": achieved / peak,
+                                      "traffic": (tr * M * cycles if tr is not None else None),
+                                      "peak_kind": f"{peak_kind} HBM copy bandwidth",
+                                      "algorithmic_bytes_per_node_cycle": BYTES_PER_NODE_CYCLE[form]}}
+    # accuracy: mixed vs FP64 GPU solutions (the FP64 form matches the CPU oracle in the parity tests)
+    acc = None
+    if len(forms) == 2:
+        um = grids["mixed"].get_solution(0)
+        uf = grids["fp64"].get_solution(0)
+        acc = float(np.linalg.norm(um - uf) / np.linalg.norm(uf))
+    # end to end through the C ABI with host buffers (pinned), copies and setup inside
+    e2e = None
+    if not args.no_e2e:
+        form = forms[0]
+        g = grids[form]
+        f_h = torch.from_numpy(f).pin_memory().numpy()
+        s_h = torch.from_numpy(sig).pin_memory().numpy()
+        u_h = torch.empty(M, dtype=torch.float64).pin_memory().numpy().reshape(N, N, N)
+        for _ in range(1):
+            g.set_coeffs(0, s_h)
+            g.set_source(0, f_h)
+            g.solve_to_tol(TOL)
+            g.get_solution(0, u_h)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            g.set_coeffs(0, s_h)
+            g.set_source(0, f_h)
+            st, cyc, rel = g.solve_to_tol(TOL)
+            g.get_solution(0, u_h)
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        if world > 1:
+            t = torch.tensor([el], device=f"cuda:{local}")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            el = float(t.item())
+        e2e = {"value": world * M * args.steps / el, "unit": "nodes/s", "h2d_bytes_per_step": 2 * M * 8,
+               "d2h_bytes_per_step": M * 8}
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        s, dt = oracle_seconds_per_node_cycle(args.cpu_n, 1)
+        K = results.get("fp64", results[forms[0]])["cycles"]
+        cpu = {"value": 1.0 / (s * K), "unit": "nodes/s", "cores": 1, "kind": "oracle",
+               "sample": f"one outer step + one cycle of the FP64 oracle on the {2 ** args.cpu_n + 1}^3 instance "
+                         f"of the recipe ({dt:.1f} s, single thread), scaled by the {K} cycles the FP64 form "
+                         f"needs at {N}^3"}
+    if rank != 0:
+        return
+    main = results[forms[0]]
+    line = {"metric": METRIC, "value": main["value"], "unit": "nodes/s", "n_gpus": world, "steps": main["steps"],
+            "warmup": args.warmup, "ms_per_step": main["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64" if forms[0] == "mixed" else "f64", "data": "synthetic",
+            "config": {"workload": workload_name(n), "form": forms[0], "nodes": M, "cycles": main["cycles"],
+                       "rel_residual": main["rel"], "l2": "inputs larger than L2 (working set > 1 GB per replica)",
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+            "roofline": main["roofline"], "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": int(round(main["launches_per_step"] * main["steps"])), "clocks": main["clocks"]}
+    if "fp64" in results and forms[0] != "fp64":
+        fp = results["fp64"]
+        line["fp64_form"] = {"value": fp["value"], "ms_per_step": fp["ms_per_step"], "cycles": fp["cycles"],
+                             "rel_residual": fp["rel"], "steps": fp["steps"], "roofline": fp["roofline"],
+                             "clocks": fp["clocks"]}
+        line["mixed_over_fp64"] = main["value"] / fp["value"]
+        line["mixed_vs_fp64_rel_l2"] = acc
+    print(json.dumps(line), flush=True)
+    for g in grids.values():
+        g.close()
+
+
+def run_ncu_case(args):
+    """Small case for ncu: one run_cycle launch of `--ncu-cycles` cycles on the workload."""
+    import torch
+    from paper_1703_07206_gb300 import build, inputs, sgml
+    build.build()
+    torch.cuda.set_device(0)
+    d = inputs.dielectric_spheres_3d(n=args.n, seed=2000)
+    prec = sgml.MIXED if args.form in ("mixed", "both") else sgml.FP64
+    g = sgml.Grid(3, [args.n], precision=prec)
+    if args.phased:
+        g.set_launch(0, 1, 1)
+    sgml.problem_into_grid(g, 0, d)
+    g.run_cycle(1)  # warm-up launch (and setup)
+    g.run_cycle(args.ncu_cycles)
+    torch.cuda.synchronize()
+    c, rel, st = g.get_stats(0)
+    print(json.dumps({"ncu_case": True, "n": args.n, "form": args.form, "cycles": c, "rel": rel, "status": st}))
+    g.close()
+
+
+args_global = None
+
+
+def main():
+    global args_global
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--form", default="both", choices=["both", "mixed", "fp64"])
+    ap.add_argument("--n", type=int, default=8, help="N = 2^n + 1 nodes per side (8: 257^3)")
+    ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--max-cycles", type=int, default=400)
+    ap.add_argument("--cpu-n", type=int, default=7)
+    ap.add_argument("--ref-cycles", type=int, default=185, help="cycles to tolerance used to scale the oracle sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--ncu-case", action="store_true")
+    ap.add_argument("--ncu-cycles", type=int, default=2)
+    ap.add_argument("--phased", action="store_true")
+    args = ap.parse_args()
+    args_global = args
+    if args.warmup < 3 and args.impl == "gb300" and not args.ncu_case:
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        run_reference(args)
+    elif args.ncu_case:
+        run_ncu_case(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

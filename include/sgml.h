@@ -132,10 +132,15 @@ int sgml_residual(sgml_grid_t g, int problem, const double* u, double* r);
  * Returns SGML_ERR_ARG for a problem with a Neumann face.  Synchronises. */
 int sgml_sigma_gradient(sgml_grid_t g, int problem, const double* lambda, const double* u, double* grad);
 
-/* Launch shape of the cycle kernel: threads per CTA (multiple of 32, 64..1024) and CTAs per SM
- * (0 = as many as fit).  The cooperative launch needs all CTAs resident; the library clamps to the
- * occupancy limit.  Used by the autotuner. */
-int sgml_set_launch(sgml_grid_t g, int threads, int ctas_per_sm);
+/* Launch shape of the cycle kernel (256 threads per CTA, 32 x 8 column tiles): ctas_per_sm CTAs
+ * per SM (0 = as many as fit; the cooperative launch needs all CTAs resident, so the library clamps
+ * to the occupancy limit); z_waves (>= 1): in 3-D each level's columns are cut along z so that every
+ * CTA gets about z_waves tiles.  mode 0 (default): every run_cycle / solve_to_tol / residual_norm
+ * call is one persistent cooperative launch with grid-wide barriers between phases.  mode 1: the
+ * same device code with one ordinary launch per phase (for profiling single phases; run_cycle then
+ * needs no host synchronisation and can be captured in a CUDA graph).  Used by the autotuner.
+ * Results do not depend on the launch shape. */
+int sgml_set_launch(sgml_grid_t g, int ctas_per_sm, int z_waves, int mode);
 
 /* Number of kernel launches the library issued on this grid since creation (every kernel,
  * setup included). */

@@ -35,9 +35,11 @@ def _stale() -> bool:
     return any(os.path.getmtime(d) > t for d in deps if os.path.exists(d))
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile libsgml.so if any source changed (or force).  Returns the library path."""
-    if not force and not _stale():
+def build(force: bool = False, verbose: bool = False, defines=(), out: str | None = None) -> str:
+    """Compile libsgml.so if any source changed (or force).  Returns the library path.  `defines`
+    (e.g. ["SGML_SWEEP_STAGES=8"]) and `out` build a variant elsewhere (tuning experiments)."""
+    lib = out or LIB
+    if not force and out is None and not _stale():
         return LIB
     os.makedirs(BUILD, exist_ok=True)
     cc = nvcc()
@@ -45,20 +47,21 @@ def build(force: bool = False, verbose: bool = False) -> str:
                     "-I", CSRC]
     if verbose:
         flags += ["-Xptxas", "-v"]
+    flags += [f"-D{d}" for d in defines]
 
     def compile_one(src):
-        obj = os.path.join(BUILD, src.replace(".cu", f".{os.getpid()}.o"))
+        obj = os.path.join(BUILD, src.replace(".cu", f".{os.getpid()}.{abs(hash(lib))}.o"))
         subprocess.run([cc, *flags, "-c", os.path.join(CSRC, src), "-o", obj], check=True)
         return obj
 
     with ThreadPoolExecutor(len(SOURCES)) as ex:
         objs = list(ex.map(compile_one, SOURCES))
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     subprocess.run([cc, *ARCH, "-shared", "-o", tmp, *objs], check=True)
-    os.replace(tmp, LIB)
+    os.replace(tmp, lib)
     for o in objs:
         os.remove(o)
-    return LIB
+    return lib
 
 
 if __name__ == "__main__":

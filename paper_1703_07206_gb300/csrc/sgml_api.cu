@@ -46,10 +46,13 @@ struct sgml_grid {
   GridSync* d_sync = nullptr;
   Phase* d_phases = nullptr;
   int nphases = 0;
-  long long* d_tiles = nullptr;
+  long long* d_rows = nullptr;
+  TileTask* d_tasks = nullptr;
+  int* d_task_off = nullptr;
   double* d_hist = nullptr;
   int hist_cap = 0;
-  double *U = nullptr, *F = nullptr, *SIG64 = nullptr, *A64 = nullptr;
+  double *U = nullptr, *F = nullptr, *SIG64 = nullptr, *A64 = nullptr, *RES64 = nullptr;
+  void* A0 = nullptr;
   void *E = nullptr, *E2 = nullptr, *B = nullptr, *R = nullptr, *SIG = nullptr, *Q = nullptr;
   long long full_total = 0, lvl_total = 0;
   // parameters
@@ -57,7 +60,8 @@ struct sgml_grid {
   double theta = 0.7;
   int stencil = SGML_STENCIL_CONSISTENT;
   int max_cycles = 200;
-  int threads = 256, ctas_per_sm = 0, blocks = 0;
+  int threads = kThreads, ctas_per_sm = 0, blocks = 0, z_waves = 1;
+  int mode = 0;  // 0: one persistent cooperative launch per call, 1: one launch per phase
   bool dirty_coeffs = true, dirty_desc = true, dirty_phases = true, dirty_tiles = true, fresh = true;
   long long launches = 0;
   ProblemState* h_state = nullptr;  // pinned
@@ -144,20 +148,54 @@ static int upload_phases(sgml_grid* g) {
   return SGML_OK;
 }
 
+// Work tables: column tiles of every level (3-D: z cut into chunks so that each level has about
+// z_waves tiles per CTA) and the prefix of node rows per level.
 static int upload_tiles(sgml_grid* g) {
   int bps = 0;
-  if (cycle_kernel_occupancy(g->mixed, g->dim, g->threads, &bps) != 0 || bps < 1)
+  if (cycle_kernel_occupancy(g->mixed, g->dim, kThreads, &bps) != 0 || bps < 1)
     return fail(SGML_ERR_CUDA, "occupancy query failed for the cycle kernel");
   if (g->ctas_per_sm > 0) bps = std::min(bps, g->ctas_per_sm);
   g->blocks = g->sms * bps;
-  std::vector<long long> tp((size_t)kMaxLevels * (g->batch + 1), 0);
-  for (int l = 0; l < kMaxLevels; ++l)
+  std::vector<long long> rp((size_t)kMaxLevels * (g->batch + 1), 0);
+  std::vector<TileTask> tasks;
+  std::vector<int> toff(kMaxLevels + 1, 0);
+  for (int l = 0; l < kMaxLevels; ++l) {
+    toff[l] = (int)tasks.size();
+    long long nxy = 0;
     for (int b = 0; b < g->batch; ++b) {
-      long long t = (l <= g->P[b].n - 1) ? (nodes(g->dim, g->P[b].n, l) + g->threads - 1) / g->threads : 0;
-      tp[(size_t)l * (g->batch + 1) + b + 1] = tp[(size_t)l * (g->batch + 1) + b] + t;
+      const int n = g->P[b].n;
+      const long long N = side(n, std::min(l, n - 1));
+      const long long rows = (l <= n - 1) ? (g->dim == 3 ? N * N : N) : 0;
+      rp[(size_t)l * (g->batch + 1) + b + 1] = rp[(size_t)l * (g->batch + 1) + b] + rows;
+      if (l <= n - 1) nxy += ((N + kTX - 1) / kTX) * ((N + kTY - 1) / kTY);
     }
-  if (!g->d_tiles) SGML_CUDA(cudaMalloc(&g->d_tiles, sizeof(long long) * tp.size()));
-  SGML_CUDA(cudaMemcpyAsync(g->d_tiles, tp.data(), sizeof(long long) * tp.size(), cudaMemcpyHostToDevice, g->stream));
+    long long nzc = 1;
+    if (g->dim == 3 && nxy > 0) nzc = std::max(1LL, (long long)std::llround((double)g->blocks * g->z_waves / nxy));
+    for (int b = 0; b < g->batch; ++b) {
+      const int n = g->P[b].n;
+      if (l > n - 1) continue;
+      const int N = (int)side(n, l);
+      const int chunk = g->dim == 3 ? (int)std::max<long long>(2, (N + std::min<long long>(nzc, N) - 1) / std::min<long long>(nzc, N)) : 1;
+      const int zmax = g->dim == 3 ? N : 1;
+      for (int z0 = 0; z0 < zmax; z0 += chunk)
+        for (int y0 = 0; y0 < N; y0 += kTY)
+          for (int x0 = 0; x0 < N; x0 += kTX)
+            tasks.push_back(TileTask{b, (short)x0, (short)y0, (short)z0, (short)std::min(chunk, zmax - z0)});
+    }
+  }
+  toff[kMaxLevels] = (int)tasks.size();
+  if (g->d_rows) SGML_CUDA(cudaFree(g->d_rows));
+  if (g->d_tasks) SGML_CUDA(cudaFree(g->d_tasks));
+  if (g->d_task_off) SGML_CUDA(cudaFree(g->d_task_off));
+  g->d_rows = nullptr;
+  g->d_tasks = nullptr;
+  g->d_task_off = nullptr;
+  SGML_CUDA(cudaMalloc(&g->d_rows, sizeof(long long) * rp.size()));
+  SGML_CUDA(cudaMalloc(&g->d_tasks, sizeof(TileTask) * std::max<size_t>(tasks.size(), 1)));
+  SGML_CUDA(cudaMalloc(&g->d_task_off, sizeof(int) * toff.size()));
+  SGML_CUDA(cudaMemcpyAsync(g->d_rows, rp.data(), sizeof(long long) * rp.size(), cudaMemcpyHostToDevice, g->stream));
+  SGML_CUDA(cudaMemcpyAsync(g->d_tasks, tasks.data(), sizeof(TileTask) * tasks.size(), cudaMemcpyHostToDevice, g->stream));
+  SGML_CUDA(cudaMemcpyAsync(g->d_task_off, toff.data(), sizeof(int) * toff.size(), cudaMemcpyHostToDevice, g->stream));
   SGML_CUDA(cudaStreamSynchronize(g->stream));
   g->dirty_tiles = false;
   return SGML_OK;
@@ -174,6 +212,8 @@ static int ensure_hetero_pools(sgml_grid* g, bool need_a) {
   if (need_a && !g->A64) {
     SGML_CUDA(cudaMalloc(&g->A64, sizeof(double) * g->full_total));
     SGML_CUDA(cudaMemsetAsync(g->A64, 0, sizeof(double) * g->full_total, g->stream));
+    SGML_CUDA(cudaMalloc(&g->A0, (size_t)g->elem * g->lvl_total));
+    SGML_CUDA(cudaMemsetAsync(g->A0, 0, (size_t)g->elem * g->lvl_total, g->stream));
   }
   return SGML_OK;
 }
@@ -213,7 +253,7 @@ static int build_coeffs(sgml_grid* g) {
     }
     for (int l = 0; l <= P.n - 1; ++l) {
       SGML_CUDA(launch_setup_level(g->mixed, g->dim, P, l, sig[l], av[l], kap, w_edge(), w_corner(), tg, g->SIG, g->Q,
-                                   g->stream));
+                                   (l == 0 && P.a_per_node) ? g->A0 : nullptr, g->stream));
       g->launches++;
     }
   }
@@ -271,8 +311,9 @@ static int launch(sgml_grid* g, int max_cycles, double tol) {
   p.accum = g->d_accum;
   p.phases = g->d_phases;
   p.nphases = g->nphases;
-  p.tile_prefix = g->d_tiles;
-  p.tile = g->threads;
+  p.tasks = g->d_tasks;
+  p.task_off = g->d_task_off;
+  p.row_prefix = g->d_rows;
   p.fresh = fresh ? 1 : 0;
   p.max_cycles = max_cycles;
   p.tol = tol;
@@ -289,14 +330,37 @@ static int launch(sgml_grid* g, int max_cycles, double tol) {
   p.F = g->F;
   p.SIG64 = g->SIG64;
   p.A64 = g->A64;
+  p.RES64 = g->RES64;
+  p.A0 = g->A0;
   p.E = g->E;
   p.E2 = g->E2;
   p.B = g->B;
   p.R = g->R;
   p.SIG = g->SIG;
   p.Q = g->Q;
-  SGML_CUDA(launch_cycle_kernel(p, g->mixed, g->dim, g->blocks, g->threads, g->stream));
-  g->launches++;
+  if (g->mode == 0) {
+    SGML_CUDA(launch_cycle_kernel(p, g->mixed, g->dim, g->blocks, g->threads, g->stream));
+    g->launches++;
+  } else {
+    // one launch per phase: the same device code, kernel boundaries instead of grid barriers
+    auto one = [&](int which, int c) -> cudaError_t {
+      g->launches++;
+      return launch_phase_kernel(p, g->mixed, g->dim, g->blocks, g->threads, which, c, g->stream);
+    };
+    if (fresh) SGML_CUDA(one(-3, 0));
+    for (int c = 0;; ++c) {
+      SGML_CUDA(one(-2, c));
+      SGML_CUDA(one(-1, c));
+      if (c >= max_cycles) break;
+      if (tol >= 0.0) {
+        GridSync s;
+        SGML_CUDA(cudaMemcpyAsync(&s, g->d_sync, sizeof(GridSync), cudaMemcpyDeviceToHost, g->stream));
+        SGML_CUDA(cudaStreamSynchronize(g->stream));
+        if (!s.active[c & 1]) break;
+      }
+      for (int q = 0; q < g->nphases; ++q) SGML_CUDA(one(q, c));
+    }
+  }
   g->fresh = false;
   return SGML_OK;
 }
@@ -363,6 +427,9 @@ int sgml_create_grid(int dim, int batch, const int* n_levels, int precision, voi
     return cleanup(SGML_ERR_CUDA, cudaGetErrorString(e));
   ALLOC(g->U, sizeof(double) * full);
   ALLOC(g->F, sizeof(double) * full);
+  if (g->mixed) {
+    ALLOC(g->RES64, sizeof(double) * full);
+  }
   ALLOC(g->E, (size_t)g->elem * lvl);
   ALLOC(g->E2, (size_t)g->elem * lvl);
   ALLOC(g->B, (size_t)g->elem * lvl);
@@ -572,12 +639,13 @@ int sgml_sigma_gradient(sgml_grid_t g, int problem, const double* lambda, const 
   return SGML_OK;
 }
 
-int sgml_set_launch(sgml_grid_t g, int threads, int ctas_per_sm) {
+int sgml_set_launch(sgml_grid_t g, int ctas_per_sm, int z_waves, int mode) {
   if (!valid(g)) return fail(SGML_ERR_ARG, "invalid grid");
-  if (threads < 64 || threads > 1024 || threads % 32 != 0 || ctas_per_sm < 0)
-    return fail(SGML_ERR_ARG, "threads must be a multiple of 32 in 64..1024, ctas_per_sm >= 0");
-  g->threads = threads;
+  if (ctas_per_sm < 0 || z_waves < 1 || z_waves > 64 || (mode != 0 && mode != 1))
+    return fail(SGML_ERR_ARG, "ctas_per_sm >= 0, z_waves in 1..64, mode 0 or 1");
   g->ctas_per_sm = ctas_per_sm;
+  g->z_waves = z_waves;
+  g->mode = mode;
   g->dirty_tiles = true;
   return SGML_OK;
 }
@@ -591,8 +659,9 @@ int sgml_launch_count(sgml_grid_t g, long long* count) {
 int sgml_destroy(sgml_grid_t g) {
   if (!g) return SGML_OK;
   cudaStreamSynchronize(g->stream);
-  void* ptrs[] = {g->U, g->F, g->SIG64, g->A64, g->E, g->E2, g->B, g->R, g->SIG, g->Q,
-                  g->d_probs, g->d_state, g->d_accum, g->d_sync, g->d_phases, g->d_tiles, g->d_hist};
+  void* ptrs[] = {g->U, g->F, g->SIG64, g->A64, g->RES64, g->A0, g->E, g->E2, g->B, g->R, g->SIG, g->Q,
+                  g->d_probs, g->d_state, g->d_accum, g->d_sync, g->d_phases, g->d_rows, g->d_tasks,
+                  g->d_task_off, g->d_hist};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (g->h_state) cudaFreeHost(g->h_state);

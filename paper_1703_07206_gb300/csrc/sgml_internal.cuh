@@ -3,12 +3,13 @@
 //
 // Memory layout in HBM (one allocation per pool, all problems of the batch back to back):
 //   FP64 full-grid pools, N^d doubles per problem at ProblemDesc::off_full:
-//     U (solution), F (source), SIG64 (sigma), A64 (per-node a)
+//     U (solution), F (source), SIG64 (sigma), A64 (per-node a), RES64 (accumulated residual, mixed)
 //   cycle-precision level pools (T = double or float), per problem levels 0..n-1 back to back at
 //   ProblemDesc::off_lvl[l], level l holding (2^(n-l)+1)^d nodes (the level-l subset of the single
 //   grid stored compactly, row-major [z][y][x]):
 //     E, E2 (Jacobi ping-pong of the correction e), B (value of E when last injected from below),
-//     R (restricted residual pyramid), SIG (restricted sigma), Q (local step times kappa/(2H^2)).
+//     R (restricted residual pyramid), SIG (restricted sigma), Q (local step times kappa/(2H^2)),
+//     A0 (per-node a, level 0 only).
 // Every level array starts on a 256-byte boundary.
 #pragma once
 #include <cuda_runtime.h>
@@ -60,6 +61,9 @@ struct ProblemState {
   int status;             // sgml_status of the problem
   int grow;               // consecutive cycles with a growing residual
   int hist_len;           // entries of the history row written by the last launch
+  double anchor_rel;      // relative residual at the last FP64 anchor (mixed form)
+  int anchor_next;        // the next residual is an FP64 anchor (else the FP32-stencil recurrence)
+  int last_anchor;        // cycle index of the last anchor in this launch
 };
 
 // Norm accumulators and the per-launch stop flag (zeroed by the host before every launch).
@@ -80,6 +84,14 @@ struct GridSync {
   int pad[3];
 };
 
+// Work unit of the tiled phases.  3-D: the kTX x kTY columns starting at (x0, y0) of one level of
+// problem b, planes z0 .. z0 + nz - 1 (the CTA marches in z).  2-D: the kTX x kTY nodes at (x0, y0).
+constexpr int kTX = 32, kTY = 8, kThreads = kTX * kTY;
+struct TileTask {
+  int b;
+  short x0, y0, z0, nz;
+};
+
 struct KernelParams {
   int dim, batch, n_max;
   int mixed;
@@ -88,8 +100,9 @@ struct KernelParams {
   Accum* accum;
   const Phase* phases;
   int nphases;
-  const long long* tile_prefix;  // [kMaxLevels][batch + 1] cumulative tile counts per level
-  int tile;                      // nodes per tile (= blockDim.x)
+  const TileTask* tasks;         // column tiles of every level, level l at tasks[task_off[l] ..]
+  const int* task_off;           // [kMaxLevels + 1]
+  const long long* row_prefix;   // [kMaxLevels][batch + 1] cumulative node-row counts per level
   int fresh;                     // lift u and measure f first
   int max_cycles;
   double tol;
@@ -102,16 +115,20 @@ struct KernelParams {
   double* hist;
   int hist_cap;
   double *U, *F, *SIG64, *A64;
+  double* RES64;   // accumulated FP64 residual of the mixed form (full grid)
   void *E, *E2, *B, *R, *SIG, *Q;
+  void* A0;        // per-node a at level 0 in cycle precision (recurrence operand)
 };
 
 // Host-side launchers (sgml_kernels.cu)
 cudaError_t launch_cycle_kernel(const KernelParams& p, int precision_mixed, int dim, int blocks,
                                 int threads, cudaStream_t s);
+cudaError_t launch_phase_kernel(const KernelParams& p, int precision_mixed, int dim, int blocks, int threads,
+                                int which, int c, cudaStream_t s);
 int cycle_kernel_occupancy(int precision_mixed, int dim, int threads, int* blocks_per_sm);
 cudaError_t launch_setup_level(int mixed, int dim, const ProblemDesc& P, int level, const double* sig_l,
                                const double* a_l, double kappa, double w_edge, double w_corner,
-                               double theta_gain, void* SIG_T, void* Q_T, cudaStream_t s);
+                               double theta_gain, void* SIG_T, void* Q_T, void* A_T, cudaStream_t s);
 cudaError_t launch_restrict64(int dim, const double* src, int Ns, double* dst, int Nt, cudaStream_t s);
 cudaError_t launch_residual64(int dim, const ProblemDesc& P, const double* U, const double* F,
                               const double* SIG64, const double* A64, double kappa, double w_edge,

@@ -135,6 +135,80 @@ __device__ bool grid_sync(GridSync* gs, unsigned long long timeout_ns) {
   return s_ok != 0;
 }
 
+// ---------------------------------------------------------------------------------------------
+// Work distribution.  Tiled phases take column tiles (TileTask) of one level, CTA c handling tasks
+// c, c + G, ...; row phases take node rows (fixed y, z) of one level, one row per warp.
+// ---------------------------------------------------------------------------------------------
+template <class Body>
+__device__ __forceinline__ void for_tasks(const KernelParams& p, int l, Body&& body) {
+  const int t0 = p.task_off[l], t1 = p.task_off[l + 1];
+  for (int t = t0 + blockIdx.x; t < t1; t += gridDim.x) body(p.tasks[t]);
+}
+
+// Rows of level l of all problems; body(b, N, y, z) runs on one warp (lanes cover x).
+template <int DIM, class Body>
+__device__ __forceinline__ void for_rows(const KernelParams& p, int l, Body&& body) {
+  const long long* rp = p.row_prefix + (long long)l * (p.batch + 1);
+  const long long total = rp[p.batch];
+  const int warps = blockDim.x >> 5;
+  int b = 0;
+  for (long long r = (long long)blockIdx.x * warps + (threadIdx.x >> 5); r < total; r += (long long)gridDim.x * warps) {
+    while (rp[b + 1] <= r) ++b;
+    const ProblemDesc& P = p.probs[b];
+    const int N = level_side(P.n, l);
+    const int local = (int)(r - rp[b]);
+    body(b, P, N, DIM == 3 ? local % N : local, DIM == 3 ? local / N : 0);
+  }
+}
+
+// Number of sweeps of a visit of tooth nu1 for a problem with n levels (Algorithm 3).
+__device__ __forceinline__ int visit_sweeps(int n_r, int n, int tooth, bool final_visit) {
+  const int e = n - tooth;
+  const int cap = e >= 30 ? (1 << 30) : (1 << e);
+  const int k = n_r < cap ? n_r : cap;
+  return final_visit ? 3 * k : k;
+}
+
+// Halo cells of a kTX x kTY tile: (kTX + 2) x (kTY + 2) = 340 cells, at most 2 per thread.
+constexpr int kHX = kTX + 2, kHY = kTY + 2, kHalo = kHX * kHY;
+
+struct HaloCells {
+  int off[2];    // y * N + x of the cell (images applied), -1 if the thread has no such cell
+  double ghost[2];  // Neumann image offset 2 k h g of the cell (x, y directions)
+};
+
+__device__ __forceinline__ HaloCells halo_cells(const ProblemDesc& P, int N, int x0, int y0, bool flux) {
+  HaloCells hc;
+#pragma unroll
+  for (int s = 0; s < 2; ++s) {
+    const int k = threadIdx.x + s * kThreads;
+    hc.off[s] = -1;
+    hc.ghost[s] = 0.0;
+    if (k < kHalo) {
+      int gx = x0 - 1 + k % kHX, gy = y0 - 1 + k / kHX;
+      double g = 0.0;
+      if (gx < 0) { g += (P.face_type[0] == 1) ? 2.0 * P.h * P.face_value[0] : 0.0; }
+      if (gx > N - 1) { g += (P.face_type[1] == 1) ? 2.0 * P.h * P.face_value[1] : 0.0; }
+      if (gy < 0) { g += (P.face_type[2] == 1) ? 2.0 * P.h * P.face_value[2] : 0.0; }
+      if (gy > N - 1) { g += (P.face_type[3] == 1) ? 2.0 * P.h * P.face_value[3] : 0.0; }
+      // cells beyond the image of the far edge (tile overhang past N) are clamped: never used
+      gx = refl(gx, N);
+      gy = refl(gy, N);
+      gx = gx < 0 ? 0 : (gx > N - 1 ? N - 1 : gx);
+      gy = gy < 0 ? 0 : (gy > N - 1 ? N - 1 : gy);
+      hc.off[s] = gy * N + gx;
+      hc.ghost[s] = flux ? g : 0.0;
+    }
+  }
+  return hc;
+}
+
+__device__ __forceinline__ double z_ghost(const ProblemDesc& P, int z, int N) {
+  if (z < 0 && P.face_type[4] == 1) return 2.0 * P.h * P.face_value[4];
+  if (z > N - 1 && P.face_type[5] == 1) return 2.0 * P.h * P.face_value[5];
+  return 0.0;
+}
+
 // Block reduction of (max, sum) and one atomic per block into the accumulators.
 __device__ void block_flush(double mx, double s2, unsigned long long* mx_dst, double* s2_dst) {
   __shared__ double smx[32], ss2[32];
@@ -163,6 +237,844 @@ __device__ void block_flush(double mx, double s2, unsigned long long* mx_dst, do
     }
   }
   __syncthreads();
+}
+
+// ---------------------------------------------------------------------------------------------
+// Asynchronous global -> shared copies (cp.async): the tiled phases keep several planes (3-D) or
+// tiles (2-D) in flight per CTA so that HBM latency is hidden behind the stencil arithmetic.
+// ---------------------------------------------------------------------------------------------
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(s), "l"(gmem), "n"(BYTES) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+template <typename T>
+__device__ __forceinline__ void cp_async_t(T* smem, const T* gmem) {
+  cp_async<sizeof(T)>(smem, gmem);
+}
+
+// Pipeline depths (stages of shared memory per CTA).
+#ifndef SGML_SWEEP_STAGES
+#define SGML_SWEEP_STAGES 6
+#endif
+#ifndef SGML_OUTER_STAGES
+#define SGML_OUTER_STAGES 7
+#endif
+#ifndef SGML_MIN_CTAS
+#define SGML_MIN_CTAS 2
+#endif
+constexpr int kSweepStages = SGML_SWEEP_STAGES;  // loads issued kSweepStages - 2 planes ahead
+constexpr int kOuterStages = SGML_OUTER_STAGES;  // loads issued kOuterStages - 3 planes ahead (three planes resident)
+
+template <typename T>
+struct SweepStage {
+  T e[kHalo];        // correction e on the halo tile
+  T s[kHalo];        // sigma on the halo tile (heterogeneous problems)
+  T r[kThreads];     // restricted residual at the tile's nodes
+  T q[kThreads];     // local step factor at the tile's nodes
+  double u[kThreads];  // FP64 solution (last sweep of a cycle)
+};
+struct OuterStage {  // size of the FP64 residual stage (ResStage<double>)
+  double u[kHalo];
+  double s[kHalo];
+  double f[kThreads];
+  double a[kThreads];
+};
+
+template <typename T>
+constexpr size_t sweep_smem_bytes() {
+  return sizeof(SweepStage<T>) * kSweepStages;
+}
+constexpr size_t outer_smem_bytes() { return sizeof(OuterStage) * kOuterStages; }
+template <typename T>
+constexpr size_t phase_smem_bytes() {
+  return sweep_smem_bytes<T>() > outer_smem_bytes() ? sweep_smem_bytes<T>() : outer_smem_bytes();
+}
+
+// ---------------------------------------------------------------------------------------------
+// Lift: u = Dirichlet values on fixed nodes, 0 on unknowns; ||f|| over the unknowns.
+// ---------------------------------------------------------------------------------------------
+template <typename T, int DIM>
+__device__ void phase_lift(const KernelParams& p) {
+  for_tasks(p, 0, [&](const TileTask& tk) {
+    const ProblemDesc& P = p.probs[tk.b];
+    const int N = level_side(P.n, 0);
+    const int x = tk.x0 + (threadIdx.x % kTX), y = tk.y0 + (threadIdx.x / kTX);
+    double mx = 0.0, s2 = 0.0;
+    if (x < N && y < N) {
+      for (int z = tk.z0; z < tk.z0 + tk.nz; ++z) {
+        const long long g = P.off_full + ((long long)z * N + y) * N + x;
+        if (is_fixed<DIM>(P, N, x, y, z)) {
+          p.U[g] = dirichlet_value<DIM>(P, N, x, y, z);
+        } else {
+          p.U[g] = 0.0;
+          const double f = p.F[g];
+          mx = nan_max(mx, fabs(f));
+          s2 += f * f;
+        }
+      }
+    }
+    block_flush(mx, s2, &p.accum[tk.b].fmax_bits, &p.accum[tk.b].fsum2);
+  });
+}
+
+// Scale of the residual cast of cycle c (mixed form): 1 / (max-norm of the previous residual).
+__device__ __forceinline__ double cast_scale(const KernelParams& p, int b, int c) {
+  if (!p.mixed) return 1.0;
+  double ref = (c == 0 && p.fresh) ? __longlong_as_double((long long)p.accum[b].fmax_bits)
+                                   : p.state[b].rmax_prev;
+  return (ref > 0.0 && ref < 1e300) ? 1.0 / ref : 1.0;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Residual phases.  Anchor (FP64, Sec. 2's recurrence restarted from the accumulated solution):
+// r = f - delta L_0 u.  Recurrence (mixed form, the paper's r_i = r_{i-1} - delta L(e_{i-1})):
+// r = r_prev - delta L_0 e / s with e the previous cycle's correction in FP32 (scale s), the
+// stencil applied in FP32 and the sum accumulated in FP64.  Both evaluate Eq. 5 as
+// sigma-weighted differences (v_o - v_c) grouped in face, edge and corner classes, write the cast
+// level-0 source of the next cycle and the max / L2 norms; Neumann images carry 2 k h g in the
+// anchor (the correction e satisfies homogeneous conditions).  3-D tiles march in z keeping
+// kOuterStages - 3 planes in flight (three resident for the stencil); 2-D tiles are pipelined across
+// the CTA's tasks.
+// ---------------------------------------------------------------------------------------------
+template <typename V>
+struct ResStage {
+  V u[kHalo];         // operand (u or e) on the halo tile
+  V s[kHalo];         // sigma on the halo tile
+  double f[kThreads];  // right-hand side at the tile's nodes (f, or the previous residual)
+  V a[kThreads];      // per-node a at the tile's nodes
+};
+
+template <typename V>
+struct ResSrc {
+  const V* u;          // operand, packed N^d array of the problem
+  const V* s;          // sigma (heterogeneous problems)
+  const double* rhs;   // f or the accumulated residual
+  const V* a;          // per-node a, or null for a_scalar
+  double a_scalar;
+  double opscale;      // r = rhs - opscale * (delta L v)
+  bool images;         // Neumann images carry the prescribed derivative (anchor only)
+};
+
+template <typename V, bool HET, int NP>
+__device__ __forceinline__ void res_sums(V uc, V sc, const ResStage<V>* const* S, int cc, V cls[3]) {
+  cls[0] = cls[1] = cls[2] = (V)0;
+#pragma unroll
+  for (int pz = 0; pz < NP; ++pz) {
+#pragma unroll
+    for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+      for (int dx = -1; dx <= 1; ++dx) {
+        const int dz = NP == 3 ? pz - 1 : 0;
+        if (dx == 0 && dy == 0 && dz == 0) continue;
+        const int nz = (dx != 0) + (dy != 0) + (dz != 0);
+        const int o = cc + dy * kHX + dx;
+        const V du = S[pz]->u[o] - uc;
+        if (HET) cls[nz - 1] = fma(sc + S[pz]->s[o], du, cls[nz - 1]);
+        else cls[nz - 1] += du;
+      }
+  }
+}
+
+// Does the tile need Neumann image offsets (non-zero prescribed derivative on a face it touches)?
+__device__ __forceinline__ bool tile_has_flux(const ProblemDesc& P, int N, int x0, int y0, int dim) {
+  bool f = false;
+  if (P.face_type[0] == 1 && P.face_value[0] != 0.0 && x0 == 0) f = true;
+  if (P.face_type[1] == 1 && P.face_value[1] != 0.0 && x0 + kTX >= N - 1) f = true;
+  if (P.face_type[2] == 1 && P.face_value[2] != 0.0 && y0 == 0) f = true;
+  if (P.face_type[3] == 1 && P.face_value[3] != 0.0 && y0 + kTY >= N - 1) f = true;
+  if (dim == 3 && ((P.face_type[4] == 1 && P.face_value[4] != 0.0) || (P.face_type[5] == 1 && P.face_value[5] != 0.0)))
+    f = true;
+  return f;
+}
+
+// Finish one node: r = rhs - opscale * (c0 * sum + a * v_c); store the cast source (and the FP64
+// residual in the mixed form); fold |r| and r^2 into the thread's norms.
+template <typename T, typename V>
+__device__ __forceinline__ void res_finish(const ResSrc<V>& src, V c0v, V sum, V uc, V a, double rhs, double scale,
+                                           T* R0, double* RES, long long idx, double& mx, double& s2) {
+  double r;
+  if (sizeof(V) == 8) {
+    r = rhs - src.opscale * fma((double)c0v, (double)sum, (double)a * (double)uc);
+    mx = nan_max(mx, fabs(r));
+    s2 = fma(r, r, s2);
+  } else {
+    const V Lv = fma(c0v, sum, a * uc);
+    r = fma(-src.opscale, (double)Lv, rhs);
+    const float rf = (float)r;  // norms of the recurrence in FP32 (they only steer the schedule)
+    mx = nan_max(mx, (double)fabsf(rf));
+    s2 += (double)(rf * rf);
+  }
+  if (RES) RES[idx] = r;
+  R0[idx] = (T)(r * scale);
+}
+
+template <typename T, typename V, bool HET>
+__device__ void residual3(const KernelParams& p, const TileTask& tk, int c, ResStage<V>* st, const ResSrc<V>& src) {
+  constexpr int D = kOuterStages;
+  const ProblemDesc& P = p.probs[tk.b];
+  const int N = level_side(P.n, 0);
+  const int tid = threadIdx.x, tx = tid % kTX, ty = tid / kTX;
+  const int x = tk.x0 + tx, y = tk.y0 + ty;
+  const bool col = x < N && y < N;
+  const double scale = cast_scale(p, tk.b, c);
+  T* R0 = (T*)p.R + P.off_lvl[0];
+  double* RES = p.RES64 ? p.RES64 + P.off_full : nullptr;
+  const HaloCells hc = halo_cells(P, N, tk.x0, tk.y0, true);
+  const bool flux = src.images && tile_has_flux(P, N, tk.x0, tk.y0, 3);
+  const V c0v = (V)(p.kappa / (2.0 * P.h * P.h) * (HET ? 1.0 : 2.0));
+  const V a_s = (V)src.a_scalar;
+  const int cc = (ty + 1) * kHX + tx + 1;
+  const int nplanes = tk.nz + 2;
+  double mx = 0.0, s2 = 0.0;
+  auto issue = [&](int k) {
+    if (k < nplanes) {
+      ResStage<V>& S = st[k % D];
+      const int zz = tk.z0 - 1 + k;
+      const long long base = (long long)refl(zz, N) * N * N;
+#pragma unroll
+      for (int s = 0; s < 2; ++s)
+        if (hc.off[s] >= 0) {
+          cp_async_t(&S.u[tid + s * kThreads], src.u + base + hc.off[s]);
+          if (HET) cp_async_t(&S.s[tid + s * kThreads], src.s + base + hc.off[s]);
+        }
+      if (k >= 1 && k <= tk.nz && col) {
+        const long long idx = base + (long long)y * N + x;
+        cp_async_t(&S.f[tid], src.rhs + idx);
+        if (src.a) cp_async_t(&S.a[tid], src.a + idx);
+      }
+    }
+    cp_async_commit();
+  };
+  for (int k = 0; k < D - 3; ++k) issue(k);
+  for (int k = 0; k < nplanes; ++k) {
+    cp_async_wait<D - 4>();
+    __syncthreads();
+    issue(k + D - 3);
+    if (flux) {  // Neumann images: u_image = u_mirror + 2 k h g, added once to the arrived plane
+      ResStage<V>& S = st[k % D];
+      const double gz = z_ghost(P, tk.z0 - 1 + k, N);
+#pragma unroll
+      for (int s = 0; s < 2; ++s)
+        if (hc.off[s] >= 0) S.u[tid + s * kThreads] += (V)(hc.ghost[s] + gz);
+      __syncthreads();
+    }
+    if (k >= 2 && col) {
+      const int z = tk.z0 + k - 2;
+      if (!is_fixed<3>(P, N, x, y, z)) {
+        const ResStage<V>* Sp[3] = {&st[(k - 2) % D], &st[(k - 1) % D], &st[k % D]};
+        const V uc = Sp[1]->u[cc];
+        const V sc = HET ? Sp[1]->s[cc] : (V)1;
+        V cls[3];
+        res_sums<V, HET, 3>(uc, sc, Sp, cc, cls);
+        const V sum = cls[0] + (V)p.w_edge * cls[1] + (V)p.w_corner * cls[2];
+        const V a = src.a ? Sp[1]->a[tid] : a_s;
+        res_finish<T, V>(src, c0v, sum, uc, a, Sp[1]->f[tid], scale, R0, RES, ((long long)z * N + y) * N + x, mx, s2);
+      }
+    }
+  }
+  cp_async_wait<0>();
+  __syncthreads();
+  block_flush(mx, s2, &p.accum[tk.b].rmax_bits[c & 1], &p.accum[tk.b].rsum2[c & 1]);
+}
+
+// Residual sources of problem b in cycle c: the anchor (FP64 solution) or the recurrence (FP32
+// correction of the previous cycle).
+template <typename T>
+__device__ __forceinline__ bool use_anchor(const KernelParams& p, int b, int c) {
+  return !p.mixed || c == 0 || p.state[b].anchor_next;
+}
+
+__device__ __forceinline__ ResSrc<double> anchor_src(const KernelParams& p, const ProblemDesc& P) {
+  ResSrc<double> s;
+  s.u = p.U + P.off_full;
+  s.s = P.hetero ? p.SIG64 + P.off_full : nullptr;
+  s.rhs = p.F + P.off_full;
+  s.a = P.a_per_node ? p.A64 + P.off_full : nullptr;
+  s.a_scalar = P.a_scalar;
+  s.opscale = 1.0;
+  s.images = true;
+  return s;
+}
+
+template <typename T>
+__device__ __forceinline__ ResSrc<T> recur_src(const KernelParams& p, const ProblemDesc& P, int b, int c) {
+  ResSrc<T> s;
+  const int k_last = visit_sweeps(p.n_r, P.n, 0, true) - 1;  // index of the cycle's last sweep
+  s.u = ((k_last & 1) ? (const T*)p.E : (const T*)p.E2) + P.off_lvl[0];
+  s.s = P.hetero ? (const T*)p.SIG + P.off_lvl[0] : nullptr;
+  s.rhs = p.RES64 + P.off_full;
+  s.a = P.a_per_node ? (const T*)p.A0 + P.off_lvl[0] : nullptr;
+  s.a_scalar = P.a_scalar;
+  s.opscale = 1.0 / p.state[b].scale_used[(c - 1) & 1];
+  s.images = false;
+  return s;
+}
+
+// 2-D: one halo tile per task, the CTA's tasks pipelined kOuterStages - 2 deep; `anchor` selects
+// which problems this pass serves.
+template <typename T, typename V>
+__device__ void residual2(const KernelParams& p, int c, ResStage<V>* st, bool anchor) {
+  constexpr int D = kOuterStages;
+  const int t0 = p.task_off[0], t1 = p.task_off[1];
+  const int tid = threadIdx.x, tx = tid % kTX, ty = tid / kTX;
+  const int cc = (ty + 1) * kHX + tx + 1;
+  const int J = t1 - t0 > (int)blockIdx.x ? (t1 - t0 - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x : 0;
+  auto task = [&](int j) -> const TileTask& { return p.tasks[t0 + blockIdx.x + j * gridDim.x]; };
+  auto mine = [&](int b) { return !p.accum[b].done && use_anchor<T>(p, b, c) == anchor; };
+  auto source = [&](int b) -> ResSrc<V> {
+    if constexpr (sizeof(V) == 8) return anchor_src(p, p.probs[b]);
+    else return recur_src<T>(p, p.probs[b], b, c);
+  };
+  auto issue = [&](int j) {
+    if (j < J) {
+      const TileTask& tk = task(j);
+      if (mine(tk.b)) {
+        const ProblemDesc& P = p.probs[tk.b];
+        const int N = level_side(P.n, 0);
+        const HaloCells hc = halo_cells(P, N, tk.x0, tk.y0, true);
+        const ResSrc<V> src = source(tk.b);
+        ResStage<V>& S = st[j % D];
+#pragma unroll
+        for (int s = 0; s < 2; ++s)
+          if (hc.off[s] >= 0) {
+            cp_async_t(&S.u[tid + s * kThreads], src.u + hc.off[s]);
+            if (src.s) cp_async_t(&S.s[tid + s * kThreads], src.s + hc.off[s]);
+          }
+        const int x = tk.x0 + tx, y = tk.y0 + ty;
+        if (x < N && y < N) {
+          cp_async_t(&S.f[tid], src.rhs + (long long)y * N + x);
+          if (src.a) cp_async_t(&S.a[tid], src.a + (long long)y * N + x);
+        }
+      }
+    }
+    cp_async_commit();
+  };
+  for (int j = 0; j < D - 2; ++j) issue(j);
+  for (int j = 0; j < J; ++j) {
+    cp_async_wait<D - 3>();
+    __syncthreads();
+    issue(j + D - 2);
+    const TileTask& tk = task(j);
+    if (!mine(tk.b)) continue;  // uniform over the CTA
+    const ProblemDesc& P = p.probs[tk.b];
+    const ResSrc<V> src = source(tk.b);
+    ResStage<V>& S = st[j % D];
+    const int N = level_side(P.n, 0);
+    if (src.images && tile_has_flux(P, N, tk.x0, tk.y0, 2)) {
+      const HaloCells hc = halo_cells(P, N, tk.x0, tk.y0, true);
+#pragma unroll
+      for (int s = 0; s < 2; ++s)
+        if (hc.off[s] >= 0) S.u[tid + s * kThreads] += (V)hc.ghost[s];
+      __syncthreads();
+    }
+    const int x = tk.x0 + tx, y = tk.y0 + ty;
+    double mx = 0.0, s2 = 0.0;
+    if (x < N && y < N && !is_fixed<2>(P, N, x, y, 0)) {
+      const ResStage<V>* Sp[1] = {&S};
+      const V uc = S.u[cc];
+      V cls[3];
+      if (src.s) res_sums<V, true, 1>(uc, S.s[cc], Sp, cc, cls);
+      else res_sums<V, false, 1>(uc, (V)1, Sp, cc, cls);
+      const V c0v = (V)(p.kappa / (2.0 * P.h * P.h) * (src.s ? 1.0 : 2.0));
+      const V sum = cls[0] + (V)p.w_edge * cls[1];
+      const V a = src.a ? S.a[tid] : (V)src.a_scalar;
+      res_finish<T, V>(src, c0v, sum, uc, a, S.f[tid], cast_scale(p, tk.b, c), (T*)p.R + P.off_lvl[0],
+                       p.RES64 ? p.RES64 + P.off_full : nullptr, (long long)y * N + x, mx, s2);
+    }
+    block_flush(mx, s2, &p.accum[tk.b].rmax_bits[c & 1], &p.accum[tk.b].rsum2[c & 1]);
+  }
+  cp_async_wait<0>();
+  __syncthreads();
+}
+
+template <typename T, int DIM>
+__device__ void phase_outer(const KernelParams& p, int c, unsigned char* smem) {
+  if (DIM == 2) {
+    residual2<T, double>(p, c, (ResStage<double>*)smem, true);
+    if (p.mixed) residual2<T, T>(p, c, (ResStage<T>*)smem, false);
+    return;
+  }
+  for_tasks(p, 0, [&](const TileTask& tk) {
+    if (p.accum[tk.b].done) return;
+    const ProblemDesc& P = p.probs[tk.b];
+    if (use_anchor<T>(p, tk.b, c)) {
+      const ResSrc<double> src = anchor_src(p, P);
+      if (P.hetero) residual3<T, double, true>(p, tk, c, (ResStage<double>*)smem, src);
+      else residual3<T, double, false>(p, tk, c, (ResStage<double>*)smem, src);
+    } else {
+      const ResSrc<T> src = recur_src<T>(p, P, tk.b, c);
+      if (P.hetero) residual3<T, T, true>(p, tk, c, (ResStage<T>*)smem, src);
+      else residual3<T, T, false>(p, tk, c, (ResStage<T>*)smem, src);
+    }
+  });
+}
+
+// Convergence check after the outer step of cycle c (CTA 0 only): relative residuals, stop
+// decisions, history, next cast scale.  Writes sync->active[c & 1].
+template <typename T, int DIM>
+__device__ void phase_check(const KernelParams& p, int c) {
+  int any = 0;
+  for (int b = threadIdx.x; b < p.batch; b += blockDim.x) {
+    ProblemState& S = p.state[b];
+    Accum& A = p.accum[b];
+    if (A.done) continue;
+    const double rmax = __longlong_as_double((long long)A.rmax_bits[c & 1]);
+    const double rs2 = A.rsum2[c & 1];
+    if (c == 0 && p.fresh) {
+      const double fmax = __longlong_as_double((long long)A.fmax_bits);
+      S.fnorm = fmax > 0.0 ? fmax : rmax;
+      S.fnorm2 = fmax > 0.0 ? sqrt(A.fsum2) : sqrt(rs2);
+      S.rel_prev = 1e300;
+      S.grow = 0;
+    }
+    S.scale_used[c & 1] = cast_scale(p, b, c);
+    const double rel = S.fnorm > 0.0 ? rmax / S.fnorm : 0.0;
+    const double rel2 = S.fnorm2 > 0.0 ? sqrt(rs2) / S.fnorm2 : 0.0;
+    S.rel = rel;
+    S.rel_l2 = rel2;
+    if (c < p.hist_cap) p.hist[(long long)b * p.hist_cap + c] = rel;
+    S.hist_len = c + 1;
+    if (c > 0) S.cycles += 1;
+    const bool anchored = !p.mixed || c == 0 || S.anchor_next;
+    const double rho = S.rel_prev < 1e300 && S.rel_prev > 0.0 ? rel / S.rel_prev : 1.0;
+    S.grow = (rel > S.rel_prev) ? S.grow + 1 : 0;
+    S.rel_prev = rel;
+    S.rmax_prev = rmax;
+    if (anchored) {
+      S.anchor_rel = rel;
+      S.last_anchor = c;
+    }
+    int st = 0, stop = 0;
+    if (!(rel <= 1e300)) {
+      st = -6;  // SGML_ERR_NONFINITE
+      stop = 1;
+    } else if (anchored && rel <= p.tol) {
+      stop = 1;
+    } else if (S.grow >= 3 && rel > 1.0) {
+      st = -4;  // SGML_ERR_DIVERGED
+      stop = 1;
+    } else if (c >= p.max_cycles) {
+      st = p.tol >= 0.0 ? -3 : 0;  // SGML_ERR_NOT_CONVERGED for a solve; fine for run_cycle
+      stop = 1;
+    }
+    // Mixed form: the next residual is the FP64 anchor when the recurrence can no longer be trusted
+    // to ~1 % (the residual fell ten-fold since the last anchor, the cycle contracts fast, the
+    // tolerance may have been reached) and before the last cycle of the launch.
+    S.anchor_next = !p.mixed || rho < 0.2 || rel <= 0.1 * S.anchor_rel || rel <= p.tol || c + 1 >= p.max_cycles ||
+                    c + 1 - S.last_anchor >= 32;
+    S.status = st;
+    A.done = stop;
+    A.rmax_bits[(c + 1) & 1] = 0ull;
+    A.rsum2[(c + 1) & 1] = 0.0;
+    if (!stop) any = 1;
+  }
+  any = __syncthreads_or(any);
+  if (threadIdx.x == 0) p.sync->active[c & 1] = any;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Jacobi sweep of the pseudo-time equation at level l (Eq. 2, explicit Euler, local step):
+//   e_new = e + dtau (delta L_l e - r_l)
+//         = (1 - omega) e_i + q_i (sigma_i CS(e) + CS(sigma e) - r_i / c),  c = kappa / (2 H^2),
+// with CS(v) = sum_o w_o v_{i+o} over the level-l neighbours, q_i = dtau_i c and
+// omega = dtau_i D_i (constant for the Jacobi-scaled step).  3-D: each plane's in-plane face and
+// corner sums are formed once from shared memory and combined across three planes held in
+// registers (faces = F(z) + v(z-1) + v(z+1), edges = C(z) + F(z-1) + F(z+1),
+// corners = C(z-1) + C(z+1)); plane loads run kSweepStages - 2 planes ahead with cp.async.
+// The last sweep of a cycle adds its result, unscaled, to the FP64 solution instead of storing it.
+// ---------------------------------------------------------------------------------------------
+template <typename T>
+struct PlaneSums {
+  T v, F, C;     // e at the own column, in-plane face sum, in-plane corner sum
+  T sv, sF, sC;  // the same for sigma * e
+};
+
+struct SweepCtl {
+  bool active, zero_in, last;
+  int N;
+  long long off;
+};
+
+__device__ __forceinline__ SweepCtl sweep_ctl(const KernelParams& p, const Phase& ph, int b) {
+  SweepCtl s;
+  const ProblemDesc& P = p.probs[b];
+  const bool final_visit = (ph.flags & kFinalVisit) != 0;
+  const int k_b = visit_sweeps(p.n_r, P.n, ph.tooth, final_visit);
+  s.active = !p.accum[b].done && ph.tooth <= P.n - 1 && ph.sweep < k_b;
+  s.zero_in = ph.sweep == 0 && (ph.flags & kFirstOfTooth) && ph.tooth == P.n - 1;
+  s.last = final_visit && ph.sweep == k_b - 1;
+  s.N = level_side(P.n, ph.level);
+  s.off = P.off_lvl[ph.level];
+  return s;
+}
+
+template <typename T, bool HET>
+__device__ __forceinline__ PlaneSums<T> plane_sums(const SweepStage<T>& S, int cc, bool zero) {
+  PlaneSums<T> ps;
+  if (zero) {
+    ps.v = ps.F = ps.C = ps.sv = ps.sF = ps.sC = (T)0;
+    return ps;
+  }
+  const T* E = S.e;
+  ps.v = E[cc];
+  ps.F = (E[cc - 1] + E[cc + 1]) + (E[cc - kHX] + E[cc + kHX]);
+  ps.C = (E[cc - kHX - 1] + E[cc - kHX + 1]) + (E[cc + kHX - 1] + E[cc + kHX + 1]);
+  if (HET) {
+    const T* s = S.s;
+    ps.sv = s[cc] * E[cc];
+    ps.sF = (s[cc - 1] * E[cc - 1] + s[cc + 1] * E[cc + 1]) + (s[cc - kHX] * E[cc - kHX] + s[cc + kHX] * E[cc + kHX]);
+    ps.sC = (s[cc - kHX - 1] * E[cc - kHX - 1] + s[cc - kHX + 1] * E[cc - kHX + 1]) +
+            (s[cc + kHX - 1] * E[cc + kHX - 1] + s[cc + kHX + 1] * E[cc + kHX + 1]);
+  } else {
+    ps.sv = ps.sF = ps.sC = (T)0;
+  }
+  return ps;
+}
+
+// Per-task constants of the update: 1 - omega, 1 / c = 2 H^2 / kappa, and q for a homogeneous problem.
+template <typename T>
+struct SweepConst {
+  T one_m_omega, inv_c, q_const;
+};
+
+template <typename T>
+__device__ __forceinline__ SweepConst<T> sweep_const(const KernelParams& p, const ProblemDesc& P, int l) {
+  SweepConst<T> k;
+  const double H = P.h * (double)(1 << l);
+  k.one_m_omega = (T)(1.0 - p.omega);
+  k.inv_c = (T)(2.0 * H * H / p.kappa);
+  k.q_const = (T)P.q_const[l];
+  return k;
+}
+
+template <typename T, bool HET>
+__device__ __forceinline__ T sweep_update(const SweepConst<T>& k, const SweepStage<T>& S, int cc, T CSe, T CSse,
+                                          T e_c) {
+  const T r_i = S.r[threadIdx.x];
+  if (HET) return k.one_m_omega * e_c + S.q[threadIdx.x] * (S.s[cc] * CSe + CSse - r_i * k.inv_c);
+  return k.one_m_omega * e_c + k.q_const * ((T)2 * CSe - r_i * k.inv_c);
+}
+
+template <typename T, bool HET>
+__device__ void sweep3(const KernelParams& p, const Phase& ph, int c, const TileTask& tk, SweepStage<T>* st) {
+  constexpr int D = kSweepStages;
+  const SweepCtl sc = sweep_ctl(p, ph, tk.b);
+  if (!sc.active) return;
+  const ProblemDesc& P = p.probs[tk.b];
+  const int N = sc.N;
+  const int tid = threadIdx.x, tx = tid % kTX, ty = tid / kTX;
+  const int x = tk.x0 + tx, y = tk.y0 + ty;
+  const bool col = x < N && y < N;
+  const T* src = (ph.sweep & 1) ? (const T*)p.E2 + sc.off : (const T*)p.E + sc.off;
+  T* dst = (ph.sweep & 1) ? (T*)p.E + sc.off : (T*)p.E2 + sc.off;
+  const T* R = (const T*)p.R + sc.off;
+  const T* SG = HET ? (const T*)p.SIG + sc.off : nullptr;
+  const T* Q = HET ? (const T*)p.Q + sc.off : nullptr;
+  const double* Ug = p.U + P.off_full;
+  const HaloCells hc = halo_cells(P, N, tk.x0, tk.y0, false);
+  const T w_e = (T)p.w_edge, w_c = (T)p.w_corner;
+  const int cc = (ty + 1) * kHX + tx + 1;
+  const double inv_scale = sc.last ? 1.0 / p.state[tk.b].scale_used[c & 1] : 0.0;
+  const SweepConst<T> kc = sweep_const<T>(p, P, ph.level);
+  const int nplanes = tk.nz + 2;
+  auto issue = [&](int k) {
+    if (k < nplanes) {
+      SweepStage<T>& S = st[k % D];
+      const int zz = tk.z0 - 1 + k;
+      const long long base = (long long)refl(zz, N) * N * N;
+#pragma unroll
+      for (int s = 0; s < 2; ++s)
+        if (hc.off[s] >= 0) {
+          if (!sc.zero_in) cp_async_t(&S.e[tid + s * kThreads], src + base + hc.off[s]);
+          if (HET) cp_async_t(&S.s[tid + s * kThreads], SG + base + hc.off[s]);
+        }
+      if (k >= 1 && k <= tk.nz && col) {
+        const long long idx = base + (long long)y * N + x;
+        cp_async_t(&S.r[tid], R + idx);
+        if (HET) cp_async_t(&S.q[tid], Q + idx);
+        if (sc.last) cp_async_t(&S.u[tid], Ug + idx);
+      }
+    }
+    cp_async_commit();
+  };
+  for (int k = 0; k < D - 2; ++k) issue(k);
+  PlaneSums<T> m{}, o{};
+  for (int k = 0; k < nplanes; ++k) {
+    cp_async_wait<D - 3>();
+    __syncthreads();
+    issue(k + D - 2);
+    const PlaneSums<T> pz = plane_sums<T, HET>(st[k % D], cc, sc.zero_in);
+    if (k >= 2 && col) {
+      const int z = tk.z0 + k - 2;
+      if (!is_fixed<3>(P, N, x, y, z)) {
+        const T CSe = (o.F + m.v + pz.v) + w_e * (o.C + m.F + pz.F) + w_c * (m.C + pz.C);
+        const T CSse = HET ? (o.sF + m.sv + pz.sv) + w_e * (o.sC + m.sF + pz.sF) + w_c * (m.sC + pz.sC) : (T)0;
+        const SweepStage<T>& S = st[(k - 1) % D];
+        const T e_new = sweep_update<T, HET>(kc, S, cc, CSe, CSse, o.v);
+        const long long idx = ((long long)z * N + y) * N + x;
+        if (sc.last) {
+          p.U[P.off_full + idx] = S.u[tid] + (double)e_new * inv_scale;
+          if (p.mixed) dst[idx] = e_new;
+        } else {
+          dst[idx] = e_new;
+        }
+      }
+    }
+    m = o;
+    o = pz;
+  }
+  cp_async_wait<0>();
+  __syncthreads();
+}
+
+// 2-D: one halo tile per task, the CTA's tasks pipelined kSweepStages - 2 deep.
+template <typename T>
+__device__ void sweep2(const KernelParams& p, const Phase& ph, int c, SweepStage<T>* st) {
+  constexpr int D = kSweepStages;
+  const int l = ph.level;
+  const int t0 = p.task_off[l], t1 = p.task_off[l + 1];
+  const int tid = threadIdx.x, tx = tid % kTX, ty = tid / kTX;
+  const int cc = (ty + 1) * kHX + tx + 1;
+  const int J = t1 - t0 > (int)blockIdx.x ? (t1 - t0 - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x : 0;
+  auto task = [&](int j) -> const TileTask& { return p.tasks[t0 + blockIdx.x + j * gridDim.x]; };
+  auto issue = [&](int j) {
+    if (j < J) {
+      const TileTask& tk = task(j);
+      const SweepCtl sc = sweep_ctl(p, ph, tk.b);
+      if (sc.active) {
+        const ProblemDesc& P = p.probs[tk.b];
+        const int N = sc.N;
+        const HaloCells hc = halo_cells(P, N, tk.x0, tk.y0, false);
+        SweepStage<T>& S = st[j % D];
+        const T* src = (ph.sweep & 1) ? (const T*)p.E2 + sc.off : (const T*)p.E + sc.off;
+#pragma unroll
+        for (int s = 0; s < 2; ++s)
+          if (hc.off[s] >= 0) {
+            if (!sc.zero_in) cp_async_t(&S.e[tid + s * kThreads], src + hc.off[s]);
+            if (P.hetero) cp_async_t(&S.s[tid + s * kThreads], (const T*)p.SIG + sc.off + hc.off[s]);
+          }
+        const int x = tk.x0 + tx, y = tk.y0 + ty;
+        if (x < N && y < N) {
+          const long long idx = (long long)y * N + x;
+          cp_async_t(&S.r[tid], (const T*)p.R + sc.off + idx);
+          if (P.hetero) cp_async_t(&S.q[tid], (const T*)p.Q + sc.off + idx);
+          if (sc.last) cp_async_t(&S.u[tid], p.U + P.off_full + idx);
+        }
+      }
+    }
+    cp_async_commit();
+  };
+  for (int j = 0; j < D - 2; ++j) issue(j);
+  for (int j = 0; j < J; ++j) {
+    cp_async_wait<D - 3>();
+    __syncthreads();
+    issue(j + D - 2);
+    const TileTask& tk = task(j);
+    const SweepCtl sc = sweep_ctl(p, ph, tk.b);
+    if (!sc.active) continue;
+    const ProblemDesc& P = p.probs[tk.b];
+    const int N = sc.N;
+    const int x = tk.x0 + tx, y = tk.y0 + ty;
+    if (x >= N || y >= N || is_fixed<2>(P, N, x, y, 0)) continue;
+    const SweepStage<T>& S = st[j % D];
+    T CSe, CSse = (T)0, e_c;
+    if (P.hetero) {
+      const PlaneSums<T> ps = plane_sums<T, true>(S, cc, sc.zero_in);
+      CSe = ps.F + (T)p.w_edge * ps.C;
+      CSse = ps.sF + (T)p.w_edge * ps.sC;
+      e_c = ps.v;
+    } else {
+      const PlaneSums<T> ps = plane_sums<T, false>(S, cc, sc.zero_in);
+      CSe = ps.F + (T)p.w_edge * ps.C;
+      e_c = ps.v;
+    }
+    const SweepConst<T> kc = sweep_const<T>(p, P, l);
+    const T e_new = P.hetero ? sweep_update<T, true>(kc, S, cc, CSe, CSse, e_c)
+                             : sweep_update<T, false>(kc, S, cc, CSe, CSse, e_c);
+    const long long idx = (long long)y * N + x;
+    T* dst = (ph.sweep & 1) ? (T*)p.E + sc.off : (T*)p.E2 + sc.off;
+    if (sc.last) {
+      p.U[P.off_full + idx] = S.u[tid] + (double)e_new * (1.0 / p.state[tk.b].scale_used[c & 1]);
+      if (p.mixed) dst[idx] = e_new;
+    } else {
+      dst[idx] = e_new;
+    }
+  }
+  cp_async_wait<0>();
+  __syncthreads();
+}
+
+template <typename T, int DIM>
+__device__ void phase_sweep(const KernelParams& p, const Phase& ph, int c, unsigned char* smem) {
+  SweepStage<T>* st = (SweepStage<T>*)smem;
+  if (DIM == 2) {
+    sweep2<T>(p, ph, c, st);
+    return;
+  }
+  for_tasks(p, ph.level, [&](const TileTask& tk) {
+    if (p.probs[tk.b].hetero) sweep3<T, true>(p, ph, c, tk, st);
+    else sweep3<T, false>(p, ph, c, tk, st);
+  });
+}
+
+// ---------------------------------------------------------------------------------------------
+// Row phases: restriction, interpolation to the next finer level, injection to the next coarser.
+// ---------------------------------------------------------------------------------------------
+
+// Restriction pass: level l-1 -> level l (Eqs. 3-4 at distance 2^(l-1) h), even images.
+template <typename T, int DIM>
+__device__ void phase_restrict(const KernelParams& p, int l) {
+  T* R = (T*)p.R;
+  const int lane = threadIdx.x & 31;
+  for_rows<DIM>(p, l, [&](int b, const ProblemDesc& P, int N, int y, int z) {
+    if (l > P.n - 1 || p.accum[b].done) return;
+    const int Ns = level_side(P.n, l - 1);
+    const T* src = R + P.off_lvl[l - 1];
+    T* dst = R + P.off_lvl[l] + ((long long)z * N + y) * N;
+    long long rows[3][3];
+#pragma unroll
+    for (int dz = 0; dz < 3; ++dz)
+#pragma unroll
+      for (int dy = 0; dy < 3; ++dy)
+        rows[dz][dy] = ((long long)(DIM == 3 ? refl(2 * z + dz - 1, Ns) : 0) * Ns + refl(2 * y + dy - 1, Ns)) * Ns;
+    for (int x = lane; x < N; x += 32) {
+      const int xm = refl(2 * x - 1, Ns), x0 = 2 * x, xp = refl(2 * x + 1, Ns);
+      T acc = (T)0;
+#pragma unroll
+      for (int dz = 0; dz < (DIM == 3 ? 3 : 1); ++dz) {
+        T accz = (T)0;
+#pragma unroll
+        for (int dy = 0; dy < 3; ++dy) {
+          const T* row = src + rows[DIM == 3 ? dz : 0][dy];
+          const T line = (T)0.25 * row[xm] + (T)0.5 * row[x0] + (T)0.25 * row[xp];
+          accz += (dy == 1 ? (T)0.5 : (T)0.25) * line;
+        }
+        acc += DIM == 3 ? (dz == 1 ? (T)0.5 : (T)0.25) * accz : accz;
+      }
+      dst[x] = acc;
+    }
+  });
+}
+
+// Buffer holding the result of a visit of tooth `tooth` at a level (E if the visit did an even
+// number of sweeps, E2 otherwise).
+template <typename T>
+__device__ __forceinline__ T* visit_result(const KernelParams& p, const ProblemDesc& P, int tooth, int l) {
+  const int k = visit_sweeps(p.n_r, P.n, tooth, false);
+  return ((k & 1) ? (T*)p.E2 : (T*)p.E) + P.off_lvl[l];
+}
+
+// Moving one level finer: E_l (+)= I(E_{l+1} - B_{l+1}) on every level-l node (hat-function
+// interpolation between consecutive levels, Algorithm 2's I_lambda).
+template <typename T, int DIM>
+__device__ void phase_prolong(const KernelParams& p, const Phase& ph) {
+  const int l = ph.level;
+  const bool init = (ph.flags & kInit) != 0;
+  const int lane = threadIdx.x & 31;
+  for_rows<DIM>(p, l, [&](int b, const ProblemDesc& P, int N, int y, int z) {
+    if (ph.tooth > P.n - 1 || p.accum[b].done) return;
+    const int Nc = level_side(P.n, l + 1);
+    const T* src = visit_result<T>(p, P, ph.tooth, l + 1);
+    const T* Bc = (const T*)p.B + P.off_lvl[l + 1];
+    const T* base = init ? nullptr : visit_result<T>(p, P, ph.prev_tooth, l);
+    T* El = (T*)p.E + P.off_lvl[l];
+    const long long row = ((long long)z * N + y) * N;
+    // coarse rows contributing to this fine row, with weights
+    const int y0 = y >> 1, z0 = z >> 1;
+    const int ny = (y & 1) ? 2 : 1, nz = (DIM == 3 && (z & 1)) ? 2 : 1;
+    const T wyz = (ny == 2 ? (T)0.5 : (T)1) * (nz == 2 ? (T)0.5 : (T)1);
+    for (int x = lane; x < N; x += 32) {
+      const int x0 = x >> 1;
+      const bool odd = x & 1;
+      T val = (T)0;
+      for (int cz = 0; cz < nz; ++cz)
+        for (int cy = 0; cy < ny; ++cy) {
+          const long long cr = ((long long)(DIM == 3 ? z0 + cz : 0) * Nc + (y0 + cy)) * Nc;
+          T d = src[cr + x0] - (init ? (T)0 : Bc[cr + x0]);
+          if (odd) d = (T)0.5 * (d + (src[cr + x0 + 1] - (init ? (T)0 : Bc[cr + x0 + 1])));
+          val += d;
+        }
+      val *= wyz;
+      El[row + x] = (init ? (T)0 : base[row + x]) + val;
+    }
+  });
+}
+
+// Moving one level coarser: E_l = B_l = (result at level l-1) on the level-l subset.
+template <typename T, int DIM>
+__device__ void phase_inject(const KernelParams& p, const Phase& ph) {
+  const int l = ph.level;
+  const int lane = threadIdx.x & 31;
+  for_rows<DIM>(p, l, [&](int b, const ProblemDesc& P, int N, int y, int z) {
+    if (ph.tooth > P.n - 1 || l > P.n - 1 || p.accum[b].done) return;
+    const int Nf = level_side(P.n, l - 1);
+    const T* src = visit_result<T>(p, P, ph.tooth, l - 1) + ((long long)(2 * z) * Nf + 2 * y) * Nf;
+    const long long row = ((long long)z * N + y) * N;
+    T* E = (T*)p.E + P.off_lvl[l] + row;
+    T* B = (T*)p.B + P.off_lvl[l] + row;
+    for (int x = lane; x < N; x += 32) {
+      const T v = src[2 * x];
+      E[x] = v;
+      B[x] = v;
+    }
+  });
+}
+
+// ---------------------------------------------------------------------------------------------
+// The persistent cycle kernel
+// ---------------------------------------------------------------------------------------------
+template <typename T, int DIM>
+__device__ __forceinline__ void run_phase(const KernelParams& p, const Phase& ph, int c, unsigned char* sm) {
+  switch (ph.op) {
+    case OP_RESTRICT: phase_restrict<T, DIM>(p, ph.level); break;
+    case OP_SWEEP: phase_sweep<T, DIM>(p, ph, c, sm); break;
+    case OP_PROLONG: phase_prolong<T, DIM>(p, ph); break;
+    default: phase_inject<T, DIM>(p, ph); break;
+  }
+}
+
+template <typename T, int DIM>
+__global__ void __launch_bounds__(kThreads, SGML_MIN_CTAS) cycle_kernel(const KernelParams p) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  if (p.fresh) {
+    phase_lift<T, DIM>(p);
+    if (!grid_sync(p.sync, p.timeout_ns)) return;
+  }
+  for (int c = 0;; ++c) {
+    phase_outer<T, DIM>(p, c, sm);
+    if (!grid_sync(p.sync, p.timeout_ns)) return;
+    if (blockIdx.x == 0) phase_check<T, DIM>(p, c);
+    if (!grid_sync(p.sync, p.timeout_ns)) return;
+    if (!ld_volatile(&p.sync->active[c & 1])) break;
+    for (int q = 0; q < p.nphases; ++q) {
+      const Phase ph = p.phases[q];
+      run_phase<T, DIM>(p, ph, c, sm);
+      if (!grid_sync(p.sync, p.timeout_ns)) return;
+    }
+  }
+}
+
+// One phase per launch (profiling / graph-capture mode).  which: -3 lift, -2 outer step,
+// -1 convergence check (launch with one CTA), >= 0 index into the phase table.
+template <typename T, int DIM>
+__global__ void __launch_bounds__(kThreads, SGML_MIN_CTAS) phase_kernel(const KernelParams p, int which, int c) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  if (which == -3) {
+    phase_lift<T, DIM>(p);
+  } else if (which == -2) {
+    phase_outer<T, DIM>(p, c, sm);
+  } else if (which == -1) {
+    if (blockIdx.x == 0) phase_check<T, DIM>(p, c);
+  } else {
+    const Phase ph = p.phases[which];
+    run_phase<T, DIM>(p, ph, c, sm);
+  }
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -210,356 +1122,9 @@ __device__ __forceinline__ double residual_at(const ProblemDesc& P, int N, int i
   return F[c] - Lu;
 }
 
-// ---------------------------------------------------------------------------------------------
-// Tile iteration: level-l nodes of all problems are cut into tiles of `tile` nodes (tiles never
-// straddle problems); CTA c takes tiles c, c + G, ...  Uniform across the CTA.
-// ---------------------------------------------------------------------------------------------
-template <class Body>
-__device__ __forceinline__ void for_tiles(const KernelParams& p, int l, Body&& body) {
-  const long long* tp = p.tile_prefix + (long long)l * (p.batch + 1);
-  const long long total = tp[p.batch];
-  int b = 0;
-  for (long long t = blockIdx.x; t < total; t += gridDim.x) {
-    while (tp[b + 1] <= t) ++b;
-    body(b, (t - tp[b]) * p.tile + threadIdx.x);
-  }
-}
-
-// ---------------------------------------------------------------------------------------------
-// Phases
-// ---------------------------------------------------------------------------------------------
-
-// Lift the Dirichlet values into u (0 on unknowns) and accumulate ||f|| over the unknowns.
 template <typename T, int DIM>
-__device__ void phase_lift(const KernelParams& p) {
-  int cur = -1;
-  double mx = 0.0, s2 = 0.0;
-  for_tiles(p, 0, [&](int b, long long local) {
-    if (b != cur) {
-      if (cur >= 0) block_flush(mx, s2, &p.accum[cur].fmax_bits, &p.accum[cur].fsum2);
-      cur = b;
-      mx = s2 = 0.0;
-    }
-    const ProblemDesc& P = p.probs[b];
-    const int N = level_side(P.n, 0);
-    if (local >= level_nodes<DIM>(N)) return;
-    int i, j, k;
-    decode<DIM>(local, N, i, j, k);
-    const long long g = P.off_full + local;
-    if (is_fixed<DIM>(P, N, i, j, k)) {
-      p.U[g] = dirichlet_value<DIM>(P, N, i, j, k);
-    } else {
-      p.U[g] = 0.0;
-      const double f = p.F[g];
-      mx = nan_max(mx, fabs(f));
-      s2 += f * f;
-    }
-  });
-  if (cur >= 0) block_flush(mx, s2, &p.accum[cur].fmax_bits, &p.accum[cur].fsum2);
-}
-
-// Scale of the residual cast of cycle c (mixed form): 1 / (max-norm of the previous residual).
-__device__ __forceinline__ double cast_scale(const KernelParams& p, int b, int c) {
-  if (!p.mixed) return 1.0;
-  double ref = (c == 0 && p.fresh) ? __longlong_as_double((long long)p.accum[b].fmax_bits)
-                                   : p.state[b].rmax_prev;
-  return (ref > 0.0 && ref < 1e300) ? 1.0 / ref : 1.0;
-}
-
-// Outer step (FP64): r = f - delta L_0 u, its norms, and the cast (scaled) level-0 source of the
-// cycle.  The correction of the previous cycle was already added to u by its last sweep.
-template <typename T, int DIM>
-__device__ void phase_outer(const KernelParams& p, int c) {
-  T* R = (T*)p.R;
-  int cur = -1;
-  double mx = 0.0, s2 = 0.0, scale = 1.0;
-  bool active = false;
-  for_tiles(p, 0, [&](int b, long long local) {
-    if (b != cur) {
-      if (cur >= 0) block_flush(mx, s2, &p.accum[cur].rmax_bits[c & 1], &p.accum[cur].rsum2[c & 1]);
-      cur = b;
-      mx = s2 = 0.0;
-      active = !p.accum[b].done;
-      scale = cast_scale(p, b, c);
-    }
-    if (!active) return;
-    const ProblemDesc& P = p.probs[b];
-    const int N = level_side(P.n, 0);
-    if (local >= level_nodes<DIM>(N)) return;
-    int i, j, k;
-    decode<DIM>(local, N, i, j, k);
-    T* R0 = R + P.off_lvl[0];
-    if (is_fixed<DIM>(P, N, i, j, k)) {
-      R0[local] = (T)0;
-      return;
-    }
-    const double r = residual_at<DIM>(P, N, i, j, k, p.U + P.off_full, p.F + P.off_full,
-                                      p.SIG64 ? p.SIG64 + P.off_full : nullptr,
-                                      p.A64 ? p.A64 + P.off_full : nullptr, p.kappa, p.w_edge, p.w_corner);
-    R0[local] = (T)(r * scale);
-    mx = nan_max(mx, fabs(r));
-    s2 += r * r;
-  });
-  if (cur >= 0) block_flush(mx, s2, &p.accum[cur].rmax_bits[c & 1], &p.accum[cur].rsum2[c & 1]);
-}
-
-// Convergence check after the outer step of cycle c (CTA 0 only): relative residuals, stop
-// decisions, history, next cast scale.  Writes sync->active[c & 1].
-template <typename T, int DIM>
-__device__ void phase_check(const KernelParams& p, int c) {
-  int any = 0;
-  for (int b = threadIdx.x; b < p.batch; b += blockDim.x) {
-    ProblemState& S = p.state[b];
-    Accum& A = p.accum[b];
-    if (A.done) continue;
-    const double rmax = __longlong_as_double((long long)A.rmax_bits[c & 1]);
-    const double rs2 = A.rsum2[c & 1];
-    if (c == 0 && p.fresh) {
-      const double fmax = __longlong_as_double((long long)A.fmax_bits);
-      S.fnorm = fmax > 0.0 ? fmax : rmax;
-      S.fnorm2 = fmax > 0.0 ? sqrt(A.fsum2) : sqrt(rs2);
-      S.rel_prev = 1e300;
-      S.grow = 0;
-    }
-    S.scale_used[c & 1] = cast_scale(p, b, c);
-    const double rel = S.fnorm > 0.0 ? rmax / S.fnorm : 0.0;
-    const double rel2 = S.fnorm2 > 0.0 ? sqrt(rs2) / S.fnorm2 : 0.0;
-    S.rel = rel;
-    S.rel_l2 = rel2;
-    if (c < p.hist_cap) p.hist[(long long)b * p.hist_cap + c] = rel;
-    S.hist_len = c + 1;
-    if (c > 0) S.cycles += 1;
-    S.grow = (rel > S.rel_prev) ? S.grow + 1 : 0;
-    S.rel_prev = rel;
-    S.rmax_prev = rmax;
-    int st = 0, stop = 0;
-    if (!(rel <= 1e300)) {
-      st = -6;  // SGML_ERR_NONFINITE
-      stop = 1;
-    } else if (rel <= p.tol) {
-      stop = 1;
-    } else if (S.grow >= 3 && rel > 1.0) {
-      st = -4;  // SGML_ERR_DIVERGED
-      stop = 1;
-    } else if (c >= p.max_cycles) {
-      st = p.tol >= 0.0 ? -3 : 0;  // SGML_ERR_NOT_CONVERGED for a solve; fine for run_cycle
-      stop = 1;
-    }
-    S.status = st;
-    A.done = stop;
-    A.rmax_bits[(c + 1) & 1] = 0ull;
-    A.rsum2[(c + 1) & 1] = 0.0;
-    if (!stop) any = 1;
-  }
-  any = __syncthreads_or(any);
-  if (threadIdx.x == 0) p.sync->active[c & 1] = any;
-}
-
-// Number of sweeps of a visit of tooth nu1 for a problem with n levels (Algorithm 3).
-__device__ __forceinline__ int visit_sweeps(int n_r, int n, int tooth, bool final_visit) {
-  const int e = n - tooth;
-  const int cap = e >= 30 ? (1 << 30) : (1 << e);
-  const int k = n_r < cap ? n_r : cap;
-  return final_visit ? 3 * k : k;
-}
-
-// Restriction pass: level l-1 -> level l (Eqs. 3-4 at distance 2^(l-1) h), even images.
-template <typename T, int DIM>
-__device__ void phase_restrict(const KernelParams& p, int l) {
-  T* R = (T*)p.R;
-  for_tiles(p, l, [&](int b, long long local) {
-    const ProblemDesc& P = p.probs[b];
-    if (l > P.n - 1 || p.accum[b].done) return;
-    const int Nt = level_side(P.n, l), Ns = level_side(P.n, l - 1);
-    if (local >= level_nodes<DIM>(Nt)) return;
-    int i, j, k;
-    decode<DIM>(local, Nt, i, j, k);
-    const T* src = R + P.off_lvl[l - 1];
-    T acc = (T)0;
-#pragma unroll
-    for (int dz = (DIM == 3 ? -1 : 0); dz <= (DIM == 3 ? 1 : 0); ++dz) {
-      const int kk = DIM == 3 ? refl(2 * k + dz, Ns) : 0;
-#pragma unroll
-      for (int dy = -1; dy <= 1; ++dy) {
-        const int jj = refl(2 * j + dy, Ns);
-#pragma unroll
-        for (int dx = -1; dx <= 1; ++dx) {
-          const int ii = refl(2 * i + dx, Ns);
-          const T w = (T)((dx ? 0.25 : 0.5) * (dy ? 0.25 : 0.5) * (DIM == 3 ? (dz ? 0.25 : 0.5) : 1.0));
-          acc += w * src[lin<DIM>(ii, jj, kk, Ns)];
-        }
-      }
-    }
-    R[P.off_lvl[l] + local] = acc;
-  });
-}
-
-// One Jacobi sweep of the pseudo-time equation at level l (Eq. 2, explicit Euler, local step):
-//   e_new = e + dtau (delta L_l e - r_l)
-//         = (1 - omega) e_i + q_i (sigma_i CS(e) + CS(sigma e) - r_i / c),  c = kappa / (2 H^2),
-// with CS(v) = sum_o w_o v_{i+o} over the level-l neighbours, q_i = dtau_i c and
-// omega = dtau_i D_i (constant for the Jacobi-scaled step).  The last sweep of a cycle adds its
-// result, unscaled, to the FP64 solution instead of storing it.
-template <typename T, int DIM>
-__device__ void phase_sweep(const KernelParams& p, const Phase& ph, int c) {
-  T* E = (T*)p.E;
-  T* E2 = (T*)p.E2;
-  const T* R = (const T*)p.R;
-  const T* SG = (const T*)p.SIG;
-  const T* Q = (const T*)p.Q;
-  const int l = ph.level;
-  const bool final_visit = (ph.flags & kFinalVisit) != 0;
-  const T one_m_omega = (T)(1.0 - p.omega);
-  const T w_e = (T)p.w_edge, w_c = (T)p.w_corner;
-  for_tiles(p, l, [&](int b, long long local) {
-    const ProblemDesc& P = p.probs[b];
-    if (ph.tooth > P.n - 1 || p.accum[b].done) return;
-    const int k_b = visit_sweeps(p.n_r, P.n, ph.tooth, final_visit);
-    if (ph.sweep >= k_b) return;
-    const int N = level_side(P.n, l);
-    if (local >= level_nodes<DIM>(N)) return;
-    int i, j, k;
-    decode<DIM>(local, N, i, j, k);
-    const bool zero_in = ph.sweep == 0 && (ph.flags & kFirstOfTooth) && ph.tooth == P.n - 1;
-    const bool last = final_visit && ph.sweep == k_b - 1;
-    const long long off = P.off_lvl[l];
-    const T* src = (ph.sweep & 1) ? E2 + off : E + off;
-    T* dst = (ph.sweep & 1) ? E + off : E2 + off;
-    if (is_fixed<DIM>(P, N, i, j, k)) {
-      if (!last) dst[local] = (T)0;
-      return;
-    }
-    const double H = P.h * (double)(1 << l);
-    const T inv_c = (T)(2.0 * H * H / p.kappa);
-    T e_c = (T)0, cs_e[3] = {(T)0, (T)0, (T)0}, cs_se[3] = {(T)0, (T)0, (T)0};
-    const T* sg = SG + off;
-    if (!zero_in) {
-      e_c = src[local];
-#pragma unroll
-      for (int dz = (DIM == 3 ? -1 : 0); dz <= (DIM == 3 ? 1 : 0); ++dz) {
-        const int kk = DIM == 3 ? refl(k + dz, N) : 0;
-#pragma unroll
-        for (int dy = -1; dy <= 1; ++dy) {
-          const int jj = refl(j + dy, N);
-#pragma unroll
-          for (int dx = -1; dx <= 1; ++dx) {
-            if (dx == 0 && dy == 0 && dz == 0) continue;
-            const int nz = (dx != 0) + (dy != 0) + (dz != 0);
-            const int o = lin<DIM>(refl(i + dx, N), jj, kk, N);
-            const T ev = src[o];
-            cs_e[nz - 1] += ev;
-            if (P.hetero) cs_se[nz - 1] += sg[o] * ev;
-          }
-        }
-      }
-    }
-    const T CSe = cs_e[0] + w_e * cs_e[1] + (DIM == 3 ? w_c * cs_e[2] : (T)0);
-    const T r_i = R[off + local];
-    T e_new;
-    if (P.hetero) {
-      const T CSse = cs_se[0] + w_e * cs_se[1] + (DIM == 3 ? w_c * cs_se[2] : (T)0);
-      e_new = one_m_omega * e_c + Q[off + local] * (sg[local] * CSe + CSse - r_i * inv_c);
-    } else {
-      e_new = one_m_omega * e_c + (T)P.q_const[l] * ((T)2 * CSe - r_i * inv_c);
-    }
-    if (last) {
-      p.U[P.off_full + local] += (double)e_new / p.state[b].scale_used[c & 1];
-    } else {
-      dst[local] = e_new;
-    }
-  });
-}
-
-// Buffer holding the result of a visit of tooth `tooth` at a level (E if the visit did an even
-// number of sweeps, E2 otherwise).
-template <typename T>
-__device__ __forceinline__ T* visit_result(const KernelParams& p, const ProblemDesc& P, int tooth, int l) {
-  const int k = visit_sweeps(p.n_r, P.n, tooth, false);
-  return ((k & 1) ? (T*)p.E2 : (T*)p.E) + P.off_lvl[l];
-}
-
-// Moving one level finer: E_l (+)= I(E_{l+1} - B_{l+1}) on every level-l node (hat-function
-// interpolation, Algorithm 2's I_lambda, between consecutive levels).
-template <typename T, int DIM>
-__device__ void phase_prolong(const KernelParams& p, const Phase& ph) {
-  const int l = ph.level;
-  const bool init = (ph.flags & kInit) != 0;
-  const T* B = (const T*)p.B;
-  for_tiles(p, l, [&](int b, long long local) {
-    const ProblemDesc& P = p.probs[b];
-    if (ph.tooth > P.n - 1 || p.accum[b].done) return;
-    const int N = level_side(P.n, l), Nc = level_side(P.n, l + 1);
-    if (local >= level_nodes<DIM>(N)) return;
-    int i, j, k;
-    decode<DIM>(local, N, i, j, k);
-    T* El = (T*)p.E + P.off_lvl[l];
-    if (is_fixed<DIM>(P, N, i, j, k)) {
-      El[local] = (T)0;
-      return;
-    }
-    const T* src = visit_result<T>(p, P, ph.tooth, l + 1);
-    const T* Bc = B + P.off_lvl[l + 1];
-    const int i0 = i >> 1, j0 = j >> 1, k0 = k >> 1;
-    const int ni = (i & 1) ? 2 : 1, nj = (j & 1) ? 2 : 1, nk = (DIM == 3 && (k & 1)) ? 2 : 1;
-    const T half = (T)0.5;
-    T val = (T)0;
-    for (int cz = 0; cz < nk; ++cz)
-      for (int cy = 0; cy < nj; ++cy)
-        for (int cx = 0; cx < ni; ++cx) {
-          const int o = lin<DIM>(i0 + cx, j0 + cy, DIM == 3 ? k0 + cz : 0, Nc);
-          const T w = (ni == 2 ? half : (T)1) * (nj == 2 ? half : (T)1) * (nk == 2 ? half : (T)1);
-          const T d = init ? src[o] : src[o] - Bc[o];
-          val += w * d;
-        }
-    const T base = init ? (T)0 : visit_result<T>(p, P, ph.prev_tooth, l)[local];
-    El[local] = base + val;
-  });
-}
-
-// Moving one level coarser: E_{l} = B_{l} = (result at level l-1) on the level-l subset.
-template <typename T, int DIM>
-__device__ void phase_inject(const KernelParams& p, const Phase& ph) {
-  const int l = ph.level;
-  for_tiles(p, l, [&](int b, long long local) {
-    const ProblemDesc& P = p.probs[b];
-    if (ph.tooth > P.n - 1 || l > P.n - 1 || p.accum[b].done) return;
-    const int N = level_side(P.n, l), Nf = level_side(P.n, l - 1);
-    if (local >= level_nodes<DIM>(N)) return;
-    int i, j, k;
-    decode<DIM>(local, N, i, j, k);
-    const T* src = visit_result<T>(p, P, ph.tooth, l - 1);
-    const T v = src[lin<DIM>(2 * i, 2 * j, 2 * k, Nf)];
-    ((T*)p.E)[P.off_lvl[l] + local] = v;
-    ((T*)p.B)[P.off_lvl[l] + local] = v;
-  });
-}
-
-// ---------------------------------------------------------------------------------------------
-// The persistent cycle kernel
-// ---------------------------------------------------------------------------------------------
-template <typename T, int DIM>
-__global__ void __launch_bounds__(1024) cycle_kernel(const KernelParams p) {
-  if (p.fresh) {
-    phase_lift<T, DIM>(p);
-    if (!grid_sync(p.sync, p.timeout_ns)) return;
-  }
-  for (int c = 0;; ++c) {
-    phase_outer<T, DIM>(p, c);
-    if (!grid_sync(p.sync, p.timeout_ns)) return;
-    if (blockIdx.x == 0) phase_check<T, DIM>(p, c);
-    if (!grid_sync(p.sync, p.timeout_ns)) return;
-    if (!ld_volatile(&p.sync->active[c & 1])) break;
-    for (int q = 0; q < p.nphases; ++q) {
-      const Phase ph = p.phases[q];
-      switch (ph.op) {
-        case OP_RESTRICT: phase_restrict<T, DIM>(p, ph.level); break;
-        case OP_SWEEP: phase_sweep<T, DIM>(p, ph, c); break;
-        case OP_PROLONG: phase_prolong<T, DIM>(p, ph); break;
-        default: phase_inject<T, DIM>(p, ph); break;
-      }
-      if (!grid_sync(p.sync, p.timeout_ns)) return;
-    }
-  }
+static void* phase_fn() {
+  return (void*)phase_kernel<T, DIM>;
 }
 
 template <typename T, int DIM>
@@ -567,19 +1132,46 @@ static void* cycle_fn() {
   return (void*)cycle_kernel<T, DIM>;
 }
 
-static void* pick_cycle(int mixed, int dim) {
-  if (mixed) return dim == 3 ? cycle_fn<float, 3>() : cycle_fn<float, 2>();
-  return dim == 3 ? cycle_fn<double, 3>() : cycle_fn<double, 2>();
+static size_t smem_for(int mixed) { return mixed ? phase_smem_bytes<float>() : phase_smem_bytes<double>(); }
+
+static void* pick(int mixed, int dim, bool cycle) {
+  if (cycle) {
+    if (mixed) return dim == 3 ? cycle_fn<float, 3>() : cycle_fn<float, 2>();
+    return dim == 3 ? cycle_fn<double, 3>() : cycle_fn<double, 2>();
+  }
+  if (mixed) return dim == 3 ? phase_fn<float, 3>() : phase_fn<float, 2>();
+  return dim == 3 ? phase_fn<double, 3>() : phase_fn<double, 2>();
 }
 
-cudaError_t launch_cycle_kernel(const KernelParams& p, int mixed, int dim, int blocks, int threads,
+// Opt the kernel into its dynamic shared memory (above the 48 KB default); idempotent.
+static cudaError_t prepare_fn(void* fn, int mixed) {
+  return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_for(mixed));
+}
+
+cudaError_t launch_phase_kernel(const KernelParams& p, int mixed, int dim, int blocks, int threads, int which, int c,
                                 cudaStream_t s) {
+  (void)threads;
+  void* fn = pick(mixed, dim, false);
+  cudaError_t e = prepare_fn(fn, mixed);
+  if (e != cudaSuccess) return e;
+  void* args[] = {(void*)&p, (void*)&which, (void*)&c};
+  return cudaLaunchKernel(fn, dim3(which == -1 ? 1 : blocks), dim3(kThreads), args, smem_for(mixed), s);
+}
+
+cudaError_t launch_cycle_kernel(const KernelParams& p, int mixed, int dim, int blocks, int threads, cudaStream_t s) {
+  (void)threads;
+  void* fn = pick(mixed, dim, true);
+  cudaError_t e = prepare_fn(fn, mixed);
+  if (e != cudaSuccess) return e;
   void* args[] = {(void*)&p};
-  return cudaLaunchCooperativeKernel(pick_cycle(mixed, dim), dim3(blocks), dim3(threads), args, 0, s);
+  return cudaLaunchCooperativeKernel(fn, dim3(blocks), dim3(kThreads), args, smem_for(mixed), s);
 }
 
 int cycle_kernel_occupancy(int mixed, int dim, int threads, int* blocks_per_sm) {
-  return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, pick_cycle(mixed, dim), threads, 0);
+  (void)threads;
+  void* fn = pick(mixed, dim, true);
+  if (prepare_fn(fn, mixed) != cudaSuccess) return 1;
+  return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, kThreads, smem_for(mixed));
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -609,7 +1201,7 @@ __global__ void restrict64_kernel(const double* __restrict__ src, int Ns, double
 template <typename T, int DIM>
 __global__ void setup_level_kernel(ProblemDesc P, int l, const double* __restrict__ sig, const double* __restrict__ a,
                                    double kappa, double w_edge, double w_corner, double theta_gain,
-                                   T* __restrict__ SIG, T* __restrict__ Q) {
+                                   T* __restrict__ SIG, T* __restrict__ Q, T* __restrict__ AT) {
   const int N = level_side(P.n, l);
   const long long M = level_nodes<DIM>(N);
   const double H = P.h * (double)(1 << l);
@@ -632,6 +1224,7 @@ __global__ void setup_level_kernel(ProblemDesc P, int l, const double* __restric
     const double D = cH * sum - av;
     SIG[t] = (T)sc;
     Q[t] = (T)(theta_gain / D * cH);
+    if (AT) AT[t] = (T)av;
   }
 }
 
@@ -693,20 +1286,22 @@ cudaError_t launch_restrict64(int dim, const double* src, int Ns, double* dst, i
 
 cudaError_t launch_setup_level(int mixed, int dim, const ProblemDesc& P, int l, const double* sig, const double* a,
                                double kappa, double w_edge, double w_corner, double theta_gain, void* SIG_T,
-                               void* Q_T, cudaStream_t s) {
+                               void* Q_T, void* A_T, cudaStream_t s) {
   const int N = (1 << (P.n - l)) + 1;
   const long long M = dim == 3 ? (long long)N * N * N : (long long)N * N;
   const long long off = P.off_lvl[l];
   if (mixed) {
     float* S = (float*)SIG_T + off;
     float* Q = (float*)Q_T + off;
-    if (dim == 3) setup_level_kernel<float, 3><<<grid_for(M), 256, 0, s>>>(P, l, sig, a, kappa, w_edge, w_corner, theta_gain, S, Q);
-    else setup_level_kernel<float, 2><<<grid_for(M), 256, 0, s>>>(P, l, sig, a, kappa, w_edge, w_corner, theta_gain, S, Q);
+    float* AT = A_T ? (float*)A_T + off : nullptr;
+    if (dim == 3) setup_level_kernel<float, 3><<<grid_for(M), 256, 0, s>>>(P, l, sig, a, kappa, w_edge, w_corner, theta_gain, S, Q, AT);
+    else setup_level_kernel<float, 2><<<grid_for(M), 256, 0, s>>>(P, l, sig, a, kappa, w_edge, w_corner, theta_gain, S, Q, AT);
   } else {
     double* S = (double*)SIG_T + off;
     double* Q = (double*)Q_T + off;
-    if (dim == 3) setup_level_kernel<double, 3><<<grid_for(M), 256, 0, s>>>(P, l, sig, a, kappa, w_edge, w_corner, theta_gain, S, Q);
-    else setup_level_kernel<double, 2><<<grid_for(M), 256, 0, s>>>(P, l, sig, a, kappa, w_edge, w_corner, theta_gain, S, Q);
+    double* AT = A_T ? (double*)A_T + off : nullptr;
+    if (dim == 3) setup_level_kernel<double, 3><<<grid_for(M), 256, 0, s>>>(P, l, sig, a, kappa, w_edge, w_corner, theta_gain, S, Q, AT);
+    else setup_level_kernel<double, 2><<<grid_for(M), 256, 0, s>>>(P, l, sig, a, kappa, w_edge, w_corner, theta_gain, S, Q, AT);
   }
   return cudaGetLastError();
 }

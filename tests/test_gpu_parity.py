@@ -166,3 +166,56 @@ def test_run_cycle_continues_and_residual_norm():
     rel = g.residual_norm(sgml.NORM_MAX)[0]
     assert rel == pytest.approx(p.rel_residual(u, d["f"]), rel=1e-9)
     assert g.get_stats(0)[0] == 3
+
+
+def test_phased_launch_mode_matches_persistent_mode():
+    """The one-launch-per-phase mode runs the same device code: identical results."""
+    d = inputs.random_problem(3, 4, seed=320, flux=True)
+    for prec in (sgml.FP64, sgml.MIXED):
+        g1 = gpu_grid([d], prec)
+        g1.run_cycle(3)
+        g2 = gpu_grid([d], prec)
+        g2.set_launch(0, 1, 1)
+        g2.run_cycle(3)
+        assert np.array_equal(g1.get_solution(0), g2.get_solution(0))
+        s1 = g1.solve_to_tol(1e-11)
+        s2 = g2.solve_to_tol(1e-11)
+        assert s1[0] == s2[0] == sgml.OK and s1[1][0] == s2[1][0]
+        assert np.array_equal(g1.get_solution(0), g2.get_solution(0))
+
+
+@pytest.mark.parametrize("dim,ctas,waves", [(2, 1, 1), (3, 1, 3), (3, 2, 8), (3, 0, 2)])
+def test_launch_shapes_give_identical_results(dim, ctas, waves):
+    d = inputs.random_problem(dim, 6 if dim == 2 else 5, seed=321)
+    g1 = gpu_grid([d], sgml.MIXED)
+    g1.run_cycle(2)
+    g2 = gpu_grid([d], sgml.MIXED)
+    g2.set_launch(ctas, waves)
+    g2.run_cycle(2)
+    assert np.array_equal(g1.get_solution(0), g2.get_solution(0))
+
+
+def high_contrast(dim, n, seed):
+    """Slowly converging problem: sigma jumps between 1 and 80 on a random pattern of 2^d blocks."""
+    d = inputs.random_problem(dim, n, seed=seed, hetero=True, helmholtz=False, mixed_bc=False)
+    rng = np.random.default_rng(seed)
+    N = 2 ** n + 1
+    blk = rng.uniform(size=(N // 2 + 1,) * dim) < 0.3
+    d["sigma"] = np.where(np.kron(blk, np.ones((2,) * dim))[(slice(0, N),) * dim], 80.0, 1.0)
+    return d
+
+
+@pytest.mark.parametrize("dim,n", [(2, 6), (3, 4)])
+def test_mixed_recurrence_converges_to_oracle_solution(dim, n):
+    """Slow contraction: the mixed form runs most cycles on the FP32-stencil residual recurrence,
+    re-anchored on the FP64 residual; the converged solution is the oracle's."""
+    d = high_contrast(dim, n, seed=400 + dim)
+    p = oracle_problem(d)
+    u_ref, c_ref, hist = p.solve(d["f"], tol=1e-12, max_cycles=600)
+    assert c_ref > 10 and np.max(hist[2:] / hist[1:-1]) > 0.2  # slow enough for the recurrence to be used
+    g = gpu_grid([d], sgml.MIXED, max_cycles=600)
+    st, cyc, rel = g.solve_to_tol(1e-12)
+    assert st == sgml.OK and rel[0] <= 1e-12
+    assert abs(int(cyc[0]) - c_ref) <= max(3, c_ref // 10)
+    assert rel_l2(g.get_solution(0), u_ref) <= 1e-10
+    assert p.rel_residual(g.get_solution(0), d["f"]) <= 1.5e-12
