@@ -352,7 +352,11 @@ def run_ncu_case(args):
         g.set_launch(0, 1, 1)
     sgml.problem_into_grid(g, 0, d)
     g.run_cycle(1)  # warm-up launch (and setup)
-    g.run_cycle(args.ncu_cycles)
+    if args.ncu_solve:
+        g.set_params(max_cycles=args.max_cycles)
+        g.solve_to_tol(TOL)
+    else:
+        g.run_cycle(args.ncu_cycles)
     torch.cuda.synchronize()
     c, rel, st = g.get_stats(0)
     print(json.dumps({"ncu_case": True, "n": args.n, "form": args.form, "cycles": c, "rel": rel, "status": st}))
@@ -379,6 +383,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--ncu-case", action="store_true")
     ap.add_argument("--ncu-cycles", type=int, default=2)
+    ap.add_argument("--ncu-solve", action="store_true", help="ncu case: one full solve instead of --ncu-cycles")
     ap.add_argument("--phased", action="store_true")
     args = ap.parse_args()
     args_global = args
