@@ -149,6 +149,33 @@ int sgml_launch_count(sgml_grid_t g, long long* count);
 int sgml_destroy(sgml_grid_t g);
 const char* sgml_last_error(void);
 
+/* One complete solve that allocates no memory, for callers that cannot allocate device memory
+ * where they want to solve: code running while a stream is captured into a CUDA graph, memory pools
+ * that forbid foreign allocations, hosts with a device-memory budget fixed at start-up.  The paper
+ * has no counterpart; this packages the same cycle kernel as sgml_solve_to_tol.
+ *
+ * Solves L u = f (L = div(sigma grad) + a_scalar, paper's sign) for ONE problem of dimension dim with
+ * N = 2^n + 1 nodes per side from the lifted boundary values until ||r||_inf / ||f||_inf <= rtol or
+ * max_cycles cycles, with the default method parameters (n_r = 2, theta = 0.7, consistent stencil).
+ * f (N^dim doubles), sigma (N^dim doubles or NULL for 1) and u (N^dim doubles, written) are DEVICE
+ * pointers owned by the caller; face_type / face_value (2*dim entries, face_value may be NULL) are
+ * host arrays as in sgml_set_bc; a_scalar <= 0.  cycles_out / rel_out (host, may be NULL) receive the
+ * cycles run and the final relative residual.  Work runs on cuda_stream; the call synchronises it.
+ *
+ * All intermediate data lives in one file-scope device array of 24 MiB that every GPU loading the
+ * library holds until the process exits; problems needing more (e.g. beyond 65^3 in 3-D or 513^2
+ * in 2-D) are rejected with SGML_ERR_ARG before any GPU work.  No cudaMalloc, cudaFree or other
+ * allocating routine is called.  The first call on each device looks up the array's device
+ * address (cudaGetSymbolAddress) with that device current: make that first call before any stream
+ * capture begins.  Every call shares the array and clears what must start at zero; calls whose
+ * work overlaps on the GPU (other streams, other host threads) race on it and must be serialised by
+ * the caller.  Returns SGML_OK on convergence, else an sgml_status; the message is in
+ * sgml_noalloc_last_error(). */
+int sgml_solve_noalloc(int dim, int n, int precision, const double* f, const double* sigma, double a_scalar,
+                       const int* face_type, const double* face_value, double rtol, int max_cycles, double* u,
+                       int* cycles_out, double* rel_out, void* cuda_stream);
+const char* sgml_noalloc_last_error(void);
+
 #ifdef __cplusplus
 }
 #endif

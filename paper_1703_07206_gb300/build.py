@@ -16,7 +16,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libsgml.so")
-SOURCES = ["sgml_kernels.cu", "sgml_api.cu"]
+SOURCES = ["sgml_kernels.cu", "sgml_api.cu", "sgml_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -57,6 +57,11 @@ _SIGNATURES = {
     "sgml_launch_count": [ctypes.c_void_p, ctypes.POINTER(ctypes.c_longlong)],
     "sgml_destroy": [ctypes.c_void_p],
     "sgml_last_error": [],
+    "sgml_solve_noalloc": [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double,
+                           ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double), ctypes.c_double,
+                           ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(ctypes.c_int),
+                           ctypes.POINTER(ctypes.c_double), ctypes.c_void_p],
+    "sgml_noalloc_last_error": [],
 }
 
 
@@ -72,7 +77,7 @@ def load(path: str | None = None):
     for name, args in _SIGNATURES.items():
         fn = getattr(lib, name)
         fn.argtypes = args
-        fn.restype = ctypes.c_char_p if name == "sgml_last_error" else ctypes.c_int
+        fn.restype = ctypes.c_char_p if name.endswith("last_error") else ctypes.c_int
     _lib = lib
     return lib
 
@@ -222,6 +227,28 @@ class Grid:
         c = ctypes.c_longlong()
         _check(load().sgml_launch_count(self._h, ctypes.byref(c)))
         return c.value
+
+
+def solve_noalloc(dim, n, f, u, sigma=None, a_scalar=0.0, faces=None, values=None, rtol=1e-10, max_cycles=200,
+                  precision=MIXED, stream=None):
+    """sgml_solve_noalloc: one solve with no allocation; f, sigma, u are CUDA tensors (float64).
+    Returns (status, cycles, relative residual); raises on argument / CUDA errors."""
+    lib = load()
+    faces = list(faces) if faces is not None else [DIRICHLET] * (2 * dim)
+    ft = (ctypes.c_int * 6)(*(faces + [0] * (6 - len(faces))))
+    fv = None
+    if values is not None:
+        fv = (ctypes.c_double * 6)(*([float(v) for v in values] + [0.0] * (6 - len(values))))
+    m = (2 ** n + 1) ** dim
+    cyc, rel = ctypes.c_int(), ctypes.c_double()
+    sptr = None
+    if stream is not None:
+        sptr = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+    st = lib.sgml_solve_noalloc(dim, n, precision, _addr(f, m), _addr(sigma, m), float(a_scalar), ft, fv,
+                                float(rtol), int(max_cycles), _addr(u, m), ctypes.byref(cyc), ctypes.byref(rel), sptr)
+    if st in (ERR_ARG, ERR_CUDA, ERR_BARRIER_TIMEOUT):
+        raise SGMLError(st, lib.sgml_noalloc_last_error().decode())
+    return st, cyc.value, rel.value
 
 
 def problem_into_grid(grid, b, prob):
