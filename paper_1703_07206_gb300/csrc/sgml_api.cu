@@ -16,6 +16,7 @@
 
 #include "sgml.h"
 #include "sgml_internal.cuh"
+#include "sgml_tasks.h"
 
 using namespace sgml;
 
@@ -157,33 +158,21 @@ static int upload_tiles(sgml_grid* g) {
   if (g->ctas_per_sm > 0) bps = std::min(bps, g->ctas_per_sm);
   g->blocks = g->sms * bps;
   std::vector<long long> rp((size_t)kMaxLevels * (g->batch + 1), 0);
-  std::vector<TileTask> tasks;
-  std::vector<int> toff(kMaxLevels + 1, 0);
-  for (int l = 0; l < kMaxLevels; ++l) {
-    toff[l] = (int)tasks.size();
-    long long nxy = 0;
+  std::vector<int> nb(g->batch), dir_hi(g->batch);
+  for (int b = 0; b < g->batch; ++b) {
+    nb[b] = g->P[b].n;
+    dir_hi[b] = (g->P[b].face_type[1] == SGML_DIRICHLET ? 1 : 0) | (g->P[b].face_type[3] == SGML_DIRICHLET ? 2 : 0);
+  }
+  for (int l = 0; l < kMaxLevels; ++l)
     for (int b = 0; b < g->batch; ++b) {
       const int n = g->P[b].n;
       const long long N = side(n, std::min(l, n - 1));
       const long long rows = (l <= n - 1) ? (g->dim == 3 ? N * N : N) : 0;
       rp[(size_t)l * (g->batch + 1) + b + 1] = rp[(size_t)l * (g->batch + 1) + b] + rows;
-      if (l <= n - 1) nxy += ((N + kTX - 1) / kTX) * ((N + kTY - 1) / kTY);
     }
-    long long nzc = 1;
-    if (g->dim == 3 && nxy > 0) nzc = std::max(1LL, (long long)std::llround((double)g->blocks * g->z_waves / nxy));
-    for (int b = 0; b < g->batch; ++b) {
-      const int n = g->P[b].n;
-      if (l > n - 1) continue;
-      const int N = (int)side(n, l);
-      const int chunk = g->dim == 3 ? (int)std::max<long long>(2, (N + std::min<long long>(nzc, N) - 1) / std::min<long long>(nzc, N)) : 1;
-      const int zmax = g->dim == 3 ? N : 1;
-      for (int z0 = 0; z0 < zmax; z0 += chunk)
-        for (int y0 = 0; y0 < N; y0 += kTY)
-          for (int x0 = 0; x0 < N; x0 += kTX)
-            tasks.push_back(TileTask{b, (short)x0, (short)y0, (short)z0, (short)std::min(chunk, zmax - z0)});
-    }
-  }
-  toff[kMaxLevels] = (int)tasks.size();
+  std::vector<TileTask> tasks((size_t)partition_bound(g->dim, nb.data(), g->batch, g->blocks));
+  std::vector<int> toff((size_t)kMaxLevels * (g->blocks + 1));
+  tasks.resize(build_partition(g->dim, nb.data(), dir_hi.data(), g->batch, g->blocks, tasks.data(), toff.data()));
   if (g->d_rows) SGML_CUDA(cudaFree(g->d_rows));
   if (g->d_tasks) SGML_CUDA(cudaFree(g->d_tasks));
   if (g->d_task_off) SGML_CUDA(cudaFree(g->d_task_off));
@@ -519,6 +508,7 @@ int sgml_set_bc(sgml_grid_t g, int problem, const int* face_type, const double* 
     }
   }
   g->dirty_desc = true;
+  g->dirty_tiles = true;
   g->fresh = true;
   return SGML_OK;
 }

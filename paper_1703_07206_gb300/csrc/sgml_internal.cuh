@@ -86,7 +86,8 @@ struct GridSync {
 
 // Work unit of the tiled phases.  3-D: the kTX x kTY columns starting at (x0, y0) of one level of
 // problem b, planes z0 .. z0 + nz - 1 (the CTA marches in z).  2-D: the kTX x kTY nodes at (x0, y0).
-constexpr int kTX = 32, kTY = 8, kThreads = kTX * kTY;
+// A CTA of kThreads threads covers a tile, two vertically adjacent columns per thread.
+constexpr int kTX = 32, kTY = 16, kThreads = 256;
 struct TileTask {
   int b;
   short x0, y0, z0, nz;
@@ -100,8 +101,8 @@ struct KernelParams {
   Accum* accum;
   const Phase* phases;
   int nphases;
-  const TileTask* tasks;         // column tiles of every level, level l at tasks[task_off[l] ..]
-  const int* task_off;           // [kMaxLevels + 1]
+  const TileTask* tasks;         // column-tile pieces of every level
+  const int* task_off;           // [kMaxLevels][gridDim.x + 1]: CTA c owns tasks[off[c] .. off[c + 1])
   const long long* row_prefix;   // [kMaxLevels][batch + 1] cumulative node-row counts per level
   int fresh;                     // lift u and measure f first
   int max_cycles;

@@ -141,8 +141,9 @@ __device__ bool grid_sync(GridSync* gs, unsigned long long timeout_ns) {
 // ---------------------------------------------------------------------------------------------
 template <class Body>
 __device__ __forceinline__ void for_tasks(const KernelParams& p, int l, Body&& body) {
-  const int t0 = p.task_off[l], t1 = p.task_off[l + 1];
-  for (int t = t0 + blockIdx.x; t < t1; t += gridDim.x) body(p.tasks[t]);
+  const int* o = p.task_off + (long long)l * (gridDim.x + 1) + blockIdx.x;
+  const int t0 = o[0], t1 = o[1];
+  for (int t = t0; t < t1; ++t) body(p.tasks[t]);
 }
 
 // Rows of level l of all problems; body(b, N, y, z) runs on one warp (lanes cover x).
@@ -169,35 +170,40 @@ __device__ __forceinline__ int visit_sweeps(int n_r, int n, int tooth, bool fina
   return final_visit ? 3 * k : k;
 }
 
-// Halo cells of a kTX x kTY tile: (kTX + 2) x (kTY + 2) = 340 cells, at most 2 per thread.
+// Halo of a kTX x kTY tile: (kTX + 2) x (kTY + 2) cells, at most kCells per thread.  Thread
+// (tx, ty) = (tid % 32, tid / 32) owns the columns (x0 + tx, y0 + 2 ty + r), r = 0, 1.
 constexpr int kHX = kTX + 2, kHY = kTY + 2, kHalo = kHX * kHY;
+constexpr int kCells = (kHalo + kThreads - 1) / kThreads;
+static_assert(kTY == 2 * (kThreads / kTX), "two rows per thread");
 
 struct HaloCells {
-  int off[2];    // y * N + x of the cell (images applied), -1 if the thread has no such cell
-  double ghost[2];  // Neumann image offset 2 k h g of the cell (x, y directions)
+  int off[kCells];        // y * N + x of the cell (images applied), -1 if the thread has no such cell
+  double ghost[kCells];   // Neumann image offset 2 k h g of the cell (x, y directions)
 };
 
 __device__ __forceinline__ HaloCells halo_cells(const ProblemDesc& P, int N, int x0, int y0, bool flux) {
   HaloCells hc;
 #pragma unroll
-  for (int s = 0; s < 2; ++s) {
+  for (int s = 0; s < kCells; ++s) {
     const int k = threadIdx.x + s * kThreads;
     hc.off[s] = -1;
     hc.ghost[s] = 0.0;
     if (k < kHalo) {
       int gx = x0 - 1 + k % kHX, gy = y0 - 1 + k / kHX;
       double g = 0.0;
-      if (gx < 0) { g += (P.face_type[0] == 1) ? 2.0 * P.h * P.face_value[0] : 0.0; }
-      if (gx > N - 1) { g += (P.face_type[1] == 1) ? 2.0 * P.h * P.face_value[1] : 0.0; }
-      if (gy < 0) { g += (P.face_type[2] == 1) ? 2.0 * P.h * P.face_value[2] : 0.0; }
-      if (gy > N - 1) { g += (P.face_type[3] == 1) ? 2.0 * P.h * P.face_value[3] : 0.0; }
+      if (flux) {
+        if (gx < 0 && P.face_type[0] == 1) g += 2.0 * P.h * P.face_value[0];
+        if (gx > N - 1 && P.face_type[1] == 1) g += 2.0 * P.h * P.face_value[1];
+        if (gy < 0 && P.face_type[2] == 1) g += 2.0 * P.h * P.face_value[2];
+        if (gy > N - 1 && P.face_type[3] == 1) g += 2.0 * P.h * P.face_value[3];
+      }
       // cells beyond the image of the far edge (tile overhang past N) are clamped: never used
       gx = refl(gx, N);
       gy = refl(gy, N);
       gx = gx < 0 ? 0 : (gx > N - 1 ? N - 1 : gx);
       gy = gy < 0 ? 0 : (gy > N - 1 ? N - 1 : gy);
       hc.off[s] = gy * N + gx;
-      hc.ghost[s] = flux ? g : 0.0;
+      hc.ghost[s] = g;
     }
   }
   return hc;
@@ -207,6 +213,35 @@ __device__ __forceinline__ double z_ghost(const ProblemDesc& P, int z, int N) {
   if (z < 0 && P.face_type[4] == 1) return 2.0 * P.h * P.face_value[4];
   if (z > N - 1 && P.face_type[5] == 1) return 2.0 * P.h * P.face_value[5];
   return 0.0;
+}
+
+// The two columns a thread owns in a tile: in-level flags, 2-D offsets, and whether an x / y face
+// fixes them (Dirichlet); z faces are checked per plane.
+struct Columns {
+  int off[2];
+  bool in[2];
+  bool fixed_xy[2];
+  bool dz0, dz1;  // -z / +z faces are Dirichlet
+};
+
+__device__ __forceinline__ Columns own_columns(const ProblemDesc& P, int N, int x0, int y0) {
+  Columns cl;
+  const int x = x0 + (threadIdx.x & 31);
+  const bool fx = (x == 0 && P.face_type[0] == 0) || (x == N - 1 && P.face_type[1] == 0);
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    const int y = y0 + 2 * (threadIdx.x >> 5) + r;
+    cl.in[r] = x < N && y < N;
+    cl.off[r] = y * N + x;
+    cl.fixed_xy[r] = fx || (y == 0 && P.face_type[2] == 0) || (y == N - 1 && P.face_type[3] == 0);
+  }
+  cl.dz0 = P.face_type[4] == 0;
+  cl.dz1 = P.face_type[5] == 0;
+  return cl;
+}
+
+__device__ __forceinline__ bool z_fixed(const Columns& cl, int z, int N) {
+  return (z == 0 && cl.dz0) || (z == N - 1 && cl.dz1);
 }
 
 // Block reduction of (max, sum) and one atomic per block into the accumulators.
@@ -260,67 +295,87 @@ __device__ __forceinline__ void cp_async_t(T* smem, const T* gmem) {
 
 // Pipeline depths (stages of shared memory per CTA).
 #ifndef SGML_SWEEP_STAGES
-#define SGML_SWEEP_STAGES 6
+#define SGML_SWEEP_STAGES 4
 #endif
 #ifndef SGML_OUTER_STAGES
-#define SGML_OUTER_STAGES 7
+#define SGML_OUTER_STAGES 5
 #endif
 #ifndef SGML_MIN_CTAS
 #define SGML_MIN_CTAS 2
 #endif
 constexpr int kSweepStages = SGML_SWEEP_STAGES;  // loads issued kSweepStages - 2 planes ahead
-constexpr int kOuterStages = SGML_OUTER_STAGES;  // loads issued kOuterStages - 3 planes ahead (three planes resident)
+constexpr int kOuterStages = SGML_OUTER_STAGES;  // loads issued kOuterStages - 3 planes ahead (three resident)
 
 template <typename T>
 struct SweepStage {
-  T e[kHalo];        // correction e on the halo tile
-  T s[kHalo];        // sigma on the halo tile (heterogeneous problems)
-  T r[kThreads];     // restricted residual at the tile's nodes
-  T q[kThreads];     // local step factor at the tile's nodes
-  double u[kThreads];  // FP64 solution (last sweep of a cycle)
+  T e[kHalo];            // correction e on the halo tile
+  T s[kHalo];            // sigma on the halo tile (heterogeneous problems)
+  T r[2 * kThreads];     // restricted residual at the tile's nodes
+  T q[2 * kThreads];     // local step factor at the tile's nodes
+  double u[2 * kThreads];  // FP64 solution (last sweep of a cycle)
 };
-struct OuterStage {  // size of the FP64 residual stage (ResStage<double>)
-  double u[kHalo];
-  double s[kHalo];
-  double f[kThreads];
-  double a[kThreads];
+
+// Stage of the residual phases: halo tiles of the operand (u in FP64, or e in the cycle precision)
+// and of sigma, the right-hand side at the tile's nodes (f, or the previous residual), and a
+// per-node Helmholtz coefficient.
+template <typename V>
+struct ResStage {
+  V u[kHalo];
+  V s[kHalo];
+  double f[2 * kThreads];
+  V a[2 * kThreads];
 };
 
 template <typename T>
 constexpr size_t sweep_smem_bytes() {
   return sizeof(SweepStage<T>) * kSweepStages;
 }
-constexpr size_t outer_smem_bytes() { return sizeof(OuterStage) * kOuterStages; }
+constexpr size_t outer_smem_bytes() { return sizeof(ResStage<double>) * kOuterStages; }
 template <typename T>
 constexpr size_t phase_smem_bytes() {
   return sweep_smem_bytes<T>() > outer_smem_bytes() ? sweep_smem_bytes<T>() : outer_smem_bytes();
 }
 
 // ---------------------------------------------------------------------------------------------
-// Lift: u = Dirichlet values on fixed nodes, 0 on unknowns; ||f|| over the unknowns.
+// Lift: u = Dirichlet values on fixed nodes, 0 on unknowns; ||f|| over the unknowns.  One node row
+// per warp; each warp folds its rows' norms and flushes them when its problem changes.
 // ---------------------------------------------------------------------------------------------
+__device__ __forceinline__ void warp_flush(double mx, double s2, unsigned long long* mx_dst, double* s2_dst) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    mx = nan_max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(mx_dst, (unsigned long long)__double_as_longlong(mx));
+    atomicAdd(s2_dst, s2);
+  }
+}
+
 template <typename T, int DIM>
 __device__ void phase_lift(const KernelParams& p) {
-  for_tasks(p, 0, [&](const TileTask& tk) {
-    const ProblemDesc& P = p.probs[tk.b];
-    const int N = level_side(P.n, 0);
-    const int x = tk.x0 + (threadIdx.x % kTX), y = tk.y0 + (threadIdx.x / kTX);
-    double mx = 0.0, s2 = 0.0;
-    if (x < N && y < N) {
-      for (int z = tk.z0; z < tk.z0 + tk.nz; ++z) {
-        const long long g = P.off_full + ((long long)z * N + y) * N + x;
-        if (is_fixed<DIM>(P, N, x, y, z)) {
-          p.U[g] = dirichlet_value<DIM>(P, N, x, y, z);
-        } else {
-          p.U[g] = 0.0;
-          const double f = p.F[g];
-          mx = nan_max(mx, fabs(f));
-          s2 += f * f;
-        }
+  const int lane = threadIdx.x & 31;
+  int cur = -1;
+  double mx = 0.0, s2 = 0.0;
+  for_rows<DIM>(p, 0, [&](int b, const ProblemDesc& P, int N, int y, int z) {
+    if (b != cur) {
+      if (cur >= 0) warp_flush(mx, s2, &p.accum[cur].fmax_bits, &p.accum[cur].fsum2);
+      cur = b;
+      mx = s2 = 0.0;
+    }
+    const long long row = P.off_full + ((long long)z * N + y) * N;
+    for (int x = lane; x < N; x += 32) {
+      if (is_fixed<DIM>(P, N, x, y, z)) {
+        p.U[row + x] = dirichlet_value<DIM>(P, N, x, y, z);
+      } else {
+        p.U[row + x] = 0.0;
+        const double f = p.F[row + x];
+        mx = nan_max(mx, fabs(f));
+        s2 += f * f;
       }
     }
-    block_flush(mx, s2, &p.accum[tk.b].fmax_bits, &p.accum[tk.b].fsum2);
   });
+  if (cur >= 0) warp_flush(mx, s2, &p.accum[cur].fmax_bits, &p.accum[cur].fsum2);
 }
 
 // Scale of the residual cast of cycle c (mixed form): 1 / (max-norm of the previous residual).
@@ -343,14 +398,6 @@ __device__ __forceinline__ double cast_scale(const KernelParams& p, int b, int c
 // the CTA's tasks.
 // ---------------------------------------------------------------------------------------------
 template <typename V>
-struct ResStage {
-  V u[kHalo];         // operand (u or e) on the halo tile
-  V s[kHalo];         // sigma on the halo tile
-  double f[kThreads];  // right-hand side at the tile's nodes (f, or the previous residual)
-  V a[kThreads];      // per-node a at the tile's nodes
-};
-
-template <typename V>
 struct ResSrc {
   const V* u;          // operand, packed N^d array of the problem
   const V* s;          // sigma (heterogeneous problems)
@@ -360,26 +407,6 @@ struct ResSrc {
   double opscale;      // r = rhs - opscale * (delta L v)
   bool images;         // Neumann images carry the prescribed derivative (anchor only)
 };
-
-template <typename V, bool HET, int NP>
-__device__ __forceinline__ void res_sums(V uc, V sc, const ResStage<V>* const* S, int cc, V cls[3]) {
-  cls[0] = cls[1] = cls[2] = (V)0;
-#pragma unroll
-  for (int pz = 0; pz < NP; ++pz) {
-#pragma unroll
-    for (int dy = -1; dy <= 1; ++dy)
-#pragma unroll
-      for (int dx = -1; dx <= 1; ++dx) {
-        const int dz = NP == 3 ? pz - 1 : 0;
-        if (dx == 0 && dy == 0 && dz == 0) continue;
-        const int nz = (dx != 0) + (dy != 0) + (dz != 0);
-        const int o = cc + dy * kHX + dx;
-        const V du = S[pz]->u[o] - uc;
-        if (HET) cls[nz - 1] = fma(sc + S[pz]->s[o], du, cls[nz - 1]);
-        else cls[nz - 1] += du;
-      }
-  }
-}
 
 // Does the tile need Neumann image offsets (non-zero prescribed derivative on a face it touches)?
 __device__ __forceinline__ bool tile_has_flux(const ProblemDesc& P, int N, int x0, int y0, int dim) {
@@ -391,6 +418,34 @@ __device__ __forceinline__ bool tile_has_flux(const ProblemDesc& P, int N, int x
   if (dim == 3 && ((P.face_type[4] == 1 && P.face_value[4] != 0.0) || (P.face_type[5] == 1 && P.face_value[5] != 0.0)))
     f = true;
   return f;
+}
+
+// Add one plane's contribution to the class sums of the thread's two nodes: the 4 x 3 block of
+// cells around the two columns, dz = the plane's offset (-1, 0, +1).
+template <typename V, bool HET>
+__device__ __forceinline__ void res_plane(const ResStage<V>& S, int b0, int dz, const V uc[2], const V sc[2],
+                                          V cls[2][3]) {
+  V a[4][3], s[4][3];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      a[i][j] = S.u[b0 + i * kHX + j];
+      if (HET) s[i][j] = S.s[b0 + i * kHX + j];
+    }
+#pragma unroll
+  for (int r = 0; r < 2; ++r)
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        const int dy = i - 1, dx = j - 1;
+        if (dx == 0 && dy == 0 && dz == 0) continue;
+        const int nz = (dx != 0) + (dy != 0) + (dz != 0);
+        const V du = a[r + i][j] - uc[r];
+        if (HET) cls[r][nz - 1] = fma(sc[r] + s[r + i][j], du, cls[r][nz - 1]);
+        else cls[r][nz - 1] += du;
+      }
 }
 
 // Finish one node: r = rhs - opscale * (c0 * sum + a * v_c); store the cast source (and the FP64
@@ -419,34 +474,39 @@ __device__ void residual3(const KernelParams& p, const TileTask& tk, int c, ResS
   constexpr int D = kOuterStages;
   const ProblemDesc& P = p.probs[tk.b];
   const int N = level_side(P.n, 0);
-  const int tid = threadIdx.x, tx = tid % kTX, ty = tid / kTX;
-  const int x = tk.x0 + tx, y = tk.y0 + ty;
-  const bool col = x < N && y < N;
+  const int tid = threadIdx.x;
+  const Columns cl = own_columns(P, N, tk.x0, tk.y0);
   const double scale = cast_scale(p, tk.b, c);
   T* R0 = (T*)p.R + P.off_lvl[0];
   double* RES = p.RES64 ? p.RES64 + P.off_full : nullptr;
-  const HaloCells hc = halo_cells(P, N, tk.x0, tk.y0, true);
   const bool flux = src.images && tile_has_flux(P, N, tk.x0, tk.y0, 3);
+  const HaloCells hc = halo_cells(P, N, tk.x0, tk.y0, flux);
   const V c0v = (V)(p.kappa / (2.0 * P.h * P.h) * (HET ? 1.0 : 2.0));
   const V a_s = (V)src.a_scalar;
-  const int cc = (ty + 1) * kHX + tx + 1;
+  const V w_e = (V)p.w_edge, w_c = (V)p.w_corner;
+  const int b0 = (2 * (tid >> 5)) * kHX + (tid & 31);  // top-left of the thread's 4 x 3 block
   const int nplanes = tk.nz + 2;
+  const long long NN = (long long)N * N;
   double mx = 0.0, s2 = 0.0;
   auto issue = [&](int k) {
     if (k < nplanes) {
       ResStage<V>& S = st[k % D];
       const int zz = tk.z0 - 1 + k;
-      const long long base = (long long)refl(zz, N) * N * N;
+      const long long base = (long long)refl(zz, N) * NN;
+      const V* u = src.u + base;
 #pragma unroll
-      for (int s = 0; s < 2; ++s)
+      for (int s = 0; s < kCells; ++s)
         if (hc.off[s] >= 0) {
-          cp_async_t(&S.u[tid + s * kThreads], src.u + base + hc.off[s]);
+          cp_async_t(&S.u[tid + s * kThreads], u + hc.off[s]);
           if (HET) cp_async_t(&S.s[tid + s * kThreads], src.s + base + hc.off[s]);
         }
-      if (k >= 1 && k <= tk.nz && col) {
-        const long long idx = base + (long long)y * N + x;
-        cp_async_t(&S.f[tid], src.rhs + idx);
-        if (src.a) cp_async_t(&S.a[tid], src.a + idx);
+      if (k >= 1 && k <= tk.nz) {
+#pragma unroll
+        for (int r = 0; r < 2; ++r)
+          if (cl.in[r]) {
+            cp_async_t(&S.f[tid + r * kThreads], src.rhs + base + cl.off[r]);
+            if (src.a) cp_async_t(&S.a[tid + r * kThreads], src.a + base + cl.off[r]);
+          }
       }
     }
     cp_async_commit();
@@ -460,21 +520,31 @@ __device__ void residual3(const KernelParams& p, const TileTask& tk, int c, ResS
       ResStage<V>& S = st[k % D];
       const double gz = z_ghost(P, tk.z0 - 1 + k, N);
 #pragma unroll
-      for (int s = 0; s < 2; ++s)
+      for (int s = 0; s < kCells; ++s)
         if (hc.off[s] >= 0) S.u[tid + s * kThreads] += (V)(hc.ghost[s] + gz);
       __syncthreads();
     }
-    if (k >= 2 && col) {
+    if (k >= 2) {
       const int z = tk.z0 + k - 2;
-      if (!is_fixed<3>(P, N, x, y, z)) {
-        const ResStage<V>* Sp[3] = {&st[(k - 2) % D], &st[(k - 1) % D], &st[k % D]};
-        const V uc = Sp[1]->u[cc];
-        const V sc = HET ? Sp[1]->s[cc] : (V)1;
-        V cls[3];
-        res_sums<V, HET, 3>(uc, sc, Sp, cc, cls);
-        const V sum = cls[0] + (V)p.w_edge * cls[1] + (V)p.w_corner * cls[2];
-        const V a = src.a ? Sp[1]->a[tid] : a_s;
-        res_finish<T, V>(src, c0v, sum, uc, a, Sp[1]->f[tid], scale, R0, RES, ((long long)z * N + y) * N + x, mx, s2);
+      const ResStage<V>& S1 = st[(k - 1) % D];
+      V uc[2], sc[2], cls[2][3];
+#pragma unroll
+      for (int r = 0; r < 2; ++r) {
+        uc[r] = S1.u[b0 + (r + 1) * kHX + 1];
+        sc[r] = HET ? S1.s[b0 + (r + 1) * kHX + 1] : (V)1;
+        cls[r][0] = cls[r][1] = cls[r][2] = (V)0;
+      }
+      res_plane<V, HET>(st[(k - 2) % D], b0, -1, uc, sc, cls);
+      res_plane<V, HET>(S1, b0, 0, uc, sc, cls);
+      res_plane<V, HET>(st[k % D], b0, 1, uc, sc, cls);
+      const bool zf = z_fixed(cl, z, N);
+#pragma unroll
+      for (int r = 0; r < 2; ++r) {
+        if (!cl.in[r] || cl.fixed_xy[r] || zf) continue;
+        const V sum = cls[r][0] + w_e * cls[r][1] + w_c * cls[r][2];
+        const V a = src.a ? S1.a[tid + r * kThreads] : a_s;
+        res_finish<T, V>(src, c0v, sum, uc[r], a, S1.f[tid + r * kThreads], scale, R0, RES,
+                         (long long)z * NN + cl.off[r], mx, s2);
       }
     }
   }
@@ -521,11 +591,11 @@ __device__ __forceinline__ ResSrc<T> recur_src(const KernelParams& p, const Prob
 template <typename T, typename V>
 __device__ void residual2(const KernelParams& p, int c, ResStage<V>* st, bool anchor) {
   constexpr int D = kOuterStages;
-  const int t0 = p.task_off[0], t1 = p.task_off[1];
-  const int tid = threadIdx.x, tx = tid % kTX, ty = tid / kTX;
-  const int cc = (ty + 1) * kHX + tx + 1;
-  const int J = t1 - t0 > (int)blockIdx.x ? (t1 - t0 - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x : 0;
-  auto task = [&](int j) -> const TileTask& { return p.tasks[t0 + blockIdx.x + j * gridDim.x]; };
+  const int* o = p.task_off + blockIdx.x;  // level 0
+  const int t0 = o[0], J = o[1] - o[0];
+  const int tid = threadIdx.x;
+  const int b0 = (2 * (tid >> 5)) * kHX + (tid & 31);
+  auto task = [&](int j) -> const TileTask& { return p.tasks[t0 + j]; };
   auto mine = [&](int b) { return !p.accum[b].done && use_anchor<T>(p, b, c) == anchor; };
   auto source = [&](int b) -> ResSrc<V> {
     if constexpr (sizeof(V) == 8) return anchor_src(p, p.probs[b]);
@@ -537,20 +607,22 @@ __device__ void residual2(const KernelParams& p, int c, ResStage<V>* st, bool an
       if (mine(tk.b)) {
         const ProblemDesc& P = p.probs[tk.b];
         const int N = level_side(P.n, 0);
-        const HaloCells hc = halo_cells(P, N, tk.x0, tk.y0, true);
+        const HaloCells hc = halo_cells(P, N, tk.x0, tk.y0, false);
+        const Columns cl = own_columns(P, N, tk.x0, tk.y0);
         const ResSrc<V> src = source(tk.b);
         ResStage<V>& S = st[j % D];
 #pragma unroll
-        for (int s = 0; s < 2; ++s)
+        for (int s = 0; s < kCells; ++s)
           if (hc.off[s] >= 0) {
             cp_async_t(&S.u[tid + s * kThreads], src.u + hc.off[s]);
             if (src.s) cp_async_t(&S.s[tid + s * kThreads], src.s + hc.off[s]);
           }
-        const int x = tk.x0 + tx, y = tk.y0 + ty;
-        if (x < N && y < N) {
-          cp_async_t(&S.f[tid], src.rhs + (long long)y * N + x);
-          if (src.a) cp_async_t(&S.a[tid], src.a + (long long)y * N + x);
-        }
+#pragma unroll
+        for (int r = 0; r < 2; ++r)
+          if (cl.in[r]) {
+            cp_async_t(&S.f[tid + r * kThreads], src.rhs + cl.off[r]);
+            if (src.a) cp_async_t(&S.a[tid + r * kThreads], src.a + cl.off[r]);
+          }
       }
     }
     cp_async_commit();
@@ -569,23 +641,30 @@ __device__ void residual2(const KernelParams& p, int c, ResStage<V>* st, bool an
     if (src.images && tile_has_flux(P, N, tk.x0, tk.y0, 2)) {
       const HaloCells hc = halo_cells(P, N, tk.x0, tk.y0, true);
 #pragma unroll
-      for (int s = 0; s < 2; ++s)
+      for (int s = 0; s < kCells; ++s)
         if (hc.off[s] >= 0) S.u[tid + s * kThreads] += (V)hc.ghost[s];
       __syncthreads();
     }
-    const int x = tk.x0 + tx, y = tk.y0 + ty;
+    const Columns cl = own_columns(P, N, tk.x0, tk.y0);
     double mx = 0.0, s2 = 0.0;
-    if (x < N && y < N && !is_fixed<2>(P, N, x, y, 0)) {
-      const ResStage<V>* Sp[1] = {&S};
-      const V uc = S.u[cc];
-      V cls[3];
-      if (src.s) res_sums<V, true, 1>(uc, S.s[cc], Sp, cc, cls);
-      else res_sums<V, false, 1>(uc, (V)1, Sp, cc, cls);
-      const V c0v = (V)(p.kappa / (2.0 * P.h * P.h) * (src.s ? 1.0 : 2.0));
-      const V sum = cls[0] + (V)p.w_edge * cls[1];
-      const V a = src.a ? S.a[tid] : (V)src.a_scalar;
-      res_finish<T, V>(src, c0v, sum, uc, a, S.f[tid], cast_scale(p, tk.b, c), (T*)p.R + P.off_lvl[0],
-                       p.RES64 ? p.RES64 + P.off_full : nullptr, (long long)y * N + x, mx, s2);
+    V uc[2], sc[2], cls[2][3];
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      uc[r] = S.u[b0 + (r + 1) * kHX + 1];
+      sc[r] = src.s ? S.s[b0 + (r + 1) * kHX + 1] : (V)1;
+      cls[r][0] = cls[r][1] = cls[r][2] = (V)0;
+    }
+    if (src.s) res_plane<V, true>(S, b0, 0, uc, sc, cls);
+    else res_plane<V, false>(S, b0, 0, uc, sc, cls);
+    const V c0v = (V)(p.kappa / (2.0 * P.h * P.h) * (src.s ? 1.0 : 2.0));
+    const double scale = cast_scale(p, tk.b, c);
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      if (!cl.in[r] || cl.fixed_xy[r]) continue;
+      const V sum = cls[r][0] + (V)p.w_edge * cls[r][1];
+      const V a = src.a ? S.a[tid + r * kThreads] : (V)src.a_scalar;
+      res_finish<T, V>(src, c0v, sum, uc[r], a, S.f[tid + r * kThreads], scale, (T*)p.R + P.off_lvl[0],
+                       p.RES64 ? p.RES64 + P.off_full : nullptr, cl.off[r], mx, s2);
     }
     block_flush(mx, s2, &p.accum[tk.b].rmax_bits[c & 1], &p.accum[tk.b].rsum2[c & 1]);
   }
@@ -684,10 +763,11 @@ __device__ void phase_check(const KernelParams& p, int c) {
 //         = (1 - omega) e_i + q_i (sigma_i CS(e) + CS(sigma e) - r_i / c),  c = kappa / (2 H^2),
 // with CS(v) = sum_o w_o v_{i+o} over the level-l neighbours, q_i = dtau_i c and
 // omega = dtau_i D_i (constant for the Jacobi-scaled step).  3-D: each plane's in-plane face and
-// corner sums are formed once from shared memory and combined across three planes held in
-// registers (faces = F(z) + v(z-1) + v(z+1), edges = C(z) + F(z-1) + F(z+1),
-// corners = C(z-1) + C(z+1)); plane loads run kSweepStages - 2 planes ahead with cp.async.
-// The last sweep of a cycle adds its result, unscaled, to the FP64 solution instead of storing it.
+// corner sums of the thread's two nodes come from one 4 x 3 block of shared memory and are combined
+// across three planes held in registers (faces = F(z) + v(z-1) + v(z+1), edges = C(z) + F(z-1) +
+// F(z+1), corners = C(z-1) + C(z+1)); plane loads run kSweepStages - 2 planes ahead with cp.async.
+// The last sweep of a cycle adds its result, unscaled, to the FP64 solution (and keeps it as the
+// recurrence operand in the mixed form).
 // ---------------------------------------------------------------------------------------------
 template <typename T>
 struct PlaneSums {
@@ -714,33 +794,41 @@ __device__ __forceinline__ SweepCtl sweep_ctl(const KernelParams& p, const Phase
   return s;
 }
 
+// In-plane sums of the thread's two nodes from the 4 x 3 block at b0.
 template <typename T, bool HET>
-__device__ __forceinline__ PlaneSums<T> plane_sums(const SweepStage<T>& S, int cc, bool zero) {
-  PlaneSums<T> ps;
+__device__ __forceinline__ void plane_sums2(const SweepStage<T>& S, int b0, bool zero, PlaneSums<T> ps[2]) {
   if (zero) {
-    ps.v = ps.F = ps.C = ps.sv = ps.sF = ps.sC = (T)0;
-    return ps;
+#pragma unroll
+    for (int r = 0; r < 2; ++r) ps[r].v = ps[r].F = ps[r].C = ps[r].sv = ps[r].sF = ps[r].sC = (T)0;
+    return;
   }
-  const T* E = S.e;
-  ps.v = E[cc];
-  ps.F = (E[cc - 1] + E[cc + 1]) + (E[cc - kHX] + E[cc + kHX]);
-  ps.C = (E[cc - kHX - 1] + E[cc - kHX + 1]) + (E[cc + kHX - 1] + E[cc + kHX + 1]);
-  if (HET) {
-    const T* s = S.s;
-    ps.sv = s[cc] * E[cc];
-    ps.sF = (s[cc - 1] * E[cc - 1] + s[cc + 1] * E[cc + 1]) + (s[cc - kHX] * E[cc - kHX] + s[cc + kHX] * E[cc + kHX]);
-    ps.sC = (s[cc - kHX - 1] * E[cc - kHX - 1] + s[cc - kHX + 1] * E[cc - kHX + 1]) +
-            (s[cc + kHX - 1] * E[cc + kHX - 1] + s[cc + kHX + 1] * E[cc + kHX + 1]);
-  } else {
-    ps.sv = ps.sF = ps.sC = (T)0;
+  T a[4][3], se[4][3];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      a[i][j] = S.e[b0 + i * kHX + j];
+      if (HET) se[i][j] = S.s[b0 + i * kHX + j] * a[i][j];
+    }
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    ps[r].v = a[r + 1][1];
+    ps[r].F = (a[r + 1][0] + a[r + 1][2]) + (a[r][1] + a[r + 2][1]);
+    ps[r].C = (a[r][0] + a[r][2]) + (a[r + 2][0] + a[r + 2][2]);
+    if (HET) {
+      ps[r].sv = se[r + 1][1];
+      ps[r].sF = (se[r + 1][0] + se[r + 1][2]) + (se[r][1] + se[r + 2][1]);
+      ps[r].sC = (se[r][0] + se[r][2]) + (se[r + 2][0] + se[r + 2][2]);
+    } else {
+      ps[r].sv = ps[r].sF = ps[r].sC = (T)0;
+    }
   }
-  return ps;
 }
 
 // Per-task constants of the update: 1 - omega, 1 / c = 2 H^2 / kappa, and q for a homogeneous problem.
 template <typename T>
 struct SweepConst {
-  T one_m_omega, inv_c, q_const;
+  T one_m_omega, inv_c, q_const, w_e, w_c;
 };
 
 template <typename T>
@@ -750,122 +838,136 @@ __device__ __forceinline__ SweepConst<T> sweep_const(const KernelParams& p, cons
   k.one_m_omega = (T)(1.0 - p.omega);
   k.inv_c = (T)(2.0 * H * H / p.kappa);
   k.q_const = (T)P.q_const[l];
+  k.w_e = (T)p.w_edge;
+  k.w_c = (T)p.w_corner;
   return k;
 }
 
 template <typename T, bool HET>
-__device__ __forceinline__ T sweep_update(const SweepConst<T>& k, const SweepStage<T>& S, int cc, T CSe, T CSse,
-                                          T e_c) {
-  const T r_i = S.r[threadIdx.x];
-  if (HET) return k.one_m_omega * e_c + S.q[threadIdx.x] * (S.s[cc] * CSe + CSse - r_i * k.inv_c);
+__device__ __forceinline__ T sweep_update(const SweepConst<T>& k, const SweepStage<T>& S, int slot, int cc, T CSe,
+                                          T CSse, T e_c) {
+  const T r_i = S.r[slot];
+  if (HET) return k.one_m_omega * e_c + S.q[slot] * (S.s[cc] * CSe + CSse - r_i * k.inv_c);
   return k.one_m_omega * e_c + k.q_const * ((T)2 * CSe - r_i * k.inv_c);
 }
 
-template <typename T, bool HET>
-__device__ void sweep3(const KernelParams& p, const Phase& ph, int c, const TileTask& tk, SweepStage<T>* st) {
+template <typename T, bool HET, bool LAST>
+__device__ void sweep3(const KernelParams& p, const Phase& ph, int c, const TileTask& tk, SweepStage<T>* st,
+                       const SweepCtl& sc) {
   constexpr int D = kSweepStages;
-  const SweepCtl sc = sweep_ctl(p, ph, tk.b);
-  if (!sc.active) return;
   const ProblemDesc& P = p.probs[tk.b];
   const int N = sc.N;
-  const int tid = threadIdx.x, tx = tid % kTX, ty = tid / kTX;
-  const int x = tk.x0 + tx, y = tk.y0 + ty;
-  const bool col = x < N && y < N;
+  const int tid = threadIdx.x;
+  const Columns cl = own_columns(P, N, tk.x0, tk.y0);
   const T* src = (ph.sweep & 1) ? (const T*)p.E2 + sc.off : (const T*)p.E + sc.off;
   T* dst = (ph.sweep & 1) ? (T*)p.E + sc.off : (T*)p.E2 + sc.off;
   const T* R = (const T*)p.R + sc.off;
   const T* SG = HET ? (const T*)p.SIG + sc.off : nullptr;
   const T* Q = HET ? (const T*)p.Q + sc.off : nullptr;
-  const double* Ug = p.U + P.off_full;
+  double* Ug = p.U + P.off_full;
   const HaloCells hc = halo_cells(P, N, tk.x0, tk.y0, false);
-  const T w_e = (T)p.w_edge, w_c = (T)p.w_corner;
-  const int cc = (ty + 1) * kHX + tx + 1;
-  const double inv_scale = sc.last ? 1.0 / p.state[tk.b].scale_used[c & 1] : 0.0;
   const SweepConst<T> kc = sweep_const<T>(p, P, ph.level);
+  const int b0 = (2 * (tid >> 5)) * kHX + (tid & 31);
+  const double inv_scale = LAST ? 1.0 / p.state[tk.b].scale_used[c & 1] : 0.0;
+  const bool keep = !LAST || p.mixed;
+  const bool zero_in = sc.zero_in;
   const int nplanes = tk.nz + 2;
+  const long long NN = (long long)N * N;
   auto issue = [&](int k) {
     if (k < nplanes) {
       SweepStage<T>& S = st[k % D];
       const int zz = tk.z0 - 1 + k;
-      const long long base = (long long)refl(zz, N) * N * N;
+      const long long base = (long long)refl(zz, N) * NN;
 #pragma unroll
-      for (int s = 0; s < 2; ++s)
+      for (int s = 0; s < kCells; ++s)
         if (hc.off[s] >= 0) {
-          if (!sc.zero_in) cp_async_t(&S.e[tid + s * kThreads], src + base + hc.off[s]);
+          if (!zero_in) cp_async_t(&S.e[tid + s * kThreads], src + base + hc.off[s]);
           if (HET) cp_async_t(&S.s[tid + s * kThreads], SG + base + hc.off[s]);
         }
-      if (k >= 1 && k <= tk.nz && col) {
-        const long long idx = base + (long long)y * N + x;
-        cp_async_t(&S.r[tid], R + idx);
-        if (HET) cp_async_t(&S.q[tid], Q + idx);
-        if (sc.last) cp_async_t(&S.u[tid], Ug + idx);
+      if (k >= 1 && k <= tk.nz) {
+#pragma unroll
+        for (int r = 0; r < 2; ++r)
+          if (cl.in[r]) {
+            cp_async_t(&S.r[tid + r * kThreads], R + base + cl.off[r]);
+            if (HET) cp_async_t(&S.q[tid + r * kThreads], Q + base + cl.off[r]);
+            if (LAST) cp_async_t(&S.u[tid + r * kThreads], Ug + base + cl.off[r]);
+          }
       }
     }
     cp_async_commit();
   };
   for (int k = 0; k < D - 2; ++k) issue(k);
-  PlaneSums<T> m{}, o{};
+  PlaneSums<T> m[2], o[2], pz[2];
+#pragma unroll
+  for (int r = 0; r < 2; ++r) m[r] = o[r] = PlaneSums<T>{};
   for (int k = 0; k < nplanes; ++k) {
     cp_async_wait<D - 3>();
     __syncthreads();
     issue(k + D - 2);
-    const PlaneSums<T> pz = plane_sums<T, HET>(st[k % D], cc, sc.zero_in);
-    if (k >= 2 && col) {
+    plane_sums2<T, HET>(st[k % D], b0, zero_in, pz);
+    if (k >= 2) {
       const int z = tk.z0 + k - 2;
-      if (!is_fixed<3>(P, N, x, y, z)) {
-        const T CSe = (o.F + m.v + pz.v) + w_e * (o.C + m.F + pz.F) + w_c * (m.C + pz.C);
-        const T CSse = HET ? (o.sF + m.sv + pz.sv) + w_e * (o.sC + m.sF + pz.sF) + w_c * (m.sC + pz.sC) : (T)0;
-        const SweepStage<T>& S = st[(k - 1) % D];
-        const T e_new = sweep_update<T, HET>(kc, S, cc, CSe, CSse, o.v);
-        const long long idx = ((long long)z * N + y) * N + x;
-        if (sc.last) {
-          p.U[P.off_full + idx] = S.u[tid] + (double)e_new * inv_scale;
-          if (p.mixed) dst[idx] = e_new;
-        } else {
-          dst[idx] = e_new;
-        }
+      const bool zf = z_fixed(cl, z, N);
+      const SweepStage<T>& S = st[(k - 1) % D];
+#pragma unroll
+      for (int r = 0; r < 2; ++r) {
+        if (!cl.in[r] || cl.fixed_xy[r] || zf) continue;
+        const T CSe = (o[r].F + m[r].v + pz[r].v) + kc.w_e * (o[r].C + m[r].F + pz[r].F) + kc.w_c * (m[r].C + pz[r].C);
+        const T CSse =
+            HET ? (o[r].sF + m[r].sv + pz[r].sv) + kc.w_e * (o[r].sC + m[r].sF + pz[r].sF) + kc.w_c * (m[r].sC + pz[r].sC)
+                : (T)0;
+        const int slot = tid + r * kThreads;
+        const T e_new = sweep_update<T, HET>(kc, S, slot, b0 + (r + 1) * kHX + 1, CSe, CSse, o[r].v);
+        const long long idx = (long long)z * NN + cl.off[r];
+        if (LAST) Ug[idx] = S.u[slot] + (double)e_new * inv_scale;
+        if (keep) dst[idx] = e_new;
       }
     }
-    m = o;
-    o = pz;
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      m[r] = o[r];
+      o[r] = pz[r];
+    }
   }
   cp_async_wait<0>();
   __syncthreads();
 }
 
 // 2-D: one halo tile per task, the CTA's tasks pipelined kSweepStages - 2 deep.
-template <typename T>
+template <typename T, bool LAST>
 __device__ void sweep2(const KernelParams& p, const Phase& ph, int c, SweepStage<T>* st) {
   constexpr int D = kSweepStages;
   const int l = ph.level;
-  const int t0 = p.task_off[l], t1 = p.task_off[l + 1];
-  const int tid = threadIdx.x, tx = tid % kTX, ty = tid / kTX;
-  const int cc = (ty + 1) * kHX + tx + 1;
-  const int J = t1 - t0 > (int)blockIdx.x ? (t1 - t0 - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x : 0;
-  auto task = [&](int j) -> const TileTask& { return p.tasks[t0 + blockIdx.x + j * gridDim.x]; };
+  const int* o = p.task_off + (long long)l * (gridDim.x + 1) + blockIdx.x;
+  const int t0 = o[0], J = o[1] - o[0];
+  const int tid = threadIdx.x;
+  const int b0 = (2 * (tid >> 5)) * kHX + (tid & 31);
+  auto task = [&](int j) -> const TileTask& { return p.tasks[t0 + j]; };
+  auto mine = [&](const SweepCtl& sc) { return sc.active && sc.last == LAST; };
   auto issue = [&](int j) {
     if (j < J) {
       const TileTask& tk = task(j);
       const SweepCtl sc = sweep_ctl(p, ph, tk.b);
-      if (sc.active) {
+      if (mine(sc)) {
         const ProblemDesc& P = p.probs[tk.b];
         const int N = sc.N;
         const HaloCells hc = halo_cells(P, N, tk.x0, tk.y0, false);
+        const Columns cl = own_columns(P, N, tk.x0, tk.y0);
         SweepStage<T>& S = st[j % D];
         const T* src = (ph.sweep & 1) ? (const T*)p.E2 + sc.off : (const T*)p.E + sc.off;
 #pragma unroll
-        for (int s = 0; s < 2; ++s)
+        for (int s = 0; s < kCells; ++s)
           if (hc.off[s] >= 0) {
             if (!sc.zero_in) cp_async_t(&S.e[tid + s * kThreads], src + hc.off[s]);
             if (P.hetero) cp_async_t(&S.s[tid + s * kThreads], (const T*)p.SIG + sc.off + hc.off[s]);
           }
-        const int x = tk.x0 + tx, y = tk.y0 + ty;
-        if (x < N && y < N) {
-          const long long idx = (long long)y * N + x;
-          cp_async_t(&S.r[tid], (const T*)p.R + sc.off + idx);
-          if (P.hetero) cp_async_t(&S.q[tid], (const T*)p.Q + sc.off + idx);
-          if (sc.last) cp_async_t(&S.u[tid], p.U + P.off_full + idx);
-        }
+#pragma unroll
+        for (int r = 0; r < 2; ++r)
+          if (cl.in[r]) {
+            cp_async_t(&S.r[tid + r * kThreads], (const T*)p.R + sc.off + cl.off[r]);
+            if (P.hetero) cp_async_t(&S.q[tid + r * kThreads], (const T*)p.Q + sc.off + cl.off[r]);
+            if (LAST) cp_async_t(&S.u[tid + r * kThreads], p.U + P.off_full + cl.off[r]);
+          }
       }
     }
     cp_async_commit();
@@ -877,33 +979,26 @@ __device__ void sweep2(const KernelParams& p, const Phase& ph, int c, SweepStage
     issue(j + D - 2);
     const TileTask& tk = task(j);
     const SweepCtl sc = sweep_ctl(p, ph, tk.b);
-    if (!sc.active) continue;
+    if (!mine(sc)) continue;
     const ProblemDesc& P = p.probs[tk.b];
     const int N = sc.N;
-    const int x = tk.x0 + tx, y = tk.y0 + ty;
-    if (x >= N || y >= N || is_fixed<2>(P, N, x, y, 0)) continue;
+    const Columns cl = own_columns(P, N, tk.x0, tk.y0);
     const SweepStage<T>& S = st[j % D];
-    T CSe, CSse = (T)0, e_c;
-    if (P.hetero) {
-      const PlaneSums<T> ps = plane_sums<T, true>(S, cc, sc.zero_in);
-      CSe = ps.F + (T)p.w_edge * ps.C;
-      CSse = ps.sF + (T)p.w_edge * ps.sC;
-      e_c = ps.v;
-    } else {
-      const PlaneSums<T> ps = plane_sums<T, false>(S, cc, sc.zero_in);
-      CSe = ps.F + (T)p.w_edge * ps.C;
-      e_c = ps.v;
-    }
     const SweepConst<T> kc = sweep_const<T>(p, P, l);
-    const T e_new = P.hetero ? sweep_update<T, true>(kc, S, cc, CSe, CSse, e_c)
-                             : sweep_update<T, false>(kc, S, cc, CSe, CSse, e_c);
-    const long long idx = (long long)y * N + x;
+    PlaneSums<T> ps[2];
+    if (P.hetero) plane_sums2<T, true>(S, b0, sc.zero_in, ps);
+    else plane_sums2<T, false>(S, b0, sc.zero_in, ps);
     T* dst = (ph.sweep & 1) ? (T*)p.E + sc.off : (T*)p.E2 + sc.off;
-    if (sc.last) {
-      p.U[P.off_full + idx] = S.u[tid] + (double)e_new * (1.0 / p.state[tk.b].scale_used[c & 1]);
-      if (p.mixed) dst[idx] = e_new;
-    } else {
-      dst[idx] = e_new;
+    const double inv_scale = LAST ? 1.0 / p.state[tk.b].scale_used[c & 1] : 0.0;
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      if (!cl.in[r] || cl.fixed_xy[r]) continue;
+      const T CSe = ps[r].F + kc.w_e * ps[r].C;
+      const int slot = tid + r * kThreads, cc = b0 + (r + 1) * kHX + 1;
+      const T e_new = P.hetero ? sweep_update<T, true>(kc, S, slot, cc, CSe, ps[r].sF + kc.w_e * ps[r].sC, ps[r].v)
+                               : sweep_update<T, false>(kc, S, slot, cc, CSe, (T)0, ps[r].v);
+      if (LAST) p.U[P.off_full + cl.off[r]] = S.u[slot] + (double)e_new * inv_scale;
+      if (!LAST || p.mixed) dst[cl.off[r]] = e_new;
     }
   }
   cp_async_wait<0>();
@@ -914,12 +1009,21 @@ template <typename T, int DIM>
 __device__ void phase_sweep(const KernelParams& p, const Phase& ph, int c, unsigned char* smem) {
   SweepStage<T>* st = (SweepStage<T>*)smem;
   if (DIM == 2) {
-    sweep2<T>(p, ph, c, st);
+    if (ph.flags & kFinalVisit) sweep2<T, true>(p, ph, c, st);  // problems whose last sweep this is
+    sweep2<T, false>(p, ph, c, st);
     return;
   }
   for_tasks(p, ph.level, [&](const TileTask& tk) {
-    if (p.probs[tk.b].hetero) sweep3<T, true>(p, ph, c, tk, st);
-    else sweep3<T, false>(p, ph, c, tk, st);
+    const SweepCtl sc = sweep_ctl(p, ph, tk.b);
+    if (!sc.active) return;
+    const bool het = p.probs[tk.b].hetero != 0;
+    if (sc.last) {
+      if (het) sweep3<T, true, true>(p, ph, c, tk, st, sc);
+      else sweep3<T, false, true>(p, ph, c, tk, st, sc);
+    } else {
+      if (het) sweep3<T, true, false>(p, ph, c, tk, st, sc);
+      else sweep3<T, false, false>(p, ph, c, tk, st, sc);
+    }
   });
 }
 

@@ -16,10 +16,12 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <string>
 
 #include "sgml.h"
 #include "sgml_internal.cuh"
+#include "sgml_tasks.h"
 
 using namespace sgml;
 
@@ -29,10 +31,12 @@ constexpr size_t kNoAllocBytes = 24u << 20;  // 24 MiB of scratch per device
 constexpr int kMaxDevices = 64;
 constexpr int kMaxTasks = 8192;
 constexpr int kMaxPhases = 256;
+constexpr int kMaxToff = kMaxLevels * 1025;  // up to 1024 CTAs
 
 __device__ __align__(256) unsigned char g_scratch[kNoAllocBytes];
 
 thread_local std::string t_error;
+std::mutex g_table_mutex;
 
 int fail(int code, const char* msg) {
   t_error = msg;
@@ -117,7 +121,7 @@ extern "C" int sgml_solve_noalloc(int dim, int n, int precision, const double* f
   const size_t o_sync = bump.take(sizeof(GridSync));
   const size_t o_phases = bump.take(sizeof(Phase) * kMaxPhases);
   const size_t o_tasks = bump.take(sizeof(TileTask) * kMaxTasks);
-  const size_t o_toff = bump.take(sizeof(int) * (kMaxLevels + 1));
+  const size_t o_toff = bump.take(sizeof(int) * kMaxToff);
   const size_t o_rows = bump.take(sizeof(long long) * kMaxLevels * 2);
   const size_t o_hist = bump.take(sizeof(double) * (max_cycles + 1));
   const size_t lvl_bytes = (size_t)elem * lvl;
@@ -144,29 +148,21 @@ extern "C" int sgml_solve_noalloc(int dim, int n, int precision, const double* f
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int blocks = sms * bps;
 
-  TileTask tasks[kMaxTasks];  // host stack, 96 KB
-  int toff[kMaxLevels + 1];
   long long rows[kMaxLevels * 2];
-  int nt = 0;
   for (int l = 0; l < kMaxLevels; ++l) {
-    toff[l] = nt;
     rows[2 * l] = 0;
-    rows[2 * l + 1] = 0;
-    if (l > n - 1) continue;
-    const int N = (int)side(n, l);
-    rows[2 * l + 1] = dim == 3 ? (long long)N * N : N;
-    const long long nxy = (long long)((N + kTX - 1) / kTX) * ((N + kTY - 1) / kTY);
-    const long long nzc = dim == 3 ? std::max(1LL, (long long)std::llround((double)blocks / nxy)) : 1;
-    const int chunk = dim == 3 ? (int)std::max<long long>(2, (N + std::min<long long>(nzc, N) - 1) / std::min<long long>(nzc, N)) : 1;
-    const int zmax = dim == 3 ? N : 1;
-    for (int z0 = 0; z0 < zmax; z0 += chunk)
-      for (int y0 = 0; y0 < N; y0 += kTY)
-        for (int x0 = 0; x0 < N; x0 += kTX) {
-          if (nt >= kMaxTasks) return fail(SGML_ERR_ARG, "problem too large for the no-alloc task table");
-          tasks[nt++] = TileTask{0, (short)x0, (short)y0, (short)z0, (short)std::min(chunk, zmax - z0)};
-        }
+    const long long N = side(n, std::min(l, n - 1));
+    rows[2 * l + 1] = l <= n - 1 ? (dim == 3 ? N * N : N) : 0;
   }
-  toff[kMaxLevels] = nt;
+  // partition tables in static host storage (no allocation); the mutex serialises their use
+  static TileTask tasks[kMaxTasks];
+  static int toff[kMaxToff];
+  std::lock_guard<std::mutex> lock(g_table_mutex);
+  if (blocks > 1024 || partition_bound(dim, &n, 1, blocks) > kMaxTasks)
+    return fail(SGML_ERR_ARG, "problem too large for the no-alloc task table");
+  const int dir_hi = (P.face_type[1] == SGML_DIRICHLET ? 1 : 0) | (P.face_type[3] == SGML_DIRICHLET ? 2 : 0);
+  const int nt = build_partition(dim, &n, &dir_hi, 1, blocks, tasks, toff);
+  const size_t toff_bytes = sizeof(int) * (size_t)kMaxLevels * (blocks + 1);
 
   // schedule of one cycle (Algorithm 3, zig-zag reading, n_r = 2)
   const int n_r = 2;
@@ -214,7 +210,7 @@ extern "C" int sgml_solve_noalloc(int dim, int n, int precision, const double* f
   NA_CUDA(cudaMemcpyAsync(base + o_desc, &P, sizeof(P), cudaMemcpyHostToDevice, stream));
   NA_CUDA(cudaMemcpyAsync(base + o_phases, phases, sizeof(Phase) * np, cudaMemcpyHostToDevice, stream));
   NA_CUDA(cudaMemcpyAsync(base + o_tasks, tasks, sizeof(TileTask) * nt, cudaMemcpyHostToDevice, stream));
-  NA_CUDA(cudaMemcpyAsync(base + o_toff, toff, sizeof(toff), cudaMemcpyHostToDevice, stream));
+  NA_CUDA(cudaMemcpyAsync(base + o_toff, toff, toff_bytes, cudaMemcpyHostToDevice, stream));
   NA_CUDA(cudaMemcpyAsync(base + o_rows, rows, sizeof(rows), cudaMemcpyHostToDevice, stream));
   // the scratch keeps the previous call's contents: clear everything that must start at zero
   NA_CUDA(cudaMemsetAsync(base + o_state, 0, sizeof(ProblemState), stream));
