@@ -339,6 +339,41 @@ def run_gpu(args):
         g.close()
 
 
+def schedule_labels(n, n_r=2):
+    """Labels of the cycle's phases, in the library's order (restriction passes, then the zig-zag
+    visits of Algorithm 3 with their transitions)."""
+    lab = [f"restrict ->{l}" for l in range(1, n)]
+    visits = []
+    for nu1 in range(n - 1, 0, -1):
+        visits += [(nu1, nu1), (nu1 - 1, nu1), (nu1, nu1)]
+    visits.append((0, 0))
+    for q, (lv, tooth) in enumerate(visits):
+        if q:
+            plv = visits[q - 1][0]
+            lab.append(f"prolong {plv}->{lv}" if lv == plv - 1 else f"inject {plv}->{lv}")
+        k = min(n_r, 2 ** (n - tooth))
+        lab += [f"sweep L{lv}"] * (3 * k if q == len(visits) - 1 else k)
+    return lab
+
+
+def run_trace(args, g, n):
+    """Per-phase time inside the persistent kernel, averaged over the traced cycles."""
+    g.set_trace(args.trace_cycles)
+    g.set_params(max_cycles=args.max_cycles)
+    g.solve_to_tol(TOL)
+    t = g.get_trace()
+    lab = ["-", "residual", "check"] + schedule_labels(n)
+    mean = t[1:].mean(axis=0) if len(t) > 1 else t.mean(axis=0)
+    groups = {}
+    for name, v in zip(lab, mean):
+        key = name.split(" ")[0] + (" L0" if name.endswith("L0") or name.endswith("->0") else
+                                    (" L1" if name.endswith("L1") or name.endswith("->1") else ""))
+        groups[key] = groups.get(key, 0.0) + v
+    rows = [{"phase": k, "us_per_cycle": round(v, 1)} for k, v in sorted(groups.items(), key=lambda kv: -kv[1])]
+    print(json.dumps({"trace": True, "n": n, "cycles_traced": int(len(t)), "us_per_cycle_total": round(float(mean.sum()), 1),
+                      "groups": rows, "per_phase_us": [round(float(x), 1) for x in mean]}))
+
+
 def run_ncu_case(args):
     """Small case for ncu: one run_cycle launch of `--ncu-cycles` cycles on the workload."""
     import torch
@@ -352,6 +387,10 @@ def run_ncu_case(args):
         g.set_launch(0, 1, 1)
     sgml.problem_into_grid(g, 0, d)
     g.run_cycle(1)  # warm-up launch (and setup)
+    if args.trace:
+        run_trace(args, g, args.n)
+        g.close()
+        return
     if args.ncu_solve:
         g.set_params(max_cycles=args.max_cycles)
         g.solve_to_tol(TOL)
@@ -385,6 +424,8 @@ def main():
     ap.add_argument("--ncu-cycles", type=int, default=2)
     ap.add_argument("--ncu-solve", action="store_true", help="ncu case: one full solve instead of --ncu-cycles")
     ap.add_argument("--phased", action="store_true")
+    ap.add_argument("--trace", action="store_true", help="with --ncu-case: per-phase times from the kernel's trace")
+    ap.add_argument("--trace-cycles", type=int, default=64)
     args = ap.parse_args()
     args_global = args
     if args.warmup < 3 and args.impl == "gb300" and not args.ncu_case:

@@ -142,6 +142,17 @@ int sgml_sigma_gradient(sgml_grid_t g, int problem, const double* lambda, const 
  * Results do not depend on the launch shape. */
 int sgml_set_launch(sgml_grid_t g, int ctas_per_sm, int z_waves, int mode);
 
+/* Per-phase tracing of the persistent cycle kernel (a profiling aid): with cycles > 0, CTA 0
+ * stamps the GPU global timer after every grid barrier of the first `cycles` cycles of each
+ * launch; 0 turns it off.  Allocates a small device buffer; synchronises. */
+int sgml_set_trace(sgml_grid_t g, int cycles);
+
+/* Durations in microseconds of the traced cycles of the last launch, row-major [cycle][slot] with
+ * *nphases slots per cycle: slot 0 is unused (0), slot 1 the residual phase (anchor or recurrence),
+ * slot 2 the convergence check, slots 3 .. the phases of the cycle's schedule in order.  Each span
+ * includes the grid barrier that ends it.  cap bounds the doubles written.  Synchronises. */
+int sgml_get_trace(sgml_grid_t g, double* us, int cap, int* nphases, int* ncycles);
+
 /* Number of kernel launches the library issued on this grid since creation (every kernel,
  * setup included). */
 int sgml_launch_count(sgml_grid_t g, long long* count);

@@ -66,6 +66,9 @@ struct sgml_grid {
   bool dirty_coeffs = true, dirty_desc = true, dirty_phases = true, dirty_tiles = true, fresh = true;
   long long launches = 0;
   ProblemState* h_state = nullptr;  // pinned
+  unsigned long long* d_trace = nullptr;  // per-phase timestamps (sgml_set_trace)
+  int trace_cycles = 0;
+  int trace_last_cycles = 0;
 };
 
 // ------------------------------------------------------------------------------------------------
@@ -315,6 +318,12 @@ static int launch(sgml_grid* g, int max_cycles, double tol) {
   p.timeout_ns = 2000000000ull;  // 2 s per barrier wait
   p.hist = g->d_hist;
   p.hist_cap = g->hist_cap;
+  p.trace = g->d_trace;
+  p.trace_cycles = g->d_trace ? g->trace_cycles : 0;
+  if (g->d_trace) {
+    SGML_CUDA(cudaMemsetAsync(g->d_trace, 0, sizeof(unsigned long long) * (size_t)g->trace_cycles * (g->nphases + 3), g->stream));
+    g->trace_last_cycles = std::min(g->trace_cycles, max_cycles + 1);
+  }
   p.U = g->U;
   p.F = g->F;
   p.SIG64 = g->SIG64;
@@ -640,6 +649,42 @@ int sgml_set_launch(sgml_grid_t g, int ctas_per_sm, int z_waves, int mode) {
   return SGML_OK;
 }
 
+int sgml_set_trace(sgml_grid_t g, int cycles) {
+  if (!valid(g) || cycles < 0 || cycles > 100000) return fail(SGML_ERR_ARG, "invalid grid or cycles");
+  int st;
+  if ((st = prepare(g)) != SGML_OK) return st;
+  SGML_CUDA(cudaStreamSynchronize(g->stream));
+  if (g->d_trace) SGML_CUDA(cudaFree(g->d_trace));
+  g->d_trace = nullptr;
+  g->trace_cycles = cycles;
+  if (cycles > 0) SGML_CUDA(cudaMalloc(&g->d_trace, sizeof(unsigned long long) * (size_t)cycles * (g->nphases + 3)));
+  return SGML_OK;
+}
+
+int sgml_get_trace(sgml_grid_t g, double* us, int cap, int* nphases, int* ncycles) {
+  if (!valid(g) || !us || !nphases || !ncycles) return fail(SGML_ERR_ARG, "bad arguments");
+  if (g->mode != 0 || !g->d_trace) return fail(SGML_ERR_ARG, "tracing is off (sgml_set_trace) or the grid is in phase mode");
+  SGML_CUDA(cudaStreamSynchronize(g->stream));
+  const int w = g->nphases + 3;
+  std::vector<unsigned long long> t((size_t)g->trace_cycles * w);
+  SGML_CUDA(cudaMemcpy(t.data(), g->d_trace, sizeof(unsigned long long) * t.size(), cudaMemcpyDeviceToHost));
+  // durations: slot k of cycle c is stamp(k) - stamp(k - 1); slot 0 of cycle c spans from the
+  // previous cycle's last stamp (or is 0 for the first cycle)
+  int n = 0;
+  for (int c = 0; c < g->trace_last_cycles && (n + 1) * w <= cap; ++c) {
+    if (t[(size_t)c * w] == 0) break;
+    for (int k = 0; k < w; ++k) {
+      const unsigned long long a = t[(size_t)c * w + k];
+      const unsigned long long prev = k > 0 ? t[(size_t)c * w + k - 1] : 0;
+      us[(size_t)n * w + k] = (a && prev && a >= prev) ? (double)(a - prev) * 1e-3 : 0.0;
+    }
+    ++n;
+  }
+  *nphases = w;
+  *ncycles = n;
+  return SGML_OK;
+}
+
 int sgml_launch_count(sgml_grid_t g, long long* count) {
   if (!valid(g) || !count) return fail(SGML_ERR_ARG, "invalid grid or count NULL");
   *count = g->launches;
@@ -651,7 +696,7 @@ int sgml_destroy(sgml_grid_t g) {
   cudaStreamSynchronize(g->stream);
   void* ptrs[] = {g->U, g->F, g->SIG64, g->A64, g->RES64, g->A0, g->E, g->E2, g->B, g->R, g->SIG, g->Q,
                   g->d_probs, g->d_state, g->d_accum, g->d_sync, g->d_phases, g->d_rows, g->d_tasks,
-                  g->d_task_off, g->d_hist};
+                  g->d_task_off, g->d_hist, g->d_trace};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (g->h_state) cudaFreeHost(g->h_state);

@@ -115,6 +115,8 @@ struct KernelParams {
   unsigned long long timeout_ns;
   double* hist;
   int hist_cap;
+  unsigned long long* trace;  // optional: globaltimer after each barrier, [cycle][2 + nphases]
+  int trace_cycles;
   double *U, *F, *SIG64, *A64;
   double* RES64;   // accumulated FP64 residual of the mixed form (full grid)
   void *E, *E2, *B, *R, *SIG, *Q;

@@ -331,9 +331,16 @@ constexpr size_t sweep_smem_bytes() {
   return sizeof(SweepStage<T>) * kSweepStages;
 }
 constexpr size_t outer_smem_bytes() { return sizeof(ResStage<double>) * kOuterStages; }
+// ProlongStage<T> (defined with the interpolation phase): (kTX/2+1)(kTY/2+1) coarse cells x 2 plus
+// 2 x 2 x kThreads fine values, 4 stages.
+template <typename T>
+constexpr size_t prolong_smem_bytes() {
+  return 4 * (sizeof(T) * 2 * (kTX / 2 + 1) * (kTY / 2 + 1) + sizeof(T) * 4 * kThreads);
+}
 template <typename T>
 constexpr size_t phase_smem_bytes() {
-  return sweep_smem_bytes<T>() > outer_smem_bytes() ? sweep_smem_bytes<T>() : outer_smem_bytes();
+  constexpr size_t a = sweep_smem_bytes<T>() > outer_smem_bytes() ? sweep_smem_bytes<T>() : outer_smem_bytes();
+  return a > prolong_smem_bytes<T>() ? a : prolong_smem_bytes<T>() + 64;
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -449,24 +456,34 @@ __device__ __forceinline__ void res_plane(const ResStage<V>& S, int b0, int dz, 
 }
 
 // Finish one node: r = rhs - opscale * (c0 * sum + a * v_c); store the cast source (and the FP64
-// residual in the mixed form); fold |r| and r^2 into the thread's norms.
+// residual in the mixed form); fold |r| and r^2 into the thread's norms (accumulated in V: FP64 for
+// the anchor, FP32 for the recurrence, whose norms only steer the schedule -- the recurrence then
+// issues three FP64-pipe instructions per node: the widening of delta L e, the FP64 accumulation
+// and the narrowing of r).
+__device__ __forceinline__ float nan_maxf(float a, float b) {
+  if (a != a) return a;
+  if (b != b) return b;
+  return a > b ? a : b;
+}
+
 template <typename T, typename V>
 __device__ __forceinline__ void res_finish(const ResSrc<V>& src, V c0v, V sum, V uc, V a, double rhs, double scale,
-                                           T* R0, double* RES, long long idx, double& mx, double& s2) {
-  double r;
-  if (sizeof(V) == 8) {
-    r = rhs - src.opscale * fma((double)c0v, (double)sum, (double)a * (double)uc);
+                                           T* R0, double* RES, long long idx, V& mx, V& s2) {
+  if constexpr (sizeof(V) == 8) {
+    const double r = rhs - src.opscale * fma((double)c0v, (double)sum, (double)a * (double)uc);
     mx = nan_max(mx, fabs(r));
     s2 = fma(r, r, s2);
+    if (RES) RES[idx] = r;
+    R0[idx] = (T)(r * scale);
   } else {
     const V Lv = fma(c0v, sum, a * uc);
-    r = fma(-src.opscale, (double)Lv, rhs);
-    const float rf = (float)r;  // norms of the recurrence in FP32 (they only steer the schedule)
-    mx = nan_max(mx, (double)fabsf(rf));
-    s2 += (double)(rf * rf);
+    const double r = fma(-src.opscale, (double)Lv, rhs);
+    if (RES) RES[idx] = r;
+    const float rf = (float)r;
+    R0[idx] = (T)(rf * (float)scale);
+    mx = nan_maxf(mx, fabsf(rf));
+    s2 = fmaf(rf, rf, s2);
   }
-  if (RES) RES[idx] = r;
-  R0[idx] = (T)(r * scale);
 }
 
 template <typename T, typename V, bool HET>
@@ -487,7 +504,7 @@ __device__ void residual3(const KernelParams& p, const TileTask& tk, int c, ResS
   const int b0 = (2 * (tid >> 5)) * kHX + (tid & 31);  // top-left of the thread's 4 x 3 block
   const int nplanes = tk.nz + 2;
   const long long NN = (long long)N * N;
-  double mx = 0.0, s2 = 0.0;
+  V mx = (V)0, s2 = (V)0;
   auto issue = [&](int k) {
     if (k < nplanes) {
       ResStage<V>& S = st[k % D];
@@ -550,7 +567,7 @@ __device__ void residual3(const KernelParams& p, const TileTask& tk, int c, ResS
   }
   cp_async_wait<0>();
   __syncthreads();
-  block_flush(mx, s2, &p.accum[tk.b].rmax_bits[c & 1], &p.accum[tk.b].rsum2[c & 1]);
+  block_flush((double)mx, (double)s2, &p.accum[tk.b].rmax_bits[c & 1], &p.accum[tk.b].rsum2[c & 1]);
 }
 
 // Residual sources of problem b in cycle c: the anchor (FP64 solution) or the recurrence (FP32
@@ -646,7 +663,7 @@ __device__ void residual2(const KernelParams& p, int c, ResStage<V>* st, bool an
       __syncthreads();
     }
     const Columns cl = own_columns(P, N, tk.x0, tk.y0);
-    double mx = 0.0, s2 = 0.0;
+    V mx = (V)0, s2 = (V)0;
     V uc[2], sc[2], cls[2][3];
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
@@ -666,7 +683,7 @@ __device__ void residual2(const KernelParams& p, int c, ResStage<V>* st, bool an
       res_finish<T, V>(src, c0v, sum, uc[r], a, S.f[tid + r * kThreads], scale, (T*)p.R + P.off_lvl[0],
                        p.RES64 ? p.RES64 + P.off_full : nullptr, cl.off[r], mx, s2);
     }
-    block_flush(mx, s2, &p.accum[tk.b].rmax_bits[c & 1], &p.accum[tk.b].rsum2[c & 1]);
+    block_flush((double)mx, (double)s2, &p.accum[tk.b].rmax_bits[c & 1], &p.accum[tk.b].rsum2[c & 1]);
   }
   cp_async_wait<0>();
   __syncthreads();
@@ -1075,9 +1092,114 @@ __device__ __forceinline__ T* visit_result(const KernelParams& p, const ProblemD
 }
 
 // Moving one level finer: E_l (+)= I(E_{l+1} - B_{l+1}) on every level-l node (hat-function
-// interpolation between consecutive levels, Algorithm 2's I_lambda).
+// interpolation between consecutive levels, Algorithm 2's I_lambda).  3-D: tiles march over coarse
+// planes; each stage holds one coarse plane of the tile's footprint (17 x 9 coarse nodes, the
+// change formed once per coarse node) and the previous values of the two fine planes it completes
+// (2 cz - 1 from coarse planes cz - 1 and cz, 2 cz from cz alone).
+constexpr int kCX = kTX / 2 + 1, kCY = kTY / 2 + 1, kCoarse = kCX * kCY;
+constexpr int kProlongStages = 4;
+static_assert(kCoarse <= kThreads, "one coarse cell per thread");
+
+template <typename T>
+struct ProlongStage {
+  T d[kCoarse];            // coarse values, then the change (value - B)
+  T b[kCoarse];            // B at the coarse nodes
+  T base[2][2 * kThreads];  // previous fine values of planes 2 cz - 1 and 2 cz at the tile's nodes
+};
+
+static_assert(sizeof(ProlongStage<float>) * kProlongStages <= phase_smem_bytes<float>(), "shared memory");
+static_assert(sizeof(ProlongStage<double>) * kProlongStages <= phase_smem_bytes<double>(), "shared memory");
+
+template <typename T>
+__device__ void prolong3(const KernelParams& p, const Phase& ph, const TileTask& tk, ProlongStage<T>* st) {
+  constexpr int D = kProlongStages;
+  const int l = ph.level;
+  const bool init = (ph.flags & kInit) != 0;
+  const ProblemDesc& P = p.probs[tk.b];
+  const int N = level_side(P.n, l), Nc = level_side(P.n, l + 1);
+  const long long NN = (long long)N * N, NNc = (long long)Nc * Nc;
+  const T* src = visit_result<T>(p, P, ph.tooth, l + 1);
+  const T* Bc = (const T*)p.B + P.off_lvl[l + 1];
+  const T* base = init ? nullptr : visit_result<T>(p, P, ph.prev_tooth, l);
+  T* El = (T*)p.E + P.off_lvl[l];
+  const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
+  const Columns cl = own_columns(P, N, tk.x0, tk.y0);
+  const int cx0 = tk.x0 >> 1, cy0 = tk.y0 >> 1;
+  // coarse footprint cells this thread loads (at most one: kCoarse <= kThreads), clamped inside
+  const int cell_x = tid % kCX, cell_y = tid / kCX;
+  const bool has_cell = tid < kCoarse;
+  const int coff = min(cy0 + cell_y, Nc - 1) * Nc + min(cx0 + cell_x, Nc - 1);
+  // interpolation weights of the thread's column (x) and its two rows (y even, y odd)
+  const int x = tk.x0 + tx;
+  const int lx0 = tx >> 1, lx1 = lx0 + (x & 1);
+  const int zc_first = tk.z0 >> 1;                       // coarse plane of the first fine plane
+  const int zc_last = (tk.z0 + tk.nz - 1 + 1) >> 1;      // coarse plane of the last fine plane's upper corner
+  const int nplanes = zc_last - zc_first + 1;
+  auto fine_in = [&](int z) { return z >= tk.z0 && z < tk.z0 + tk.nz; };
+  auto issue = [&](int k) {
+    if (k < nplanes) {
+      ProlongStage<T>& S = st[k % D];
+      const int cz = zc_first + k;
+      if (has_cell) {
+        cp_async_t(&S.d[tid], src + cz * NNc + coff);
+        if (!init) cp_async_t(&S.b[tid], Bc + cz * NNc + coff);
+      }
+      if (!init) {
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+          const int z = 2 * cz - 1 + j;
+          if (fine_in(z)) {
+#pragma unroll
+            for (int r = 0; r < 2; ++r)
+              if (cl.in[r]) cp_async_t(&S.base[j][tid + r * kThreads], base + z * NN + cl.off[r]);
+          }
+        }
+      }
+    }
+    cp_async_commit();
+  };
+  // interpolated change at the thread's two nodes from one coarse plane
+  auto plane_val = [&](const ProlongStage<T>& S, T out[2]) {
+    const T a0 = S.d[ty * kCX + lx0], a1 = S.d[ty * kCX + lx1];
+    const T b0 = S.d[(ty + 1) * kCX + lx0], b1 = S.d[(ty + 1) * kCX + lx1];
+    const T ra = (x & 1) ? (T)0.5 * (a0 + a1) : a0;
+    const T rb = (x & 1) ? (T)0.5 * (b0 + b1) : b0;
+    out[0] = ra;                    // y even: the coarse row itself
+    out[1] = (T)0.5 * (ra + rb);    // y odd: halfway between two coarse rows
+  };
+  for (int k = 0; k < D - 2; ++k) issue(k);
+  T prev[2] = {(T)0, (T)0};
+  for (int k = 0; k < nplanes; ++k) {
+    cp_async_wait<D - 3>();
+    __syncthreads();
+    issue(k + D - 2);
+    ProlongStage<T>& S = st[k % D];
+    if (!init && has_cell) S.d[tid] -= S.b[tid];
+    __syncthreads();
+    T cur[2];
+    plane_val(S, cur);
+    const int cz = zc_first + k;
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const int z = 2 * cz - 1 + j;  // odd fine plane (between cz - 1 and cz), then the even one (at cz)
+      if (!fine_in(z) || (j == 0 && k == 0)) continue;
+#pragma unroll
+      for (int r = 0; r < 2; ++r) {
+        if (!cl.in[r]) continue;
+        const T v = j == 0 ? (T)0.5 * (prev[r] + cur[r]) : cur[r];
+        const T b = init ? (T)0 : S.base[j][tid + r * kThreads];
+        El[z * NN + cl.off[r]] = b + v;
+      }
+    }
+    prev[0] = cur[0];
+    prev[1] = cur[1];
+  }
+  cp_async_wait<0>();
+  __syncthreads();
+}
+
 template <typename T, int DIM>
-__device__ void phase_prolong(const KernelParams& p, const Phase& ph) {
+__device__ void phase_prolong_rows(const KernelParams& p, const Phase& ph) {
   const int l = ph.level;
   const bool init = (ph.flags & kInit) != 0;
   const int lane = threadIdx.x & 31;
@@ -1110,6 +1232,18 @@ __device__ void phase_prolong(const KernelParams& p, const Phase& ph) {
   });
 }
 
+template <typename T, int DIM>
+__device__ void phase_prolong(const KernelParams& p, const Phase& ph, unsigned char* smem) {
+  if (DIM == 3) {
+    for_tasks(p, ph.level, [&](const TileTask& tk) {
+      if (ph.tooth > p.probs[tk.b].n - 1 || p.accum[tk.b].done) return;
+      prolong3<T>(p, ph, tk, (ProlongStage<T>*)smem);
+    });
+    return;
+  }
+  phase_prolong_rows<T, DIM>(p, ph);
+}
+
 // Moving one level coarser: E_l = B_l = (result at level l-1) on the level-l subset.
 template <typename T, int DIM>
 __device__ void phase_inject(const KernelParams& p, const Phase& ph) {
@@ -1138,7 +1272,7 @@ __device__ __forceinline__ void run_phase(const KernelParams& p, const Phase& ph
   switch (ph.op) {
     case OP_RESTRICT: phase_restrict<T, DIM>(p, ph.level); break;
     case OP_SWEEP: phase_sweep<T, DIM>(p, ph, c, sm); break;
-    case OP_PROLONG: phase_prolong<T, DIM>(p, ph); break;
+    case OP_PROLONG: phase_prolong<T, DIM>(p, ph, sm); break;
     default: phase_inject<T, DIM>(p, ph); break;
   }
 }
@@ -1150,16 +1284,25 @@ __global__ void __launch_bounds__(kThreads, SGML_MIN_CTAS) cycle_kernel(const Ke
     phase_lift<T, DIM>(p);
     if (!grid_sync(p.sync, p.timeout_ns)) return;
   }
+  // Optional trace: CTA 0 stamps the global timer after every barrier of the first cycles.
+  auto stamp = [&](int c, int slot) {
+    if (p.trace && blockIdx.x == 0 && threadIdx.x == 0 && c < p.trace_cycles)
+      p.trace[(long long)c * (p.nphases + 3) + slot] = globaltimer();
+  };
   for (int c = 0;; ++c) {
+    stamp(c, 0);
     phase_outer<T, DIM>(p, c, sm);
     if (!grid_sync(p.sync, p.timeout_ns)) return;
+    stamp(c, 1);
     if (blockIdx.x == 0) phase_check<T, DIM>(p, c);
     if (!grid_sync(p.sync, p.timeout_ns)) return;
+    stamp(c, 2);
     if (!ld_volatile(&p.sync->active[c & 1])) break;
     for (int q = 0; q < p.nphases; ++q) {
       const Phase ph = p.phases[q];
       run_phase<T, DIM>(p, ph, c, sm);
       if (!grid_sync(p.sync, p.timeout_ns)) return;
+      stamp(c, 3 + q);
     }
   }
 }

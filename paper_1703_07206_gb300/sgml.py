@@ -55,6 +55,9 @@ _SIGNATURES = {
     "sgml_sigma_gradient": [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
     "sgml_set_launch": [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int],
     "sgml_launch_count": [ctypes.c_void_p, ctypes.POINTER(ctypes.c_longlong)],
+    "sgml_set_trace": [ctypes.c_void_p, ctypes.c_int],
+    "sgml_get_trace": [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                       ctypes.POINTER(ctypes.c_int)],
     "sgml_destroy": [ctypes.c_void_p],
     "sgml_last_error": [],
     "sgml_solve_noalloc": [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double,
@@ -222,6 +225,16 @@ class Grid:
     def set_launch(self, ctas_per_sm=0, z_waves=1, mode=0):
         """mode 0: one persistent cooperative launch per call; mode 1: one launch per phase."""
         _check(load().sgml_set_launch(self._h, ctas_per_sm, z_waves, mode))
+
+    def set_trace(self, cycles):
+        _check(load().sgml_set_trace(self._h, cycles))
+
+    def get_trace(self, cap=1 << 16):
+        """(cycles x slots) microseconds of the traced cycles of the last launch (see sgml.h)."""
+        buf = (ctypes.c_double * cap)()
+        npx, ncy = ctypes.c_int(), ctypes.c_int()
+        _check(load().sgml_get_trace(self._h, buf, cap, ctypes.byref(npx), ctypes.byref(ncy)))
+        return np.array(buf[: npx.value * ncy.value]).reshape(ncy.value, npx.value)
 
     def launch_count(self):
         c = ctypes.c_longlong()
