@@ -894,57 +894,63 @@ __device__ void sweep3(const KernelParams& p, const Phase& ph, int c, const Tile
     if (k < nplanes) {
       SweepStage<T>& S = st[k % D];
       const int zz = tk.z0 - 1 + k;
-      const long long base = (long long)refl(zz, N) * NN;
+      const unsigned base = (unsigned)refl(zz, N) * (unsigned)NN;
 #pragma unroll
       for (int s = 0; s < kCells; ++s)
         if (hc.off[s] >= 0) {
-          if (!zero_in) cp_async_t(&S.e[tid + s * kThreads], src + base + hc.off[s]);
-          if (HET) cp_async_t(&S.s[tid + s * kThreads], SG + base + hc.off[s]);
+          const unsigned o = base + (unsigned)hc.off[s];
+          if (!zero_in) cp_async_t(&S.e[tid + s * kThreads], src + o);
+          if (HET) cp_async_t(&S.s[tid + s * kThreads], SG + o);
         }
       if (k >= 1 && k <= tk.nz) {
 #pragma unroll
         for (int r = 0; r < 2; ++r)
           if (cl.in[r]) {
-            cp_async_t(&S.r[tid + r * kThreads], R + base + cl.off[r]);
-            if (HET) cp_async_t(&S.q[tid + r * kThreads], Q + base + cl.off[r]);
-            if (LAST) cp_async_t(&S.u[tid + r * kThreads], Ug + base + cl.off[r]);
+            const unsigned o = base + (unsigned)cl.off[r];
+            cp_async_t(&S.r[tid + r * kThreads], R + o);
+            if (HET) cp_async_t(&S.q[tid + r * kThreads], Q + o);
+            if (LAST) cp_async_t(&S.u[tid + r * kThreads], Ug + o);
           }
       }
     }
     cp_async_commit();
   };
   for (int k = 0; k < D - 2; ++k) issue(k);
-  PlaneSums<T> m[2], o[2], pz[2];
-#pragma unroll
-  for (int r = 0; r < 2; ++r) m[r] = o[r] = PlaneSums<T>{};
-  for (int k = 0; k < nplanes; ++k) {
+  // One plane step: wait for plane k, start plane k + D - 2, form its in-plane sums into `nw`,
+  // update the nodes of plane k - 1 from (m, o, nw).  The z loop is unrolled by three so that the
+  // three-plane window rotates by renaming instead of moving registers.
+  auto step = [&](int k, const PlaneSums<T>* m, const PlaneSums<T>* o, PlaneSums<T>* nw) {
     cp_async_wait<D - 3>();
     __syncthreads();
     issue(k + D - 2);
-    plane_sums2<T, HET>(st[k % D], b0, zero_in, pz);
+    plane_sums2<T, HET>(st[k % D], b0, zero_in, nw);
     if (k >= 2) {
       const int z = tk.z0 + k - 2;
       const bool zf = z_fixed(cl, z, N);
       const SweepStage<T>& S = st[(k - 1) % D];
+      const unsigned zoff = (unsigned)z * (unsigned)NN;
 #pragma unroll
       for (int r = 0; r < 2; ++r) {
         if (!cl.in[r] || cl.fixed_xy[r] || zf) continue;
-        const T CSe = (o[r].F + m[r].v + pz[r].v) + kc.w_e * (o[r].C + m[r].F + pz[r].F) + kc.w_c * (m[r].C + pz[r].C);
-        const T CSse =
-            HET ? (o[r].sF + m[r].sv + pz[r].sv) + kc.w_e * (o[r].sC + m[r].sF + pz[r].sF) + kc.w_c * (m[r].sC + pz[r].sC)
-                : (T)0;
+        const T CSe = (o[r].F + m[r].v + nw[r].v) + kc.w_e * (o[r].C + m[r].F + nw[r].F) + kc.w_c * (m[r].C + nw[r].C);
+        const T CSse = HET ? (o[r].sF + m[r].sv + nw[r].sv) + kc.w_e * (o[r].sC + m[r].sF + nw[r].sF) +
+                                 kc.w_c * (m[r].sC + nw[r].sC)
+                           : (T)0;
         const int slot = tid + r * kThreads;
         const T e_new = sweep_update<T, HET>(kc, S, slot, b0 + (r + 1) * kHX + 1, CSe, CSse, o[r].v);
-        const long long idx = (long long)z * NN + cl.off[r];
+        const unsigned idx = zoff + (unsigned)cl.off[r];
         if (LAST) Ug[idx] = S.u[slot] + (double)e_new * inv_scale;
         if (keep) dst[idx] = e_new;
       }
     }
+  };
+  PlaneSums<T> A[2], B[2], C[2];
 #pragma unroll
-    for (int r = 0; r < 2; ++r) {
-      m[r] = o[r];
-      o[r] = pz[r];
-    }
+  for (int r = 0; r < 2; ++r) A[r] = B[r] = C[r] = PlaneSums<T>{};
+  for (int k = 0; k < nplanes; k += 3) {
+    step(k, A, B, C);
+    if (k + 1 < nplanes) step(k + 1, B, C, A);
+    if (k + 2 < nplanes) step(k + 2, C, A, B);
   }
   cp_async_wait<0>();
   __syncthreads();
