@@ -132,10 +132,10 @@ int sgml_residual(sgml_grid_t g, int problem, const double* u, double* r);
  * Returns SGML_ERR_ARG for a problem with a Neumann face.  Synchronises. */
 int sgml_sigma_gradient(sgml_grid_t g, int problem, const double* lambda, const double* u, double* grad);
 
-/* Launch shape of the cycle kernel (256 threads per CTA, 32 x 8 column tiles): ctas_per_sm CTAs
+/* Launch shape of the cycle kernel (256 threads per CTA, 32 x 16 column tiles): ctas_per_sm CTAs
  * per SM (0 = as many as fit; the cooperative launch needs all CTAs resident, so the library clamps
- * to the occupancy limit); z_waves (>= 1): in 3-D each level's columns are cut along z so that every
- * CTA gets about z_waves tiles.  mode 0 (default): every run_cycle / solve_to_tol / residual_norm
+ * to the occupancy limit); z_waves (>= 1): each level's tile-planes are cut into G * z_waves equal
+ * pieces (G = CTAs), piece j going to CTA j mod G (1: one contiguous share per CTA).  mode 0 (default): every run_cycle / solve_to_tol / residual_norm
  * call is one persistent cooperative launch with grid-wide barriers between phases.  mode 1: the
  * same device code with one ordinary launch per phase (for profiling single phases; run_cycle then
  * needs no host synchronisation and can be captured in a CUDA graph).  Used by the autotuner.

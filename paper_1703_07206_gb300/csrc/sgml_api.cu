@@ -173,9 +173,26 @@ static int upload_tiles(sgml_grid* g) {
       const long long rows = (l <= n - 1) ? (g->dim == 3 ? N * N : N) : 0;
       rp[(size_t)l * (g->batch + 1) + b + 1] = rp[(size_t)l * (g->batch + 1) + b] + rows;
     }
-  std::vector<TileTask> tasks((size_t)partition_bound(g->dim, nb.data(), g->batch, g->blocks));
-  std::vector<int> toff((size_t)kMaxLevels * (g->blocks + 1));
-  tasks.resize(build_partition(g->dim, nb.data(), dir_hi.data(), g->batch, g->blocks, tasks.data(), toff.data()));
+  // z_waves equal pieces per CTA: piece j goes to CTA j mod G (z_waves = 1: one contiguous share each)
+  const int G = g->blocks, W = g->z_waves, Gp = G * W;
+  std::vector<TileTask> pieces((size_t)partition_bound(g->dim, nb.data(), g->batch, Gp));
+  std::vector<int> poff((size_t)kMaxLevels * (Gp + 1));
+  pieces.resize(build_partition(g->dim, nb.data(), dir_hi.data(), g->batch, Gp, pieces.data(), poff.data()));
+  std::vector<TileTask> tasks;
+  tasks.reserve(pieces.size());
+  std::vector<int> toff((size_t)kMaxLevels * (G + 1));
+  for (int l = 0; l < kMaxLevels; ++l) {
+    const int* po = poff.data() + (size_t)l * (Gp + 1);
+    int* o = toff.data() + (size_t)l * (G + 1);
+    for (int c = 0; c < G; ++c) {
+      o[c] = (int)tasks.size();
+      for (int w = 0; w < W; ++w) {
+        const int j = c + w * G;
+        for (int t = po[j]; t < po[j + 1]; ++t) tasks.push_back(pieces[t]);
+      }
+    }
+    o[G] = (int)tasks.size();
+  }
   if (g->d_rows) SGML_CUDA(cudaFree(g->d_rows));
   if (g->d_tasks) SGML_CUDA(cudaFree(g->d_tasks));
   if (g->d_task_off) SGML_CUDA(cudaFree(g->d_task_off));

@@ -137,6 +137,7 @@ class Grid:
         _check(lib.sgml_create_grid(dim, self.batch, arr, precision, sptr, ctypes.byref(handle)))
         self._h = handle
         self.precision = precision
+        self.bc = {b: ([DIRICHLET] * (2 * dim), [0.0] * (2 * dim)) for b in range(self.batch)}
 
     def close(self):
         if getattr(self, "_h", None):
@@ -174,6 +175,9 @@ class Grid:
         if values is not None:
             fv = (ctypes.c_double * 6)(*([float(v) for v in values] + [0.0] * (6 - len(values))))
         _check(load().sgml_set_bc(self._h, problem, ft, fv))
+        vals = list(values) if values is not None else [0.0] * len(faces)
+        for b in (range(self.batch) if problem < 0 else [problem]):
+            self.bc[b] = (list(faces), vals)
 
     def run_cycle(self, ncycles=1):
         _check(load().sgml_run_cycle(self._h, ncycles))
