@@ -71,6 +71,7 @@ def _load():
         lib.orc_schedule.restype = I
         lib.orc_lift.argtypes = [P, D]
         lib.orc_residual.argtypes = [P, D, D, D]
+        lib.orc_residual_at.argtypes = [P, D, D, ctypes.POINTER(ctypes.c_long), ctypes.c_long, D]
         lib.orc_max_norm.argtypes = [P, D]
         lib.orc_max_norm.restype = ctypes.c_double
         lib.orc_solve.argtypes = [P, D, ctypes.c_double, I, D, D]
@@ -210,6 +211,16 @@ class Problem:
         r = self._new()
         lib.orc_residual(ctypes.byref(self._c), _ptr(u), _ptr(f), _ptr(r))
         return r
+
+    def residual_at(self, u, f, flat_idx):
+        """f - delta L u at the given flat node indices (0 at fixed nodes)."""
+        lib = _load()
+        u, f = self._arr(u), self._arr(f)
+        idx = np.ascontiguousarray(np.asarray(flat_idx, dtype=np.int64))
+        out = np.zeros(idx.size)
+        lib.orc_residual_at(ctypes.byref(self._c), _ptr(u), _ptr(f), idx.ctypes.data_as(ctypes.POINTER(ctypes.c_long)),
+                            idx.size, _ptr(out))
+        return out
 
     def max_norm(self, v):
         return _load().orc_max_norm(ctypes.byref(self._c), _ptr(self._arr(v)))

@@ -473,6 +473,16 @@ void orc_residual(const orc_problem* p, const double* u, const double* f, double
   }
 }
 
+/* r = f - delta L_0 u at the listed nodes only (flat indices), 0 at fixed nodes: the residual of
+ * Sec. 2 evaluated one node at a time, for checks on grids too large for a full pass. */
+void orc_residual_at(const orc_problem* p, const double* u, const double* f, const long* idx, long count, double* r) {
+  for (long q = 0; q < count; ++q) {
+    int c[3];
+    coords(p, idx[q], c);
+    r[q] = is_dirichlet(p, c) ? 0.0 : f[idx[q]] - op_at(p, 0, p->sigma, p->a, u, c, 1);
+  }
+}
+
 /* Maximum norm over the unknowns. */
 double orc_max_norm(const orc_problem* p, const double* v) {
   long M = nnodes(p);

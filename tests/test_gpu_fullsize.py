@@ -1,0 +1,77 @@
+"""Parity at the full sizes of the workloads, where the oracle cannot solve: the GPU's converged
+solution is checked with the oracle's FP64 residual evaluated node by node at sampled nodes (the
+discrete solution is unique, so a residual at the tolerance pins it), in the launch configuration
+bench.py times (one persistent launch per solve, default shape)."""
+import numpy as np
+import pytest
+
+from oracle.oracle import Problem
+from paper_1703_07206_gb300 import inputs, sgml
+from tests.gpu_helpers import oracle_problem
+
+pytestmark = pytest.mark.gpu
+
+
+def sampled_rel_residual(d, u, count=2000, seed=0):
+    p = oracle_problem(d)
+    rng = np.random.default_rng(seed)
+    idx = rng.choice(u.size, size=count, replace=False)
+    # include the node of the largest |f| and its neighbourhood, where the residual is hardest
+    k = int(np.argmax(np.abs(d["f"])))
+    idx = np.unique(np.concatenate([idx, [k, max(k - 1, 0), min(k + 1, u.size - 1)]]))
+    r = p.residual_at(u, d["f"], idx)
+    return np.abs(r).max() / np.abs(d["f"]).max()
+
+
+@pytest.mark.parametrize("precision", [sgml.MIXED, sgml.FP64])
+def test_dielectric_257_cubed(precision):
+    import torch
+    d = inputs.dielectric_spheres_3d(n=8, seed=2000)
+    g = sgml.Grid(3, [8], precision=precision)
+    g.set_params(max_cycles=400)
+    sgml.problem_into_grid(g, 0, d)
+    st, cyc, rel = g.solve_to_tol(1e-10)
+    assert st == sgml.OK and rel[0] <= 1e-10
+    u = g.get_solution(0)
+    assert sampled_rel_residual(d, u) <= 1e-10 * 1.0001
+
+
+def test_trefoil_513_cubed_three_components_mixed():
+    probs = inputs.trefoil_vorticity_3d(n=9)
+    g = sgml.Grid(3, [9] * 3, precision=sgml.MIXED)
+    g.set_params(max_cycles=100)
+    for b, d in enumerate(probs):
+        sgml.problem_into_grid(g, b, d)
+    st, cyc, rel = g.solve_to_tol(1e-10)
+    assert st == sgml.OK and np.all(rel <= 1e-10)
+    for b, d in enumerate(probs):
+        assert sampled_rel_residual(d, g.get_solution(b), count=500, seed=b) <= 1e-10 * 1.0001
+
+
+def test_adjoint_batch_16_of_129_cubed():
+    import torch
+    from paper_1703_07206_gb300.autograd import SGMLSolve
+    probs = inputs.lognormal_dielectric_batch_3d(count=16, n=7, seed=5000)
+    f0 = torch.tensor(np.stack([d["f"] for d in probs]), device="cuda")
+    s0 = torch.tensor(np.stack([d["sigma"] for d in probs]), device="cuda")
+    grid = sgml.Grid(3, [7] * 16, precision=sgml.FP64)
+    grid.set_params(max_cycles=400)
+    st = torch.tensor(np.stack([d["eps_target"] for d in probs]), device="cuda")
+    ut = SGMLSolve.apply(f0, st, grid, 1e-13, True).detach()
+    sig = s0.clone().requires_grad_(True)
+    u = SGMLSolve.apply(f0, sig, grid, 1e-13, True)
+    (0.5 * ((u - ut) ** 2).sum()).backward()
+    gs = sig.grad.cpu().numpy()
+
+    def J(s):
+        return float(0.5 * ((SGMLSolve.apply(f0, s, grid, 1e-14, True) - ut) ** 2).sum())
+
+    for node in [(0, 64, 64, 64), (5, 40, 70, 90)]:
+        h = 3e-4 * float(s0[node])
+        vals = []
+        for k in (1, -1, 2, -2):
+            x = s0.clone()
+            x[node] += k * h
+            vals.append(J(x))
+        fd = (8 * (vals[0] - vals[1]) - (vals[2] - vals[3])) / (12 * h)
+        assert abs(fd - gs[node]) <= 1e-6 * max(abs(fd), 1e-2 * np.abs(gs[node[0]]).max()), node

@@ -473,3 +473,12 @@ def test_sigma_and_source_gradient_match_finite_differences():
         fm[node] -= step
         fd = (J(sig, fp)[0] - J(sig, fm)[0]) / (2 * step)
         assert abs(fd - lam[node]) <= 1e-6 * max(abs(fd), 1e-3 * np.abs(lam).max())
+
+
+def test_sampled_residual_equals_full_residual():
+    d = inputs.random_problem(3, 3, seed=61, flux=True)
+    p = Problem(3, 3, faces=d["faces"], values=d["values"], sigma=d["sigma"], a=d["a"])
+    u = np.random.default_rng(62).standard_normal(p.shape)
+    full = p.residual(u, d["f"]).ravel()
+    idx = np.random.default_rng(63).choice(full.size, size=50, replace=False)
+    assert np.array_equal(p.residual_at(u, d["f"], idx), full[idx])
