@@ -191,6 +191,7 @@ def make_grid(d, precision, stream):
     from paper_1703_07206_gb300 import sgml
     g = sgml.Grid(3, [d["n"]], precision=precision, stream=stream)
     g.set_params(max_cycles=args_global.max_cycles)
+    g.set_launch(0, 1, 0, args_global.tile_x)
     return g
 
 
@@ -324,6 +325,7 @@ def run_gpu(args):
             "vs_baseline": None, "dtype": "f32+f64" if forms[0] == "mixed" else "f64", "data": "synthetic",
             "config": {"workload": workload_name(n), "form": forms[0], "nodes": M, "cycles": main["cycles"],
                        "rel_residual": main["rel"], "l2": "inputs larger than L2 (working set > 1 GB per replica)",
+                       "tile": f"{args.tile_x}x{512 // args.tile_x}",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
             "roofline": main["roofline"], "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": int(round(main["launches_per_step"] * main["steps"])), "clocks": main["clocks"]}
@@ -383,8 +385,7 @@ def run_ncu_case(args):
     d = inputs.dielectric_spheres_3d(n=args.n, seed=2000)
     prec = sgml.MIXED if args.form in ("mixed", "both") else sgml.FP64
     g = sgml.Grid(3, [args.n], precision=prec)
-    if args.phased:
-        g.set_launch(0, 1, 1)
+    g.set_launch(0, 1, 1 if args.phased else 0, args.tile_x)
     sgml.problem_into_grid(g, 0, d)
     g.run_cycle(1)  # warm-up launch (and setup)
     if args.trace:
@@ -424,6 +425,7 @@ def main():
     ap.add_argument("--ncu-cycles", type=int, default=2)
     ap.add_argument("--ncu-solve", action="store_true", help="ncu case: one full solve instead of --ncu-cycles")
     ap.add_argument("--phased", action="store_true")
+    ap.add_argument("--tile-x", type=int, default=64, choices=[32, 64], help="column tiles 32 x 16 or 64 x 8")
     ap.add_argument("--trace", action="store_true", help="with --ncu-case: per-phase times from the kernel's trace")
     ap.add_argument("--trace-cycles", type=int, default=64)
     args = ap.parse_args()

@@ -132,15 +132,16 @@ int sgml_residual(sgml_grid_t g, int problem, const double* u, double* r);
  * Returns SGML_ERR_ARG for a problem with a Neumann face.  Synchronises. */
 int sgml_sigma_gradient(sgml_grid_t g, int problem, const double* lambda, const double* u, double* grad);
 
-/* Launch shape of the cycle kernel (256 threads per CTA, 32 x 16 column tiles): ctas_per_sm CTAs
- * per SM (0 = as many as fit; the cooperative launch needs all CTAs resident, so the library clamps
- * to the occupancy limit); z_waves (>= 1): each level's tile-planes are cut into G * z_waves equal
- * pieces (G = CTAs), piece j going to CTA j mod G (1: one contiguous share per CTA).  mode 0 (default): every run_cycle / solve_to_tol / residual_norm
- * call is one persistent cooperative launch with grid-wide barriers between phases.  mode 1: the
- * same device code with one ordinary launch per phase (for profiling single phases; run_cycle then
- * needs no host synchronisation and can be captured in a CUDA graph).  Used by the autotuner.
- * Results do not depend on the launch shape. */
-int sgml_set_launch(sgml_grid_t g, int ctas_per_sm, int z_waves, int mode);
+/* Launch shape of the cycle kernel (256 threads per CTA): tile_x selects the column tiles the tiled
+ * phases work on, 32 (32 x 16 columns) or 64 (64 x 8 columns, the default); ctas_per_sm CTAs per SM
+ * (0 = as many as fit; the cooperative launch needs all CTAs resident, so the library clamps to the
+ * occupancy limit); z_waves (>= 1): each level's tile-planes are cut into G * z_waves equal pieces
+ * (G = CTAs), piece j going to CTA j mod G (1: one contiguous share per CTA).  mode 0 (default):
+ * every run_cycle / solve_to_tol / residual_norm call is one persistent cooperative launch with
+ * grid-wide barriers between phases.  mode 1: the same device code with one ordinary launch per
+ * phase (for profiling single phases; run_cycle then needs no host synchronisation and can be
+ * captured in a CUDA graph).  Used by the autotuner.  Results do not depend on the launch shape. */
+int sgml_set_launch(sgml_grid_t g, int ctas_per_sm, int z_waves, int mode, int tile_x);
 
 /* Per-phase tracing of the persistent cycle kernel (a profiling aid): with cycles > 0, CTA 0
  * stamps the GPU global timer after every grid barrier of the first `cycles` cycles of each

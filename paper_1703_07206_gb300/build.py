@@ -1,7 +1,8 @@
 """Build libsgml.so (CUDA, sm_103a) in-tree with nvcc.
 
-The two translation units are compiled in parallel and linked into
-``paper_1703_07206_gb300/_build/libsgml.so``.  Cross-compiles without a GPU.
+The kernel unit is compiled once per column-tile width (32 x 16 and 64 x 8 tiles, namespaces
+``sgml_t32`` / ``sgml_t64``), the host units once; the four objects are compiled in parallel and
+linked into ``paper_1703_07206_gb300/_build/libsgml.so``.  Cross-compiles without a GPU.
 """
 from __future__ import annotations
 
@@ -16,7 +17,13 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libsgml.so")
-SOURCES = ["sgml_kernels.cu", "sgml_api.cu", "sgml_noalloc.cu"]
+# (source, object tag, extra defines): the cycle kernels are compiled once per tile width
+UNITS = [
+    ("sgml_kernels.cu", "k32", ["SGML_TILE_X=32", "SGML_KNS=sgml_t32"]),
+    ("sgml_kernels.cu", "k64", ["SGML_TILE_X=64", "SGML_KNS=sgml_t64", "SGML_DEFINE_COMMON"]),
+    ("sgml_api.cu", "api", []),
+    ("sgml_noalloc.cu", "noalloc", []),
+]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -49,13 +56,14 @@ def build(force: bool = False, verbose: bool = False, defines=(), out: str | Non
         flags += ["-Xptxas", "-v"]
     flags += [f"-D{d}" for d in defines]
 
-    def compile_one(src):
-        obj = os.path.join(BUILD, src.replace(".cu", f".{os.getpid()}.{abs(hash(lib))}.o"))
-        subprocess.run([cc, *flags, "-c", os.path.join(CSRC, src), "-o", obj], check=True)
+    def compile_one(unit):
+        src, tag, defs = unit
+        obj = os.path.join(BUILD, f"{tag}.{os.getpid()}.{abs(hash(lib))}.o")
+        subprocess.run([cc, *flags, *[f"-D{d}" for d in defs], "-c", os.path.join(CSRC, src), "-o", obj], check=True)
         return obj
 
-    with ThreadPoolExecutor(len(SOURCES)) as ex:
-        objs = list(ex.map(compile_one, SOURCES))
+    with ThreadPoolExecutor(len(UNITS)) as ex:
+        objs = list(ex.map(compile_one, UNITS))
     tmp = lib + f".tmp{os.getpid()}"
     subprocess.run([cc, *ARCH, "-shared", "-o", tmp, *objs], check=True)
     os.replace(tmp, lib)

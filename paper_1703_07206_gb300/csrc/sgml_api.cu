@@ -62,6 +62,7 @@ struct sgml_grid {
   int stencil = SGML_STENCIL_CONSISTENT;
   int max_cycles = 200;
   int threads = kThreads, ctas_per_sm = 0, blocks = 0, z_waves = 1;
+  int tile_x = 64;  // 32 (32 x 16 tiles) or 64 (64 x 8 tiles)
   int mode = 0;  // 0: one persistent cooperative launch per call, 1: one launch per phase
   bool dirty_coeffs = true, dirty_desc = true, dirty_phases = true, dirty_tiles = true, fresh = true;
   long long launches = 0;
@@ -70,6 +71,20 @@ struct sgml_grid {
   int trace_cycles = 0;
   int trace_last_cycles = 0;
 };
+
+// Tiled kernels of the grid's tile width.
+static cudaError_t launch_cycle(sgml_grid* g, const KernelParams& p) {
+  return g->tile_x == 32 ? sgml_t32::launch_cycle_kernel(p, g->mixed, g->dim, g->blocks, kThreads, g->stream)
+                         : sgml_t64::launch_cycle_kernel(p, g->mixed, g->dim, g->blocks, kThreads, g->stream);
+}
+static cudaError_t launch_phase(sgml_grid* g, const KernelParams& p, int which, int c) {
+  return g->tile_x == 32 ? sgml_t32::launch_phase_kernel(p, g->mixed, g->dim, g->blocks, kThreads, which, c, g->stream)
+                         : sgml_t64::launch_phase_kernel(p, g->mixed, g->dim, g->blocks, kThreads, which, c, g->stream);
+}
+static int occupancy(sgml_grid* g, int* bps) {
+  return g->tile_x == 32 ? sgml_t32::cycle_kernel_occupancy(g->mixed, g->dim, kThreads, bps)
+                         : sgml_t64::cycle_kernel_occupancy(g->mixed, g->dim, kThreads, bps);
+}
 
 // ------------------------------------------------------------------------------------------------
 // Constants of the radial stencil (Eq. 5)
@@ -156,7 +171,7 @@ static int upload_phases(sgml_grid* g) {
 // z_waves tiles per CTA) and the prefix of node rows per level.
 static int upload_tiles(sgml_grid* g) {
   int bps = 0;
-  if (cycle_kernel_occupancy(g->mixed, g->dim, kThreads, &bps) != 0 || bps < 1)
+  if (occupancy(g, &bps) != 0 || bps < 1)
     return fail(SGML_ERR_CUDA, "occupancy query failed for the cycle kernel");
   if (g->ctas_per_sm > 0) bps = std::min(bps, g->ctas_per_sm);
   g->blocks = g->sms * bps;
@@ -175,9 +190,10 @@ static int upload_tiles(sgml_grid* g) {
     }
   // z_waves equal pieces per CTA: piece j goes to CTA j mod G (z_waves = 1: one contiguous share each)
   const int G = g->blocks, W = g->z_waves, Gp = G * W;
-  std::vector<TileTask> pieces((size_t)partition_bound(g->dim, nb.data(), g->batch, Gp));
+  const int tx = g->tile_x, ty = 2 * kThreads / g->tile_x;
+  std::vector<TileTask> pieces((size_t)partition_bound(g->dim, nb.data(), g->batch, Gp, tx, ty));
   std::vector<int> poff((size_t)kMaxLevels * (Gp + 1));
-  pieces.resize(build_partition(g->dim, nb.data(), dir_hi.data(), g->batch, Gp, pieces.data(), poff.data()));
+  pieces.resize(build_partition(g->dim, nb.data(), dir_hi.data(), g->batch, Gp, tx, ty, pieces.data(), poff.data()));
   std::vector<TileTask> tasks;
   tasks.reserve(pieces.size());
   std::vector<int> toff((size_t)kMaxLevels * (G + 1));
@@ -354,13 +370,13 @@ static int launch(sgml_grid* g, int max_cycles, double tol) {
   p.SIG = g->SIG;
   p.Q = g->Q;
   if (g->mode == 0) {
-    SGML_CUDA(launch_cycle_kernel(p, g->mixed, g->dim, g->blocks, g->threads, g->stream));
+    SGML_CUDA(launch_cycle(g, p));
     g->launches++;
   } else {
     // one launch per phase: the same device code, kernel boundaries instead of grid barriers
     auto one = [&](int which, int c) -> cudaError_t {
       g->launches++;
-      return launch_phase_kernel(p, g->mixed, g->dim, g->blocks, g->threads, which, c, g->stream);
+      return launch_phase(g, p, which, c);
     };
     if (fresh) SGML_CUDA(one(-3, 0));
     for (int c = 0;; ++c) {
@@ -655,13 +671,14 @@ int sgml_sigma_gradient(sgml_grid_t g, int problem, const double* lambda, const 
   return SGML_OK;
 }
 
-int sgml_set_launch(sgml_grid_t g, int ctas_per_sm, int z_waves, int mode) {
+int sgml_set_launch(sgml_grid_t g, int ctas_per_sm, int z_waves, int mode, int tile_x) {
   if (!valid(g)) return fail(SGML_ERR_ARG, "invalid grid");
-  if (ctas_per_sm < 0 || z_waves < 1 || z_waves > 64 || (mode != 0 && mode != 1))
-    return fail(SGML_ERR_ARG, "ctas_per_sm >= 0, z_waves in 1..64, mode 0 or 1");
+  if (ctas_per_sm < 0 || z_waves < 1 || z_waves > 64 || (mode != 0 && mode != 1) || (tile_x != 32 && tile_x != 64))
+    return fail(SGML_ERR_ARG, "ctas_per_sm >= 0, z_waves in 1..64, mode 0 or 1, tile_x 32 or 64");
   g->ctas_per_sm = ctas_per_sm;
   g->z_waves = z_waves;
   g->mode = mode;
+  g->tile_x = tile_x;
   g->dirty_tiles = true;
   return SGML_OK;
 }

@@ -87,7 +87,9 @@ struct GridSync {
 // Work unit of the tiled phases.  3-D: the kTX x kTY columns starting at (x0, y0) of one level of
 // problem b, planes z0 .. z0 + nz - 1 (the CTA marches in z).  2-D: the kTX x kTY nodes at (x0, y0).
 // A CTA of kThreads threads covers a tile, two vertically adjacent columns per thread.
-constexpr int kTX = 32, kTY = 16, kThreads = 256;
+// The kernels are compiled once per tile width (namespaces sgml_t32: 32 x 16 tiles, sgml_t64: 64 x 8
+// tiles; kTY = 2 * kThreads / kTX); the host picks one per grid (sgml_set_launch, autotuner).
+constexpr int kThreads = 256;
 struct TileTask {
   int b;
   short x0, y0, z0, nz;
@@ -123,12 +125,7 @@ struct KernelParams {
   void* A0;        // per-node a at level 0 in cycle precision (recurrence operand)
 };
 
-// Host-side launchers (sgml_kernels.cu)
-cudaError_t launch_cycle_kernel(const KernelParams& p, int precision_mixed, int dim, int blocks,
-                                int threads, cudaStream_t s);
-cudaError_t launch_phase_kernel(const KernelParams& p, int precision_mixed, int dim, int blocks, int threads,
-                                int which, int c, cudaStream_t s);
-int cycle_kernel_occupancy(int precision_mixed, int dim, int threads, int* blocks_per_sm);
+// Host-side launchers of the tile-independent kernels (defined once, in the 64-wide kernel unit).
 cudaError_t launch_setup_level(int mixed, int dim, const ProblemDesc& P, int level, const double* sig_l,
                                const double* a_l, double kappa, double w_edge, double w_corner,
                                double theta_gain, void* SIG_T, void* Q_T, void* A_T, cudaStream_t s);
@@ -141,3 +138,15 @@ cudaError_t launch_sigma_gradient(int dim, const ProblemDesc& P, const double* l
 cudaError_t launch_fill(double* dst, long long n, double v, cudaStream_t s);
 
 }  // namespace sgml
+
+// Launchers of the tiled cycle kernels, one set per tile width.
+#define SGML_TILED_LAUNCHERS(NS)                                                                          \
+  namespace NS {                                                                                        \
+  cudaError_t launch_cycle_kernel(const sgml::KernelParams& p, int precision_mixed, int dim, int blocks,  \
+                                  int threads, cudaStream_t s);                                          \
+  cudaError_t launch_phase_kernel(const sgml::KernelParams& p, int precision_mixed, int dim, int blocks,  \
+                                  int threads, int which, int c, cudaStream_t s);                        \
+  int cycle_kernel_occupancy(int precision_mixed, int dim, int threads, int* blocks_per_sm);            \
+  }
+SGML_TILED_LAUNCHERS(sgml_t32)
+SGML_TILED_LAUNCHERS(sgml_t64)

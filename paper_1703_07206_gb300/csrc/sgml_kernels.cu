@@ -19,7 +19,16 @@
 
 #include "sgml_internal.cuh"
 
-namespace sgml {
+#ifndef SGML_TILE_X
+#define SGML_TILE_X 64
+#endif
+#ifndef SGML_KNS
+#define SGML_KNS sgml_t64
+#endif
+
+namespace SGML_KNS {
+using namespace sgml;
+constexpr int kTX = SGML_TILE_X, kTY = 2 * (kThreads / kTX);
 
 // ---------------------------------------------------------------------------------------------
 // Small helpers
@@ -226,11 +235,11 @@ struct Columns {
 
 __device__ __forceinline__ Columns own_columns(const ProblemDesc& P, int N, int x0, int y0) {
   Columns cl;
-  const int x = x0 + (threadIdx.x & 31);
+  const int x = x0 + (int)(threadIdx.x % kTX);
   const bool fx = (x == 0 && P.face_type[0] == 0) || (x == N - 1 && P.face_type[1] == 0);
 #pragma unroll
   for (int r = 0; r < 2; ++r) {
-    const int y = y0 + 2 * (threadIdx.x >> 5) + r;
+    const int y = y0 + 2 * (int)(threadIdx.x / kTX) + r;
     cl.in[r] = x < N && y < N;
     cl.off[r] = y * N + x;
     cl.fixed_xy[r] = fx || (y == 0 && P.face_type[2] == 0) || (y == N - 1 && P.face_type[3] == 0);
@@ -501,7 +510,7 @@ __device__ void residual3(const KernelParams& p, const TileTask& tk, int c, ResS
   const V c0v = (V)(p.kappa / (2.0 * P.h * P.h) * (HET ? 1.0 : 2.0));
   const V a_s = (V)src.a_scalar;
   const V w_e = (V)p.w_edge, w_c = (V)p.w_corner;
-  const int b0 = (2 * (tid >> 5)) * kHX + (tid & 31);  // top-left of the thread's 4 x 3 block
+  const int b0 = (2 * (tid / kTX)) * kHX + (tid % kTX);  // top-left of the thread's 4 x 3 block
   const int nplanes = tk.nz + 2;
   const long long NN = (long long)N * N;
   V mx = (V)0, s2 = (V)0;
@@ -611,7 +620,7 @@ __device__ void residual2(const KernelParams& p, int c, ResStage<V>* st, bool an
   const int* o = p.task_off + blockIdx.x;  // level 0
   const int t0 = o[0], J = o[1] - o[0];
   const int tid = threadIdx.x;
-  const int b0 = (2 * (tid >> 5)) * kHX + (tid & 31);
+  const int b0 = (2 * (tid / kTX)) * kHX + (tid % kTX);
   auto task = [&](int j) -> const TileTask& { return p.tasks[t0 + j]; };
   auto mine = [&](int b) { return !p.accum[b].done && use_anchor<T>(p, b, c) == anchor; };
   auto source = [&](int b) -> ResSrc<V> {
@@ -884,7 +893,7 @@ __device__ void sweep3(const KernelParams& p, const Phase& ph, int c, const Tile
   double* Ug = p.U + P.off_full;
   const HaloCells hc = halo_cells(P, N, tk.x0, tk.y0, false);
   const SweepConst<T> kc = sweep_const<T>(p, P, ph.level);
-  const int b0 = (2 * (tid >> 5)) * kHX + (tid & 31);
+  const int b0 = (2 * (tid / kTX)) * kHX + (tid % kTX);
   const double inv_scale = LAST ? 1.0 / p.state[tk.b].scale_used[c & 1] : 0.0;
   const bool keep = !LAST || p.mixed;
   const bool zero_in = sc.zero_in;
@@ -964,7 +973,7 @@ __device__ void sweep2(const KernelParams& p, const Phase& ph, int c, SweepStage
   const int* o = p.task_off + (long long)l * (gridDim.x + 1) + blockIdx.x;
   const int t0 = o[0], J = o[1] - o[0];
   const int tid = threadIdx.x;
-  const int b0 = (2 * (tid >> 5)) * kHX + (tid & 31);
+  const int b0 = (2 * (tid / kTX)) * kHX + (tid % kTX);
   auto task = [&](int j) -> const TileTask& { return p.tasks[t0 + j]; };
   auto mine = [&](const SweepCtl& sc) { return sc.active && sc.last == LAST; };
   auto issue = [&](int j) {
@@ -1128,7 +1137,7 @@ __device__ void prolong3(const KernelParams& p, const Phase& ph, const TileTask&
   const T* Bc = (const T*)p.B + P.off_lvl[l + 1];
   const T* base = init ? nullptr : visit_result<T>(p, P, ph.prev_tooth, l);
   T* El = (T*)p.E + P.off_lvl[l];
-  const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
+  const int tid = threadIdx.x, tx = tid % kTX, ty = tid / kTX;
   const Columns cl = own_columns(P, N, tk.x0, tk.y0);
   const int cx0 = tk.x0 >> 1, cy0 = tk.y0 >> 1;
   // coarse footprint cells this thread loads (at most one: kCoarse <= kThreads), clamped inside
@@ -1525,6 +1534,11 @@ __global__ void fill_kernel(double* dst, long long n, double v) {
     dst[t] = v;
 }
 
+}  // namespace SGML_KNS
+
+#ifdef SGML_DEFINE_COMMON
+namespace sgml {
+using namespace SGML_KNS;
 static int grid_for(long long M) {
   long long b = (M + 255) / 256;
   return (int)(b < 152 * 16 ? (b > 0 ? b : 1) : 152 * 16);
@@ -1584,3 +1598,4 @@ cudaError_t launch_fill(double* dst, long long n, double v, cudaStream_t s) {
 }
 
 }  // namespace sgml
+#endif

@@ -141,7 +141,7 @@ extern "C" int sgml_solve_noalloc(int dim, int n, int precision, const double* f
 
   // ---- host-side tables (stack memory) ------------------------------------------------------
   int bps = 0;
-  if (cycle_kernel_occupancy(mixed ? 1 : 0, dim, kThreads, &bps) != 0 || bps < 1)
+  if (sgml_t64::cycle_kernel_occupancy(mixed ? 1 : 0, dim, kThreads, &bps) != 0 || bps < 1)
     return fail(SGML_ERR_CUDA, "occupancy query failed");
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
@@ -158,10 +158,11 @@ extern "C" int sgml_solve_noalloc(int dim, int n, int precision, const double* f
   static TileTask tasks[kMaxTasks];
   static int toff[kMaxToff];
   std::lock_guard<std::mutex> lock(g_table_mutex);
-  if (blocks > 1024 || partition_bound(dim, &n, 1, blocks) > kMaxTasks)
+  constexpr int kTX = 64, kTY = 2 * kThreads / 64;  // the 64 x 8 tile kernels
+  if (blocks > 1024 || partition_bound(dim, &n, 1, blocks, kTX, kTY) > kMaxTasks)
     return fail(SGML_ERR_ARG, "problem too large for the no-alloc task table");
   const int dir_hi = (P.face_type[1] == SGML_DIRICHLET ? 1 : 0) | (P.face_type[3] == SGML_DIRICHLET ? 2 : 0);
-  const int nt = build_partition(dim, &n, &dir_hi, 1, blocks, tasks, toff);
+  const int nt = build_partition(dim, &n, &dir_hi, 1, blocks, kTX, kTY, tasks, toff);
   const size_t toff_bytes = sizeof(int) * (size_t)kMaxLevels * (blocks + 1);
 
   // schedule of one cycle (Algorithm 3, zig-zag reading, n_r = 2)
@@ -272,7 +273,7 @@ extern "C" int sgml_solve_noalloc(int dim, int n, int precision, const double* f
   p.SIG = sigma ? base + o_SIG : nullptr;
   p.Q = sigma ? base + o_Q : nullptr;
   p.A0 = nullptr;
-  NA_CUDA(launch_cycle_kernel(p, mixed ? 1 : 0, dim, blocks, kThreads, stream));
+  NA_CUDA(sgml_t64::launch_cycle_kernel(p, mixed ? 1 : 0, dim, blocks, kThreads, stream));
 
   ProblemState S;
   GridSync G;

@@ -1,4 +1,4 @@
-// sgml_tasks.h -- host-side work partition of the tiled phases (used by sgml_api.cu and
+// sgml_tasks.h -- host-side work partition of the tiled phases (tiles of kTX x kTY columns) (used by sgml_api.cu and
 // sgml_noalloc.cu).  For every level, the column tiles of all problems are cut along z into
 // contiguous pieces so that each of the G CTAs of the persistent kernel receives the same number of
 // tile-planes; CTA c owns tasks[off[l * (G + 1) + c] .. off[l * (G + 1) + c + 1]).  A tile costs the
@@ -24,7 +24,7 @@ inline bool tile_all_fixed(int N, int x0, int y0, int dir_hi) {
   return (x0 == N - 1 && (dir_hi & 1)) || (y0 == N - 1 && (dir_hi & 2));
 }
 
-inline long long partition_bound(int dim, const int* n_of_b, int batch, int G) {
+inline long long partition_bound(int dim, const int* n_of_b, int batch, int G, int kTX, int kTY) {
   long long tiles = 0;
   for (int b = 0; b < batch; ++b)
     for (int l = 0; l <= n_of_b[b] - 1; ++l) {
@@ -35,8 +35,8 @@ inline long long partition_bound(int dim, const int* n_of_b, int batch, int G) {
   return tiles + (long long)kMaxLevels * G + (dim == 3 ? 0 : 0);
 }
 
-inline int build_partition(int dim, const int* n_of_b, const int* dir_hi, int batch, int G, TileTask* tasks,
-                           int* off) {
+inline int build_partition(int dim, const int* n_of_b, const int* dir_hi, int batch, int G, int kTX, int kTY,
+                           TileTask* tasks, int* off) {
   int nt = 0;
   for (int k = 0; k < kMaxLevels * (G + 1); ++k) off[k] = 0;
   for (int l = 0; l < kMaxLevels; ++l) {

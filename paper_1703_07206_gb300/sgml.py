@@ -53,7 +53,7 @@ _SIGNATURES = {
                          ctypes.POINTER(ctypes.c_int)],
     "sgml_residual": [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p],
     "sgml_sigma_gradient": [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
-    "sgml_set_launch": [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int],
+    "sgml_set_launch": [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int],
     "sgml_launch_count": [ctypes.c_void_p, ctypes.POINTER(ctypes.c_longlong)],
     "sgml_set_trace": [ctypes.c_void_p, ctypes.c_int],
     "sgml_get_trace": [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int, ctypes.POINTER(ctypes.c_int),
@@ -226,9 +226,10 @@ class Grid:
         _check(load().sgml_sigma_gradient(self._h, problem, _addr(lam, m), _addr(u, m), _addr(out, m)))
         return out
 
-    def set_launch(self, ctas_per_sm=0, z_waves=1, mode=0):
-        """mode 0: one persistent cooperative launch per call; mode 1: one launch per phase."""
-        _check(load().sgml_set_launch(self._h, ctas_per_sm, z_waves, mode))
+    def set_launch(self, ctas_per_sm=0, z_waves=1, mode=0, tile_x=64):
+        """mode 0: one persistent cooperative launch per call; mode 1: one launch per phase;
+        tile_x 32 (32 x 16 column tiles) or 64 (64 x 8)."""
+        _check(load().sgml_set_launch(self._h, ctas_per_sm, z_waves, mode, tile_x))
 
     def set_trace(self, cycles):
         _check(load().sgml_set_trace(self._h, cycles))
