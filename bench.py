@@ -191,7 +191,8 @@ def make_grid(d, precision, stream):
     from paper_1703_07206_gb300 import sgml
     g = sgml.Grid(3, [d["n"]], precision=precision, stream=stream)
     g.set_params(max_cycles=args_global.max_cycles)
-    g.set_launch(0, 1, 0, args_global.tile_x)
+    g.set_launch(0, 1, 0, args_global.tile_x, args_global.slab_z)
+    g.set_fusion(args_global.pair_levels)
     return g
 
 
@@ -325,7 +326,8 @@ def run_gpu(args):
             "vs_baseline": None, "dtype": "f32+f64" if forms[0] == "mixed" else "f64", "data": "synthetic",
             "config": {"workload": workload_name(n), "form": forms[0], "nodes": M, "cycles": main["cycles"],
                        "rel_residual": main["rel"], "l2": "inputs larger than L2 (working set > 1 GB per replica)",
-                       "tile": f"{args.tile_x}x{512 // args.tile_x}",
+                       "tile": f"{args.tile_x}x{512 // args.tile_x}", "slab_z": args.slab_z,
+                       "fused_pair_levels": args.pair_levels,
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
             "roofline": main["roofline"], "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": int(round(main["launches_per_step"] * main["steps"])), "clocks": main["clocks"]}
@@ -341,21 +343,12 @@ def run_gpu(args):
         g.close()
 
 
-def schedule_labels(n, n_r=2):
-    """Labels of the cycle's phases, in the library's order (restriction passes, then the zig-zag
-    visits of Algorithm 3 with their transitions)."""
-    lab = [f"restrict ->{l}" for l in range(1, n)]
-    visits = []
-    for nu1 in range(n - 1, 0, -1):
-        visits += [(nu1, nu1), (nu1 - 1, nu1), (nu1, nu1)]
-    visits.append((0, 0))
-    for q, (lv, tooth) in enumerate(visits):
-        if q:
-            plv = visits[q - 1][0]
-            lab.append(f"prolong {plv}->{lv}" if lv == plv - 1 else f"inject {plv}->{lv}")
-        k = min(n_r, 2 ** (n - tooth))
-        lab += [f"sweep L{lv}"] * (3 * k if q == len(visits) - 1 else k)
-    return lab
+def schedule_labels(g):
+    """Labels of the cycle's phases, from the library's own phase table (restriction passes, then
+    the zig-zag visits of Algorithm 3 with their transitions; fused sweep pairs count as one)."""
+    names = {0: lambda l: f"restrict ->{l}", 1: lambda l: f"sweep L{l}", 2: lambda l: f"prolong {l + 1}->{l}",
+             3: lambda l: f"inject {l - 1}->{l}"}
+    return [names[op](level) for op, level, _, _ in g.get_phases()]
 
 
 def run_trace(args, g, n):
@@ -364,7 +357,7 @@ def run_trace(args, g, n):
     g.set_params(max_cycles=args.max_cycles)
     g.solve_to_tol(TOL)
     t = g.get_trace()
-    lab = ["-", "residual", "check"] + schedule_labels(n)
+    lab = ["-", "residual", "check"] + schedule_labels(g)
     mean = t[1:].mean(axis=0) if len(t) > 1 else t.mean(axis=0)
     groups = {}
     for name, v in zip(lab, mean):
@@ -385,7 +378,8 @@ def run_ncu_case(args):
     d = inputs.dielectric_spheres_3d(n=args.n, seed=2000)
     prec = sgml.MIXED if args.form in ("mixed", "both") else sgml.FP64
     g = sgml.Grid(3, [args.n], precision=prec)
-    g.set_launch(0, 1, 1 if args.phased else 0, args.tile_x)
+    g.set_launch(0, 1, 1 if args.phased else 0, args.tile_x, args.slab_z)
+    g.set_fusion(args.pair_levels)
     sgml.problem_into_grid(g, 0, d)
     g.run_cycle(1)  # warm-up launch (and setup)
     if args.trace:
@@ -426,6 +420,8 @@ def main():
     ap.add_argument("--ncu-solve", action="store_true", help="ncu case: one full solve instead of --ncu-cycles")
     ap.add_argument("--phased", action="store_true")
     ap.add_argument("--tile-x", type=int, default=64, choices=[32, 64], help="column tiles 32 x 16 or 64 x 8")
+    ap.add_argument("--slab-z", type=int, default=32, help="z-slab height of the work partition (0: contiguous runs)")
+    ap.add_argument("--pair-levels", type=int, default=0, help="levels whose sweeps run in fused pairs (0: none)")
     ap.add_argument("--trace", action="store_true", help="with --ncu-case: per-phase times from the kernel's trace")
     ap.add_argument("--trace-cycles", type=int, default=64)
     args = ap.parse_args()

@@ -132,16 +132,38 @@ int sgml_residual(sgml_grid_t g, int problem, const double* u, double* r);
  * Returns SGML_ERR_ARG for a problem with a Neumann face.  Synchronises. */
 int sgml_sigma_gradient(sgml_grid_t g, int problem, const double* lambda, const double* u, double* grad);
 
-/* Launch shape of the cycle kernel (256 threads per CTA): tile_x selects the column tiles the tiled
- * phases work on, 32 (32 x 16 columns) or 64 (64 x 8 columns, the default); ctas_per_sm CTAs per SM
- * (0 = as many as fit; the cooperative launch needs all CTAs resident, so the library clamps to the
- * occupancy limit); z_waves (>= 1): each level's tile-planes are cut into G * z_waves equal pieces
- * (G = CTAs), piece j going to CTA j mod G (1: one contiguous share per CTA).  mode 0 (default):
- * every run_cycle / solve_to_tol / residual_norm call is one persistent cooperative launch with
- * grid-wide barriers between phases.  mode 1: the same device code with one ordinary launch per
- * phase (for profiling single phases; run_cycle then needs no host synchronisation and can be
- * captured in a CUDA graph).  Used by the autotuner.  Results do not depend on the launch shape. */
-int sgml_set_launch(sgml_grid_t g, int ctas_per_sm, int z_waves, int mode, int tile_x);
+/* Launch shape and work partition of the cycle kernel (256 threads per CTA).
+ *   ctas_per_sm: CTAs per SM (0 = as many as fit; the cooperative launch needs all CTAs resident, so
+ *     the library clamps to the occupancy limit).
+ *   z_waves (>= 1): with the contiguous cut, each level's tile-planes are cut into G * z_waves equal
+ *     runs (G = CTAs), run j going to CTA j mod G (1: one contiguous share per CTA).
+ *   mode 0 (default): every run_cycle / solve_to_tol / residual_norm call is one persistent
+ *     cooperative launch with grid-wide barriers between phases.  mode 1: the same device code with
+ *     one ordinary launch per phase (for profiling single phases; run_cycle then needs no host
+ *     synchronisation and can be captured in a CUDA graph).
+ *   tile_x: the column tiles of the tiled phases, 32 (32 x 16 columns) or 64 (64 x 8, the default).
+ *   slab_z (default 32): 3-D levels large enough to give every CTA two slabs of work are cut into
+ *     z-slabs of about slab_z planes; the (slab, tile) pieces are dealt to the CTAs in turn, so that
+ *     neighbouring tiles are processed at the same time and their shared halo cells are read from
+ *     HBM once.  0: contiguous runs on every level.
+ * Used by the autotuner.  Results do not depend on these settings (bit for bit). */
+int sgml_set_launch(sgml_grid_t g, int ctas_per_sm, int z_waves, int mode, int tile_x, int slab_z);
+
+/* Fused sweep pairs (3-D, SGML_MIXED): on levels 0 .. pair_levels - 1 (default 0: off) the
+ * k relaxation sweeps of a visit (Algorithm 2, Eq. 2) run two at a time in one pass over the level:
+ * the first sweep is evaluated on each tile widened by one cell and kept on chip, the second reads
+ * it there, so the level's arrays cross HBM once per pair instead of once per sweep.  The result is
+ * the same Jacobi iteration (rounding differs from the unfused form only in the order of the
+ * neighbour sums).  0 turns fusion off; ignored for 2-D grids and the FP64 form.  Takes effect at
+ * the next cycle. */
+int sgml_set_fusion(sgml_grid_t g, int pair_levels);
+
+/* The cycle's phase table as the library runs it (Algorithm 3's schedule: restriction passes, then
+ * the visits with their interpolation / injection steps).  Writes 4 ints per phase to out
+ * (op: 0 restrict, 1 sweep, 2 interpolate to the finer level, 3 inject to the coarser level; the
+ * level it writes; the index of its first sweep within the visit; the sweeps it performs (1 or 2,
+ * 0 for the other ops)) for at most cap phases, and the phase count to *count.  Host only. */
+int sgml_get_phases(sgml_grid_t g, int* out, int cap, int* count);
 
 /* Per-phase tracing of the persistent cycle kernel (a profiling aid): with cycles > 0, CTA 0
  * stamps the GPU global timer after every grid barrier of the first `cycles` cycles of each

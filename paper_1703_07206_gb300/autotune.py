@@ -1,7 +1,8 @@
 """Launch-shape autotuner for libsgml grids.
 
 Times a few cycles of the grid's own problem(s) for each candidate launch shape -- the column-tile
-shape of the tiled phases (32 x 16 or 64 x 8), CTAs per SM, work pieces per CTA (``z_waves``) and
+shape of the tiled phases (32 x 16 or 64 x 8), the z-slab height of the work partition (``slab_z``),
+CTAs per SM, work pieces per CTA (``z_waves``) and
 launch mode (one persistent cooperative launch per call, or one launch per phase) -- keeps the fastest, and caches the choice in a JSON file keyed by the problem
 configuration (dimension, precision, level counts, device).  Results do not depend on the launch
 shape, only the time does.
@@ -16,12 +17,13 @@ import time
 from . import sgml
 
 DEFAULT_CANDIDATES = [
-    {"ctas_per_sm": 0, "z_waves": 1, "mode": 0, "tile_x": 64},
-    {"ctas_per_sm": 0, "z_waves": 1, "mode": 0, "tile_x": 32},
-    {"ctas_per_sm": 0, "z_waves": 2, "mode": 0, "tile_x": 64},
-    {"ctas_per_sm": 0, "z_waves": 4, "mode": 0, "tile_x": 64},
-    {"ctas_per_sm": 1, "z_waves": 1, "mode": 0, "tile_x": 64},
-    {"ctas_per_sm": 0, "z_waves": 1, "mode": 1, "tile_x": 64},
+    {"ctas_per_sm": 0, "z_waves": 1, "mode": 0, "tile_x": 64, "slab_z": 32},
+    {"ctas_per_sm": 0, "z_waves": 1, "mode": 0, "tile_x": 64, "slab_z": 16},
+    {"ctas_per_sm": 0, "z_waves": 1, "mode": 0, "tile_x": 64, "slab_z": 0},
+    {"ctas_per_sm": 0, "z_waves": 1, "mode": 0, "tile_x": 32, "slab_z": 16},
+    {"ctas_per_sm": 0, "z_waves": 2, "mode": 0, "tile_x": 64, "slab_z": 0},
+    {"ctas_per_sm": 1, "z_waves": 1, "mode": 0, "tile_x": 64, "slab_z": 16},
+    {"ctas_per_sm": 0, "z_waves": 1, "mode": 1, "tile_x": 64, "slab_z": 16},
 ]
 
 CACHE = os.environ.get("SGML_TUNE_CACHE", os.path.join(os.path.expanduser("~"), ".cache", "sgml_autotune.json"))

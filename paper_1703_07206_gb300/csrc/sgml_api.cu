@@ -52,7 +52,8 @@ struct sgml_grid {
   int* d_task_off = nullptr;
   double* d_hist = nullptr;
   int hist_cap = 0;
-  double *U = nullptr, *F = nullptr, *SIG64 = nullptr, *A64 = nullptr, *RES64 = nullptr;
+  double *U = nullptr, *F = nullptr, *SIG64 = nullptr, *A64 = nullptr;
+  float2* RESP = nullptr;  // mixed form: accumulated residual as hi + lo float pairs
   void* A0 = nullptr;
   void *E = nullptr, *E2 = nullptr, *B = nullptr, *R = nullptr, *SIG = nullptr, *Q = nullptr;
   long long full_total = 0, lvl_total = 0;
@@ -63,6 +64,8 @@ struct sgml_grid {
   int max_cycles = 200;
   int threads = kThreads, ctas_per_sm = 0, blocks = 0, z_waves = 1;
   int tile_x = 64;  // 32 (32 x 16 tiles) or 64 (64 x 8 tiles)
+  int slab_z = 32;  // slab height of the slab cut of large 3-D levels (0: contiguous runs only)
+  int pair_levels = 0;  // levels whose sweeps run in fused pairs (3-D mixed form only; off by default)
   int mode = 0;  // 0: one persistent cooperative launch per call, 1: one launch per phase
   bool dirty_coeffs = true, dirty_desc = true, dirty_phases = true, dirty_tiles = true, fresh = true;
   long long launches = 0;
@@ -121,7 +124,9 @@ static long long round_up(long long x, long long a) { return (x + a - 1) / a * a
 // Schedule of one cycle (Algorithm 3) for the deepest problem of the batch; shallower problems
 // follow its suffix.
 // ------------------------------------------------------------------------------------------------
-static std::vector<Phase> build_phases(int n_max, int n_r) {
+// Phase table of one cycle.  On levels below pair_levels the sweeps of a visit run two at a time
+// (kPair; a visit with an odd number of sweeps ends with a single one).
+static std::vector<Phase> build_phases(int n_max, int n_r, int pair_levels) {
   std::vector<Phase> ph;
   for (int l = 1; l <= n_max - 1; ++l) ph.push_back(Phase{OP_RESTRICT, l, l - 1, 0, 0, 0});
   struct Visit {
@@ -148,15 +153,18 @@ static std::vector<Phase> build_phases(int n_max, int n_r) {
     const int e = n_max - v.tooth;
     const int k = std::min<long long>(n_r, 1LL << std::min(e, 30));
     const int kk = v.final_visit ? 3 * k : k;
-    for (int s = 0; s < kk; ++s)
-      ph.push_back(Phase{OP_SWEEP, v.level, v.tooth, s,
-                         (v.final_visit ? kFinalVisit : 0) | (v.first ? kFirstOfTooth : 0), 0});
+    const int flags = (v.final_visit ? kFinalVisit : 0) | (v.first ? kFirstOfTooth : 0);
+    const int step = v.level < pair_levels ? 2 : 1;
+    for (int s = 0; s < kk; s += step)
+      ph.push_back(Phase{OP_SWEEP, v.level, v.tooth, s, flags | (step == 2 && s + 1 < kk ? kPair : 0), 0});
   }
   return ph;
 }
 
+static int effective_pair_levels(const sgml_grid* g) { return (g->dim == 3 && g->mixed) ? g->pair_levels : 0; }
+
 static int upload_phases(sgml_grid* g) {
-  std::vector<Phase> ph = build_phases(g->n_max, g->n_r);
+  std::vector<Phase> ph = build_phases(g->n_max, g->n_r, effective_pair_levels(g));
   if (g->d_phases) SGML_CUDA(cudaFree(g->d_phases));
   g->d_phases = nullptr;
   g->nphases = (int)ph.size();
@@ -189,11 +197,13 @@ static int upload_tiles(sgml_grid* g) {
       rp[(size_t)l * (g->batch + 1) + b + 1] = rp[(size_t)l * (g->batch + 1) + b] + rows;
     }
   // z_waves equal pieces per CTA: piece j goes to CTA j mod G (z_waves = 1: one contiguous share each)
-  const int G = g->blocks, W = g->z_waves, Gp = G * W;
+  // (the slab cut deals its pieces to the CTAs itself: z_waves does not apply)
+  const int G = g->blocks, W = g->slab_z > 0 ? 1 : g->z_waves, Gp = G * W;
   const int tx = g->tile_x, ty = 2 * kThreads / g->tile_x;
-  std::vector<TileTask> pieces((size_t)partition_bound(g->dim, nb.data(), g->batch, Gp, tx, ty));
+  std::vector<TileTask> pieces((size_t)partition_bound(g->dim, nb.data(), g->batch, Gp, tx, ty, g->slab_z));
   std::vector<int> poff((size_t)kMaxLevels * (Gp + 1));
-  pieces.resize(build_partition(g->dim, nb.data(), dir_hi.data(), g->batch, Gp, tx, ty, pieces.data(), poff.data()));
+  pieces.resize(build_partition(g->dim, nb.data(), dir_hi.data(), g->batch, Gp, tx, ty, pieces.data(), poff.data(),
+                                g->slab_z));
   std::vector<TileTask> tasks;
   tasks.reserve(pieces.size());
   std::vector<int> toff((size_t)kMaxLevels * (G + 1));
@@ -347,6 +357,7 @@ static int launch(sgml_grid* g, int max_cycles, double tol) {
   p.w_corner = w_corner();
   p.omega = g->theta * jacobi_gain(g->dim);
   p.n_r = g->n_r;
+  p.pair_levels = effective_pair_levels(g);
   p.sync = g->d_sync;
   p.timeout_ns = 2000000000ull;  // 2 s per barrier wait
   p.hist = g->d_hist;
@@ -361,7 +372,7 @@ static int launch(sgml_grid* g, int max_cycles, double tol) {
   p.F = g->F;
   p.SIG64 = g->SIG64;
   p.A64 = g->A64;
-  p.RES64 = g->RES64;
+  p.RESP = g->RESP;
   p.A0 = g->A0;
   p.E = g->E;
   p.E2 = g->E2;
@@ -459,7 +470,7 @@ int sgml_create_grid(int dim, int batch, const int* n_levels, int precision, voi
   ALLOC(g->U, sizeof(double) * full);
   ALLOC(g->F, sizeof(double) * full);
   if (g->mixed) {
-    ALLOC(g->RES64, sizeof(double) * full);
+    ALLOC(g->RESP, sizeof(float2) * full);
   }
   ALLOC(g->E, (size_t)g->elem * lvl);
   ALLOC(g->E2, (size_t)g->elem * lvl);
@@ -671,15 +682,38 @@ int sgml_sigma_gradient(sgml_grid_t g, int problem, const double* lambda, const 
   return SGML_OK;
 }
 
-int sgml_set_launch(sgml_grid_t g, int ctas_per_sm, int z_waves, int mode, int tile_x) {
+int sgml_set_launch(sgml_grid_t g, int ctas_per_sm, int z_waves, int mode, int tile_x, int slab_z) {
   if (!valid(g)) return fail(SGML_ERR_ARG, "invalid grid");
-  if (ctas_per_sm < 0 || z_waves < 1 || z_waves > 64 || (mode != 0 && mode != 1) || (tile_x != 32 && tile_x != 64))
-    return fail(SGML_ERR_ARG, "ctas_per_sm >= 0, z_waves in 1..64, mode 0 or 1, tile_x 32 or 64");
+  if (ctas_per_sm < 0 || z_waves < 1 || z_waves > 64 || (mode != 0 && mode != 1) || (tile_x != 32 && tile_x != 64) ||
+      slab_z < 0 || slab_z > 4096)
+    return fail(SGML_ERR_ARG, "ctas_per_sm >= 0, z_waves in 1..64, mode 0 or 1, tile_x 32 or 64, slab_z in 0..4096");
   g->ctas_per_sm = ctas_per_sm;
   g->z_waves = z_waves;
   g->mode = mode;
   g->tile_x = tile_x;
+  g->slab_z = slab_z;
   g->dirty_tiles = true;
+  return SGML_OK;
+}
+
+int sgml_set_fusion(sgml_grid_t g, int pair_levels) {
+  if (!valid(g)) return fail(SGML_ERR_ARG, "invalid grid");
+  if (pair_levels < 0 || pair_levels > kMaxLevels) return fail(SGML_ERR_ARG, "pair_levels must be in 0..13");
+  g->pair_levels = pair_levels;
+  g->dirty_phases = true;
+  return SGML_OK;
+}
+
+int sgml_get_phases(sgml_grid_t g, int* out, int cap, int* count) {
+  if (!valid(g) || !count || (cap > 0 && !out)) return fail(SGML_ERR_ARG, "invalid grid or output");
+  const std::vector<Phase> ph = build_phases(g->n_max, g->n_r, effective_pair_levels(g));
+  *count = (int)ph.size();
+  for (int q = 0; q < (int)ph.size() && q < cap; ++q) {
+    out[4 * q + 0] = ph[q].op;
+    out[4 * q + 1] = ph[q].level;
+    out[4 * q + 2] = ph[q].sweep;
+    out[4 * q + 3] = ph[q].op == OP_SWEEP ? ((ph[q].flags & kPair) ? 2 : 1) : 0;
+  }
   return SGML_OK;
 }
 
@@ -728,7 +762,7 @@ int sgml_launch_count(sgml_grid_t g, long long* count) {
 int sgml_destroy(sgml_grid_t g) {
   if (!g) return SGML_OK;
   cudaStreamSynchronize(g->stream);
-  void* ptrs[] = {g->U, g->F, g->SIG64, g->A64, g->RES64, g->A0, g->E, g->E2, g->B, g->R, g->SIG, g->Q,
+  void* ptrs[] = {g->U, g->F, g->SIG64, g->A64, g->RESP, g->A0, g->E, g->E2, g->B, g->R, g->SIG, g->Q,
                   g->d_probs, g->d_state, g->d_accum, g->d_sync, g->d_phases, g->d_rows, g->d_tasks,
                   g->d_task_off, g->d_hist, g->d_trace};
   for (void* p : ptrs)

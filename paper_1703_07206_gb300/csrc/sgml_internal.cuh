@@ -3,7 +3,8 @@
 //
 // Memory layout in HBM (one allocation per pool, all problems of the batch back to back):
 //   FP64 full-grid pools, N^d doubles per problem at ProblemDesc::off_full:
-//     U (solution), F (source), SIG64 (sigma), A64 (per-node a), RES64 (accumulated residual, mixed)
+//     U (solution), F (source), SIG64 (sigma), A64 (per-node a); RESP (accumulated residual of the
+//     mixed form, kept as an unevaluated sum hi + lo of two floats: 8 bytes per node)
 //   cycle-precision level pools (T = double or float), per problem levels 0..n-1 back to back at
 //   ProblemDesc::off_lvl[l], level l holding (2^(n-l)+1)^d nodes (the level-l subset of the single
 //   grid stored compactly, row-major [z][y][x]):
@@ -25,6 +26,7 @@ enum Op : int { OP_RESTRICT = 0, OP_SWEEP = 1, OP_PROLONG = 2, OP_INJECT = 3 };
 constexpr int kFinalVisit = 1;   // SWEEP: merged last level-0 visit (tooth 0 and the final visit)
 constexpr int kFirstOfTooth = 2; // SWEEP: first visit of its tooth
 constexpr int kInit = 4;         // PROLONG: first arrival at the target level in this cycle
+constexpr int kPair = 8;         // SWEEP: sweeps `sweep` and `sweep + 1` of the visit, fused
 
 // One step of the cycle's schedule; a grid-wide barrier follows each phase.
 struct Phase {
@@ -113,6 +115,7 @@ struct KernelParams {
   double w_edge, w_corner;       // 1/sqrt(2), 1/sqrt(3)
   double omega;                  // delta_tau * D_i of the Jacobi-scaled step
   int n_r;
+  int pair_levels;               // levels 0 .. pair_levels - 1 run their sweeps in fused pairs (kPair)
   GridSync* sync;
   unsigned long long timeout_ns;
   double* hist;
@@ -120,7 +123,7 @@ struct KernelParams {
   unsigned long long* trace;  // optional: globaltimer after each barrier, [cycle][2 + nphases]
   int trace_cycles;
   double *U, *F, *SIG64, *A64;
-  double* RES64;   // accumulated FP64 residual of the mixed form (full grid)
+  float2* RESP;    // accumulated residual of the mixed form, hi + lo float pairs (full grid)
   void *E, *E2, *B, *R, *SIG, *Q;
   void* A0;        // per-node a at level 0 in cycle precision (recurrence operand)
 };

@@ -35,6 +35,11 @@ constexpr int kTX = SGML_TILE_X, kTY = 2 * (kThreads / kTX);
 // ---------------------------------------------------------------------------------------------
 
 __device__ __forceinline__ int refl(int i, int N) { return i < 0 ? -i : (i > N - 1 ? 2 * (N - 1) - i : i); }
+// The image index, clamped into the level (cells past the image of the far edge: never used).
+__device__ __forceinline__ int refl_clamp(int i, int N) {
+  i = refl(i, N);
+  return i < 0 ? 0 : (i > N - 1 ? N - 1 : i);
+}
 
 __device__ __forceinline__ int level_side(int n, int l) { return (1 << (n - l)) + 1; }
 
@@ -89,6 +94,17 @@ __device__ __forceinline__ double nan_max(double a, double b) {
   if (b != b) return b;
   return a > b ? a : b;
 }
+
+// Explicitly rounded arithmetic for the stencil sums and updates: the compiler may otherwise
+// contract a * b + c into an FMA in one copy of inlined or unrolled code and not in another, which
+// would make a node's value depend on which tile, z-piece or loop iteration computed it.  With
+// these, results are identical bit for bit whatever the launch shape and work partition.
+__device__ __forceinline__ float rn_fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double rn_fma(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float rn_mul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double rn_mul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float rn_add(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double rn_add(double a, double b) { return __dadd_rn(a, b); }
 
 __device__ __forceinline__ unsigned long long globaltimer() {
   unsigned long long t;
@@ -177,6 +193,17 @@ __device__ __forceinline__ int visit_sweeps(int n_r, int n, int tooth, bool fina
   const int cap = e >= 30 ? (1 << 30) : (1 << e);
   const int k = n_r < cap ? n_r : cap;
   return final_visit ? 3 * k : k;
+}
+
+// Levels whose sweeps run two at a time (fused pairs, 3-D mixed form): sweep s reads E or E2 by the
+// parity of its pair index s / 2 there, of s elsewhere; a visit of k sweeps ends in E2 if it flipped
+// the buffers an odd number of times.
+__device__ __forceinline__ bool paired_level(const KernelParams& p, int l) { return l < p.pair_levels; }
+__device__ __forceinline__ int sweep_parity(const KernelParams& p, int l, int sweep) {
+  return (paired_level(p, l) ? sweep >> 1 : sweep) & 1;
+}
+__device__ __forceinline__ int visit_flips(const KernelParams& p, int l, int k) {
+  return paired_level(p, l) ? (k + 1) >> 1 : k;
 }
 
 // Halo of a kTX x kTY tile: (kTX + 2) x (kTY + 2) cells, at most kCells per thread.  Thread
@@ -346,11 +373,7 @@ template <typename T>
 constexpr size_t prolong_smem_bytes() {
   return 4 * (sizeof(T) * 2 * (kTX / 2 + 1) * (kTY / 2 + 1) + sizeof(T) * 4 * kThreads);
 }
-template <typename T>
-constexpr size_t phase_smem_bytes() {
-  constexpr size_t a = sweep_smem_bytes<T>() > outer_smem_bytes() ? sweep_smem_bytes<T>() : outer_smem_bytes();
-  return a > prolong_smem_bytes<T>() ? a : prolong_smem_bytes<T>() + 64;
-}
+
 
 // ---------------------------------------------------------------------------------------------
 // Lift: u = Dirichlet values on fixed nodes, 0 on unknowns; ||f|| over the unknowns.  One node row
@@ -406,7 +429,9 @@ __device__ __forceinline__ double cast_scale(const KernelParams& p, int b, int c
 // Residual phases.  Anchor (FP64, Sec. 2's recurrence restarted from the accumulated solution):
 // r = f - delta L_0 u.  Recurrence (mixed form, the paper's r_i = r_{i-1} - delta L(e_{i-1})):
 // r = r_prev - delta L_0 e / s with e the previous cycle's correction in FP32 (scale s), the
-// stencil applied in FP32 and the sum accumulated in FP64.  Both evaluate Eq. 5 as
+// stencil applied in FP32 and r kept as an unevaluated sum hi + lo of two floats, updated with
+// error-free transformations (Knuth's two-sum) on the FP32 pipe: about 48 significant bits, far
+// more than the FP32 stencil term that is subtracted, and no FP64 instruction per node.  Both evaluate Eq. 5 as
 // sigma-weighted differences (v_o - v_c) grouped in face, edge and corner classes, write the cast
 // level-0 source of the next cycle and the max / L2 norms; Neumann images carry 2 k h g in the
 // anchor (the correction e satisfies homogeneous conditions).  3-D tiles march in z keeping
@@ -417,10 +442,11 @@ template <typename V>
 struct ResSrc {
   const V* u;          // operand, packed N^d array of the problem
   const V* s;          // sigma (heterogeneous problems)
-  const double* rhs;   // f or the accumulated residual
+  const double* rhs;   // anchor: f; recurrence: the hi/lo float pairs of r_prev, moved as 8-byte words
   const V* a;          // per-node a, or null for a_scalar
   double a_scalar;
   double opscale;      // r = rhs - opscale * (delta L v)
+  float opscale32;     // the same, rounded to FP32 (recurrence)
   bool images;         // Neumann images carry the prescribed derivative (anchor only)
 };
 
@@ -464,34 +490,49 @@ __device__ __forceinline__ void res_plane(const ResStage<V>& S, int b0, int dz, 
       }
 }
 
-// Finish one node: r = rhs - opscale * (c0 * sum + a * v_c); store the cast source (and the FP64
-// residual in the mixed form); fold |r| and r^2 into the thread's norms (accumulated in V: FP64 for
-// the anchor, FP32 for the recurrence, whose norms only steer the schedule -- the recurrence then
-// issues three FP64-pipe instructions per node: the widening of delta L e, the FP64 accumulation
-// and the narrowing of r).
+// Finish one node: r = rhs - opscale * (c0 * sum + a * v_c); store the cast source (and, in the
+// mixed form, r as a hi/lo float pair); fold |r| and r^2 into the thread's norms (accumulated in
+// V: FP64 for the anchor, FP32 for the recurrence, whose norms only steer the schedule).
 __device__ __forceinline__ float nan_maxf(float a, float b) {
   if (a != a) return a;
   if (b != b) return b;
   return a > b ? a : b;
 }
 
+// Knuth's two-sum: s + e == a + b exactly (round-to-nearest, no contraction into FMA).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bp = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bp)), __fsub_rn(b, bp));
+}
+
+__device__ __forceinline__ float2 word_as_pair(double w) {
+  const unsigned long long bits = (unsigned long long)__double_as_longlong(w);
+  return make_float2(__uint_as_float((unsigned)(bits & 0xffffffffull)), __uint_as_float((unsigned)(bits >> 32)));
+}
+
 template <typename T, typename V>
 __device__ __forceinline__ void res_finish(const ResSrc<V>& src, V c0v, V sum, V uc, V a, double rhs, double scale,
-                                           T* R0, double* RES, long long idx, V& mx, V& s2) {
+                                           float scale32, T* R0, float2* RES, long long idx, V& mx, V& s2) {
   if constexpr (sizeof(V) == 8) {
-    const double r = rhs - src.opscale * fma((double)c0v, (double)sum, (double)a * (double)uc);
+    const double r = __fma_rn(-src.opscale, __fma_rn((double)c0v, (double)sum, __dmul_rn((double)a, (double)uc)), rhs);
     mx = nan_max(mx, fabs(r));
     s2 = fma(r, r, s2);
-    if (RES) RES[idx] = r;
+    if (RES) {
+      const float hi = (float)r;
+      RES[idx] = make_float2(hi, (float)(r - (double)hi));
+    }
     R0[idx] = (T)(r * scale);
   } else {
-    const V Lv = fma(c0v, sum, a * uc);
-    const double r = fma(-src.opscale, (double)Lv, rhs);
-    if (RES) RES[idx] = r;
-    const float rf = (float)r;
-    R0[idx] = (T)(rf * (float)scale);
-    mx = nan_maxf(mx, fabsf(rf));
-    s2 = fmaf(rf, rf, s2);
+    const float d = __fmul_rn(__fmaf_rn(c0v, sum, __fmul_rn(a, uc)), src.opscale32);
+    const float2 prev = word_as_pair(rhs);
+    float hs, he, h, l;
+    two_sum(prev.x, -d, hs, he);
+    two_sum(hs, __fadd_rn(prev.y, he), h, l);
+    RES[idx] = make_float2(h, l);
+    R0[idx] = (T)(h * scale32);
+    mx = nan_maxf(mx, fabsf(h));
+    s2 = fmaf(h, h, s2);
   }
 }
 
@@ -503,8 +544,9 @@ __device__ void residual3(const KernelParams& p, const TileTask& tk, int c, ResS
   const int tid = threadIdx.x;
   const Columns cl = own_columns(P, N, tk.x0, tk.y0);
   const double scale = cast_scale(p, tk.b, c);
+  const float scale32 = (float)scale;
   T* R0 = (T*)p.R + P.off_lvl[0];
-  double* RES = p.RES64 ? p.RES64 + P.off_full : nullptr;
+  float2* RES = p.RESP ? p.RESP + P.off_full : nullptr;
   const bool flux = src.images && tile_has_flux(P, N, tk.x0, tk.y0, 3);
   const HaloCells hc = halo_cells(P, N, tk.x0, tk.y0, flux);
   const V c0v = (V)(p.kappa / (2.0 * P.h * P.h) * (HET ? 1.0 : 2.0));
@@ -567,9 +609,9 @@ __device__ void residual3(const KernelParams& p, const TileTask& tk, int c, ResS
 #pragma unroll
       for (int r = 0; r < 2; ++r) {
         if (!cl.in[r] || cl.fixed_xy[r] || zf) continue;
-        const V sum = cls[r][0] + w_e * cls[r][1] + w_c * cls[r][2];
+        const V sum = rn_fma(w_c, cls[r][2], rn_fma(w_e, cls[r][1], cls[r][0]));
         const V a = src.a ? S1.a[tid + r * kThreads] : a_s;
-        res_finish<T, V>(src, c0v, sum, uc[r], a, S1.f[tid + r * kThreads], scale, R0, RES,
+        res_finish<T, V>(src, c0v, sum, uc[r], a, S1.f[tid + r * kThreads], scale, scale32, R0, RES,
                          (long long)z * NN + cl.off[r], mx, s2);
       }
     }
@@ -594,6 +636,7 @@ __device__ __forceinline__ ResSrc<double> anchor_src(const KernelParams& p, cons
   s.a = P.a_per_node ? p.A64 + P.off_full : nullptr;
   s.a_scalar = P.a_scalar;
   s.opscale = 1.0;
+  s.opscale32 = 1.0f;
   s.images = true;
   return s;
 }
@@ -601,13 +644,15 @@ __device__ __forceinline__ ResSrc<double> anchor_src(const KernelParams& p, cons
 template <typename T>
 __device__ __forceinline__ ResSrc<T> recur_src(const KernelParams& p, const ProblemDesc& P, int b, int c) {
   ResSrc<T> s;
-  const int k_last = visit_sweeps(p.n_r, P.n, 0, true) - 1;  // index of the cycle's last sweep
-  s.u = ((k_last & 1) ? (const T*)p.E : (const T*)p.E2) + P.off_lvl[0];
+  // the cycle's last level-0 sweep wrote E2 after an even number of flips before it, E otherwise
+  const int flips = visit_flips(p, 0, visit_sweeps(p.n_r, P.n, 0, true));
+  s.u = (((flips - 1) & 1) ? (const T*)p.E : (const T*)p.E2) + P.off_lvl[0];
   s.s = P.hetero ? (const T*)p.SIG + P.off_lvl[0] : nullptr;
-  s.rhs = p.RES64 + P.off_full;
+  s.rhs = reinterpret_cast<const double*>(p.RESP + P.off_full);
   s.a = P.a_per_node ? (const T*)p.A0 + P.off_lvl[0] : nullptr;
   s.a_scalar = P.a_scalar;
   s.opscale = 1.0 / p.state[b].scale_used[(c - 1) & 1];
+  s.opscale32 = (float)s.opscale;
   s.images = false;
   return s;
 }
@@ -687,10 +732,10 @@ __device__ void residual2(const KernelParams& p, int c, ResStage<V>* st, bool an
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
       if (!cl.in[r] || cl.fixed_xy[r]) continue;
-      const V sum = cls[r][0] + (V)p.w_edge * cls[r][1];
+      const V sum = rn_fma((V)p.w_edge, cls[r][1], cls[r][0]);
       const V a = src.a ? S.a[tid + r * kThreads] : (V)src.a_scalar;
-      res_finish<T, V>(src, c0v, sum, uc[r], a, S.f[tid + r * kThreads], scale, (T*)p.R + P.off_lvl[0],
-                       p.RES64 ? p.RES64 + P.off_full : nullptr, cl.off[r], mx, s2);
+      res_finish<T, V>(src, c0v, sum, uc[r], a, S.f[tid + r * kThreads], scale, (float)scale,
+                       (T*)p.R + P.off_lvl[0], p.RESP ? p.RESP + P.off_full : nullptr, cl.off[r], mx, s2);
     }
     block_flush((double)mx, (double)s2, &p.accum[tk.b].rmax_bits[c & 1], &p.accum[tk.b].rsum2[c & 1]);
   }
@@ -768,11 +813,13 @@ __device__ void phase_check(const KernelParams& p, int c) {
       st = p.tol >= 0.0 ? -3 : 0;  // SGML_ERR_NOT_CONVERGED for a solve; fine for run_cycle
       stop = 1;
     }
-    // Mixed form: the next residual is the FP64 anchor when the recurrence can no longer be trusted
-    // to ~1 % (the residual fell ten-fold since the last anchor, the cycle contracts fast, the
-    // tolerance may have been reached) and before the last cycle of the launch.
-    S.anchor_next = !p.mixed || rho < 0.2 || rel <= 0.1 * S.anchor_rel || rel <= p.tol || c + 1 >= p.max_cycles ||
-                    c + 1 - S.last_anchor >= 32;
+    // Mixed form: the next residual is the FP64 anchor when the recurrence may have drifted by a few
+    // per cent of the current residual (it fell a hundred-fold since the last anchor, 32 cycles
+    // passed, or the cycle contracts fast), when the tolerance may have been reached, and before
+    // the last cycle of the launch.  The FP32 stencil's error is ~1e-7 of the stencil's terms, which
+    // exceed |delta L e| by up to ~1/h for smooth e, so the drift grows like 3e-5 * sum |r_i|.
+    S.anchor_next = !p.mixed || rho < 0.2 || rel <= 0.01 * S.anchor_rel || rel <= p.tol ||
+                    c + 1 >= p.max_cycles || c + 1 - S.last_anchor >= 32;
     S.status = st;
     A.done = stop;
     A.rmax_bits[(c + 1) & 1] = 0ull;
@@ -812,9 +859,10 @@ __device__ __forceinline__ SweepCtl sweep_ctl(const KernelParams& p, const Phase
   const ProblemDesc& P = p.probs[b];
   const bool final_visit = (ph.flags & kFinalVisit) != 0;
   const int k_b = visit_sweeps(p.n_r, P.n, ph.tooth, final_visit);
-  s.active = !p.accum[b].done && ph.tooth <= P.n - 1 && ph.sweep < k_b;
+  const int span = (ph.flags & kPair) ? 2 : 1;  // sweeps this phase performs
+  s.active = !p.accum[b].done && ph.tooth <= P.n - 1 && ph.sweep + span - 1 < k_b;
   s.zero_in = ph.sweep == 0 && (ph.flags & kFirstOfTooth) && ph.tooth == P.n - 1;
-  s.last = final_visit && ph.sweep == k_b - 1;
+  s.last = final_visit && ph.sweep + span - 1 == k_b - 1;
   s.N = level_side(P.n, ph.level);
   s.off = P.off_lvl[ph.level];
   return s;
@@ -834,7 +882,7 @@ __device__ __forceinline__ void plane_sums2(const SweepStage<T>& S, int b0, bool
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
       a[i][j] = S.e[b0 + i * kHX + j];
-      if (HET) se[i][j] = S.s[b0 + i * kHX + j] * a[i][j];
+      if (HET) se[i][j] = rn_mul(S.s[b0 + i * kHX + j], a[i][j]);
     }
 #pragma unroll
   for (int r = 0; r < 2; ++r) {
@@ -873,8 +921,8 @@ template <typename T, bool HET>
 __device__ __forceinline__ T sweep_update(const SweepConst<T>& k, const SweepStage<T>& S, int slot, int cc, T CSe,
                                           T CSse, T e_c) {
   const T r_i = S.r[slot];
-  if (HET) return k.one_m_omega * e_c + S.q[slot] * (S.s[cc] * CSe + CSse - r_i * k.inv_c);
-  return k.one_m_omega * e_c + k.q_const * ((T)2 * CSe - r_i * k.inv_c);
+  if (HET) return rn_fma(S.q[slot], rn_fma(-r_i, k.inv_c, rn_fma(S.s[cc], CSe, CSse)), rn_mul(k.one_m_omega, e_c));
+  return rn_fma(k.q_const, rn_fma(-r_i, k.inv_c, rn_mul((T)2, CSe)), rn_mul(k.one_m_omega, e_c));
 }
 
 template <typename T, bool HET, bool LAST>
@@ -885,8 +933,9 @@ __device__ void sweep3(const KernelParams& p, const Phase& ph, int c, const Tile
   const int N = sc.N;
   const int tid = threadIdx.x;
   const Columns cl = own_columns(P, N, tk.x0, tk.y0);
-  const T* src = (ph.sweep & 1) ? (const T*)p.E2 + sc.off : (const T*)p.E + sc.off;
-  T* dst = (ph.sweep & 1) ? (T*)p.E + sc.off : (T*)p.E2 + sc.off;
+  const bool odd = sweep_parity(p, ph.level, ph.sweep) != 0;
+  const T* src = odd ? (const T*)p.E2 + sc.off : (const T*)p.E + sc.off;
+  T* dst = odd ? (T*)p.E + sc.off : (T*)p.E2 + sc.off;
   const T* R = (const T*)p.R + sc.off;
   const T* SG = HET ? (const T*)p.SIG + sc.off : nullptr;
   const T* Q = HET ? (const T*)p.Q + sc.off : nullptr;
@@ -941,14 +990,15 @@ __device__ void sweep3(const KernelParams& p, const Phase& ph, int c, const Tile
 #pragma unroll
       for (int r = 0; r < 2; ++r) {
         if (!cl.in[r] || cl.fixed_xy[r] || zf) continue;
-        const T CSe = (o[r].F + m[r].v + nw[r].v) + kc.w_e * (o[r].C + m[r].F + nw[r].F) + kc.w_c * (m[r].C + nw[r].C);
-        const T CSse = HET ? (o[r].sF + m[r].sv + nw[r].sv) + kc.w_e * (o[r].sC + m[r].sF + nw[r].sF) +
-                                 kc.w_c * (m[r].sC + nw[r].sC)
+        const T CSe = rn_fma(kc.w_c, m[r].C + nw[r].C,
+                             rn_fma(kc.w_e, (o[r].C + m[r].F) + nw[r].F, (o[r].F + m[r].v) + nw[r].v));
+        const T CSse = HET ? rn_fma(kc.w_c, m[r].sC + nw[r].sC,
+                                    rn_fma(kc.w_e, (o[r].sC + m[r].sF) + nw[r].sF, (o[r].sF + m[r].sv) + nw[r].sv))
                            : (T)0;
         const int slot = tid + r * kThreads;
         const T e_new = sweep_update<T, HET>(kc, S, slot, b0 + (r + 1) * kHX + 1, CSe, CSse, o[r].v);
         const unsigned idx = zoff + (unsigned)cl.off[r];
-        if (LAST) Ug[idx] = S.u[slot] + (double)e_new * inv_scale;
+        if (LAST) Ug[idx] = __fma_rn((double)e_new, inv_scale, S.u[slot]);
         if (keep) dst[idx] = e_new;
       }
     }
@@ -986,7 +1036,7 @@ __device__ void sweep2(const KernelParams& p, const Phase& ph, int c, SweepStage
         const HaloCells hc = halo_cells(P, N, tk.x0, tk.y0, false);
         const Columns cl = own_columns(P, N, tk.x0, tk.y0);
         SweepStage<T>& S = st[j % D];
-        const T* src = (ph.sweep & 1) ? (const T*)p.E2 + sc.off : (const T*)p.E + sc.off;
+        const T* src = sweep_parity(p, l, ph.sweep) ? (const T*)p.E2 + sc.off : (const T*)p.E + sc.off;
 #pragma unroll
         for (int s = 0; s < kCells; ++s)
           if (hc.off[s] >= 0) {
@@ -1020,21 +1070,297 @@ __device__ void sweep2(const KernelParams& p, const Phase& ph, int c, SweepStage
     PlaneSums<T> ps[2];
     if (P.hetero) plane_sums2<T, true>(S, b0, sc.zero_in, ps);
     else plane_sums2<T, false>(S, b0, sc.zero_in, ps);
-    T* dst = (ph.sweep & 1) ? (T*)p.E + sc.off : (T*)p.E2 + sc.off;
+    T* dst = sweep_parity(p, l, ph.sweep) ? (T*)p.E + sc.off : (T*)p.E2 + sc.off;
     const double inv_scale = LAST ? 1.0 / p.state[tk.b].scale_used[c & 1] : 0.0;
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
       if (!cl.in[r] || cl.fixed_xy[r]) continue;
-      const T CSe = ps[r].F + kc.w_e * ps[r].C;
+      const T CSe = rn_fma(kc.w_e, ps[r].C, ps[r].F);
       const int slot = tid + r * kThreads, cc = b0 + (r + 1) * kHX + 1;
-      const T e_new = P.hetero ? sweep_update<T, true>(kc, S, slot, cc, CSe, ps[r].sF + kc.w_e * ps[r].sC, ps[r].v)
+      const T e_new = P.hetero ? sweep_update<T, true>(kc, S, slot, cc, CSe, rn_fma(kc.w_e, ps[r].sC, ps[r].sF), ps[r].v)
                                : sweep_update<T, false>(kc, S, slot, cc, CSe, (T)0, ps[r].v);
-      if (LAST) p.U[P.off_full + cl.off[r]] = S.u[slot] + (double)e_new * inv_scale;
+      if (LAST) p.U[P.off_full + cl.off[r]] = __fma_rn((double)e_new, inv_scale, S.u[slot]);
       if (!LAST || p.mixed) dst[cl.off[r]] = e_new;
     }
   }
   cp_async_wait<0>();
   __syncthreads();
+}
+
+// ---------------------------------------------------------------------------------------------
+// Two consecutive Jacobi sweeps of a visit in one z-march (3-D, FP32 cycle).  The second sweep at
+// a node needs the first sweep's result on its 3 x 3 x 3 neighbourhood, so the first sweep is
+// evaluated on the tile widened by one cell on every side ((kTX + 2) x (kTY + 2) cells; the ring is
+// evaluated by both neighbouring tiles with the same arithmetic) from inputs widened by two.  Its
+// planes pass through one shared-memory plane buffer one plane behind the loads, and the second
+// sweep runs one plane further behind, so each input plane crosses HBM once for both sweeps and the
+// intermediate correction never leaves the SM.  The z sums of both sweeps are rolled: with
+// t = v + w_e F + w_c C (a plane's part in the sums of the planes above and below) and
+// m = F + w_e C (its part in its own), CS(e) at plane z is (m_z + t_{z-1}) + t_{z+1}.  Mirror
+// images in x and y are loaded mirrored and the in-plane sums are symmetric, so a ring cell outside
+// the domain holds exactly the first sweep at its mirror node.
+// ---------------------------------------------------------------------------------------------
+constexpr int kPX = kTX + 4, kPY = kTY + 4, kPHalo = kPX * kPY;   // inputs: the tile + 2 cells
+constexpr int kPCells = (kPHalo + kThreads - 1) / kThreads;
+constexpr int kEX = kTX + 2, kEY = kTY + 2, kERegion = kEX * kEY;  // first sweep: the tile + 1 cell
+constexpr int kECells = (kERegion + kThreads - 1) / kThreads;
+constexpr int kUnits = (kEY / 2) * kEX;  // first-sweep work units: two vertically adjacent cells
+constexpr int kUnitSlots = (kUnits + kThreads - 1) / kThreads;
+constexpr int kPairStages = 5;  // planes k - 2 .. k resident, loads two planes ahead
+static_assert(kEY % 2 == 0, "two-cell units");
+
+template <typename T>
+struct PairStage {
+  T e[kPHalo];             // correction e on the widened input tile
+  T s[kPHalo];             // sigma on the same cells
+  T r[kERegion];           // restricted residual on the first sweep's cells
+  T q[kERegion];           // local step factor on the same cells
+  double u[2 * kThreads];  // FP64 solution at the tile's nodes (last sweep of a cycle)
+};
+
+template <typename T>
+constexpr size_t pair_smem_bytes() {
+  return sizeof(PairStage<T>) * kPairStages + sizeof(T) * kERegion;
+}
+
+struct PairCells {
+  int in_off[kPCells];  // y * N + x of the thread's input cells (images applied, clamped), -1: none
+  int e_off[kECells];   // the same for the thread's first-sweep cells
+};
+
+__device__ __forceinline__ PairCells pair_cells(int N, int x0, int y0) {
+  PairCells pc;
+#pragma unroll
+  for (int s = 0; s < kPCells; ++s) {
+    const int k = threadIdx.x + s * kThreads;
+    pc.in_off[s] = k < kPHalo ? refl_clamp(y0 - 2 + k / kPX, N) * N + refl_clamp(x0 - 2 + k % kPX, N) : -1;
+  }
+#pragma unroll
+  for (int s = 0; s < kECells; ++s) {
+    const int k = threadIdx.x + s * kThreads;
+    pc.e_off[s] = k < kERegion ? refl_clamp(y0 - 1 + k / kEX, N) * N + refl_clamp(x0 - 1 + k % kEX, N) : -1;
+  }
+  return pc;
+}
+
+// The thread's first-sweep units: unit u = tid + j kThreads covers the cells (ex, 2 pu) and
+// (ex, 2 pu + 1) of the widened tile, pu = u / kEX, ex = u % kEX.
+struct PairUnits {
+  int b1[kUnitSlots];    // top-left of the unit's 4 x 3 input block, -1: no unit
+  int eidx[kUnitSlots];  // first-sweep index of the unit's upper cell
+  unsigned fixed;        // bit 2 j + r: cell r of unit j mirrors onto a Dirichlet x / y face node
+};
+
+__device__ __forceinline__ PairUnits pair_units(const ProblemDesc& P, int N, int x0, int y0) {
+  PairUnits pu;
+  pu.fixed = 0u;
+#pragma unroll
+  for (int j = 0; j < kUnitSlots; ++j) {
+    const int u = threadIdx.x + j * kThreads;
+    pu.b1[j] = pu.eidx[j] = -1;
+    if (u >= kUnits) continue;
+    const int py = u / kEX, ex = u % kEX;
+    pu.b1[j] = 2 * py * kPX + ex;
+    pu.eidx[j] = 2 * py * kEX + ex;
+    const int rx = refl_clamp(x0 - 1 + ex, N);
+    const bool fx = (rx == 0 && P.face_type[0] == 0) || (rx == N - 1 && P.face_type[1] == 0);
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      const int ry = refl_clamp(y0 - 1 + 2 * py + r, N);
+      if (fx || (ry == 0 && P.face_type[2] == 0) || (ry == N - 1 && P.face_type[3] == 0)) pu.fixed |= 1u << (2 * j + r);
+    }
+  }
+  return pu;
+}
+
+// In-plane sums of the two cells of a 4 x 3 block (pitch W) of e and sigma * e: v, F, C per cell
+// and the same for sigma e, plus sigma at the two centres.
+template <typename T, bool HET, int W>
+__device__ __forceinline__ void block_sums(const T* e, int be, const T* sg, int bs, T v[2], T F[2], T C[2], T sv[2],
+                                           T sF[2], T sC[2], T sc[2]) {
+  T a[4][3], se[4][3];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      a[i][j] = e[be + i * W + j];
+      if (HET) se[i][j] = rn_mul(sg[bs + i * kPX + j], a[i][j]);
+    }
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    v[r] = a[r + 1][1];
+    F[r] = (a[r + 1][0] + a[r + 1][2]) + (a[r][1] + a[r + 2][1]);
+    C[r] = (a[r][0] + a[r][2]) + (a[r + 2][0] + a[r + 2][2]);
+    if (HET) {
+      sv[r] = se[r + 1][1];
+      sF[r] = (se[r + 1][0] + se[r + 1][2]) + (se[r][1] + se[r + 2][1]);
+      sC[r] = (se[r][0] + se[r][2]) + (se[r + 2][0] + se[r + 2][2]);
+      sc[r] = sg[bs + (r + 1) * kPX + 1];
+    } else {
+      sv[r] = sF[r] = sC[r] = sc[r] = (T)0;
+    }
+  }
+}
+
+template <typename T, bool HET, bool LAST>
+__device__ void sweep3_pair(const KernelParams& p, const Phase& ph, int c, const TileTask& tk, PairStage<T>* st,
+                            T* ebuf, const SweepCtl& sc) {
+  constexpr int D = kPairStages;
+  const ProblemDesc& P = p.probs[tk.b];
+  const int N = sc.N;
+  const int tid = threadIdx.x;
+  const Columns cl = own_columns(P, N, tk.x0, tk.y0);
+  const bool odd = sweep_parity(p, ph.level, ph.sweep) != 0;
+  const T* src = odd ? (const T*)p.E2 + sc.off : (const T*)p.E + sc.off;
+  T* dst = odd ? (T*)p.E + sc.off : (T*)p.E2 + sc.off;
+  const T* R = (const T*)p.R + sc.off;
+  const T* SG = HET ? (const T*)p.SIG + sc.off : nullptr;
+  const T* Q = HET ? (const T*)p.Q + sc.off : nullptr;
+  double* Ug = p.U + P.off_full;
+  const PairCells pc = pair_cells(N, tk.x0, tk.y0);
+  const PairUnits pu = pair_units(P, N, tk.x0, tk.y0);
+  const SweepConst<T> kc = sweep_const<T>(p, P, ph.level);
+  const double inv_scale = LAST ? 1.0 / p.state[tk.b].scale_used[c & 1] : 0.0;
+  const bool zero_in = sc.zero_in;
+  const int nplanes = tk.nz + 4;
+  const unsigned NN = (unsigned)N * (unsigned)N;
+  // second sweep: the thread's two tile nodes (tx, ty2 + r)
+  const int tx = tid % kTX, ty2 = 2 * (tid / kTX);
+  const int b2 = ty2 * kEX + tx;             // their 4 x 3 block in the plane buffer
+  const int b2s = (ty2 + 1) * kPX + tx + 1;  // the same cells in the input tile (sigma)
+  const int e2 = (ty2 + 1) * kEX + tx + 1;   // first-sweep index of the upper node (r, q)
+  auto issue = [&](int k) {
+    if (k < nplanes) {
+      PairStage<T>& S = st[k % D];
+      const unsigned base = (unsigned)refl(tk.z0 - 2 + k, N) * NN;
+#pragma unroll
+      for (int q = 0; q < kPCells; ++q)
+        if (pc.in_off[q] >= 0) {
+          const unsigned o = base + (unsigned)pc.in_off[q];
+          if (zero_in) S.e[tid + q * kThreads] = (T)0;
+          else cp_async_t(&S.e[tid + q * kThreads], src + o);
+          if (HET) cp_async_t(&S.s[tid + q * kThreads], SG + o);
+        }
+      if (k >= 1 && k <= tk.nz + 2) {  // planes the first sweep evaluates
+#pragma unroll
+        for (int q = 0; q < kECells; ++q)
+          if (pc.e_off[q] >= 0) {
+            const unsigned o = base + (unsigned)pc.e_off[q];
+            cp_async_t(&S.r[tid + q * kThreads], R + o);
+            if (HET) cp_async_t(&S.q[tid + q * kThreads], Q + o);
+          }
+      }
+      if (LAST && k >= 2 && k <= tk.nz + 1) {
+#pragma unroll
+        for (int r = 0; r < 2; ++r)
+          if (cl.in[r]) cp_async_t(&S.u[tid + r * kThreads], Ug + base + (unsigned)cl.off[r]);
+      }
+    }
+    cp_async_commit();
+  };
+  for (int k = 0; k < D - 3; ++k) issue(k);
+  // rolled z sums: first sweep per unit and cell, second sweep per tile node
+  T S1e[kUnitSlots][2], T1e[kUnitSlots][2], S1s[kUnitSlots][2], T1s[kUnitSlots][2], v1[kUnitSlots][2], s1[kUnitSlots][2];
+  T S2e[2], T2e[2], S2s[2], T2s[2], v2[2], s2[2];
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+#pragma unroll
+    for (int j = 0; j < kUnitSlots; ++j) S1e[j][r] = T1e[j][r] = S1s[j][r] = T1s[j][r] = v1[j][r] = s1[j][r] = (T)0;
+    S2e[r] = T2e[r] = S2s[r] = T2s[r] = v2[r] = s2[r] = (T)0;
+  }
+  for (int k = 0; k < nplanes; ++k) {
+    cp_async_wait<D - 4>();
+    __syncthreads();
+    issue(k + D - 3);
+    const PairStage<T>& S0 = st[k % D];            // input plane k (z0 - 2 + k)
+    const PairStage<T>& S1 = st[(k + D - 1) % D];  // input plane k - 1
+    // first sweep: sums of plane k; completes the first sweep at plane k - 1
+    const bool zf1 = z_fixed(cl, tk.z0 - 3 + k, N);
+#pragma unroll
+    for (int j = 0; j < kUnitSlots; ++j) {
+      if (pu.b1[j] < 0) continue;
+      T v[2], F[2], C[2], sv[2], sF[2], sC[2], sgc[2];
+      block_sums<T, HET, kPX>(S0.e, pu.b1[j], S0.s, pu.b1[j], v, F, C, sv, sF, sC, sgc);
+#pragma unroll
+      for (int r = 0; r < 2; ++r) {
+        const T t = rn_fma(kc.w_c, C[r], rn_fma(kc.w_e, F[r], v[r]));
+        const T m = rn_fma(kc.w_e, C[r], F[r]);
+        const T ts = HET ? rn_fma(kc.w_c, sC[r], rn_fma(kc.w_e, sF[r], sv[r])) : (T)0;
+        const T ms = HET ? rn_fma(kc.w_e, sC[r], sF[r]) : (T)0;
+        if (k >= 2) {
+          const int ei = pu.eidx[j] + r * kEX;
+          const T CSe = rn_add(S1e[j][r], t);
+          T en;
+          if (zf1 || ((pu.fixed >> (2 * j + r)) & 1u)) {
+            en = v1[j][r];
+          } else if (HET) {
+            const T CSse = rn_add(S1s[j][r], ts);
+            en = rn_fma(S1.q[ei], rn_fma(-S1.r[ei], kc.inv_c, rn_fma(s1[j][r], CSe, CSse)),
+                        rn_mul(kc.one_m_omega, v1[j][r]));
+          } else {
+            en = rn_fma(kc.q_const, rn_fma(-S1.r[ei], kc.inv_c, rn_mul((T)2, CSe)), rn_mul(kc.one_m_omega, v1[j][r]));
+          }
+          ebuf[ei] = en;
+        }
+        S1e[j][r] = rn_add(m, T1e[j][r]);
+        T1e[j][r] = t;
+        if (HET) {
+          S1s[j][r] = rn_add(ms, T1s[j][r]);
+          T1s[j][r] = ts;
+        }
+        v1[j][r] = v[r];
+        s1[j][r] = sgc[r];
+      }
+    }
+    __syncthreads();  // the plane buffer holds the first sweep at plane k - 1
+    if (k >= 2) {
+      // second sweep: sums of the buffer around the tile nodes; completes plane k - 2
+      T v[2], F[2], C[2], sv[2], sF[2], sC[2], sgc[2];
+      block_sums<T, HET, kEX>(ebuf, b2, S1.s, b2s, v, F, C, sv, sF, sC, sgc);
+      const int z2 = tk.z0 - 4 + k;
+      const bool zf2 = k < 4 || z_fixed(cl, z2, N);
+      const PairStage<T>& S2 = st[(k + D - 2) % D];  // input plane k - 2 (= z2)
+#pragma unroll
+      for (int r = 0; r < 2; ++r) {
+        const T t = rn_fma(kc.w_c, C[r], rn_fma(kc.w_e, F[r], v[r]));
+        const T m = rn_fma(kc.w_e, C[r], F[r]);
+        const T ts = HET ? rn_fma(kc.w_c, sC[r], rn_fma(kc.w_e, sF[r], sv[r])) : (T)0;
+        const T ms = HET ? rn_fma(kc.w_e, sC[r], sF[r]) : (T)0;
+        if (!zf2 && cl.in[r] && !cl.fixed_xy[r]) {
+          const int ei = e2 + r * kEX;
+          const T CSe = rn_add(S2e[r], t);
+          T en;
+          if (HET) {
+            const T CSse = rn_add(S2s[r], ts);
+            en = rn_fma(S2.q[ei], rn_fma(-S2.r[ei], kc.inv_c, rn_fma(s2[r], CSe, CSse)), rn_mul(kc.one_m_omega, v2[r]));
+          } else {
+            en = rn_fma(kc.q_const, rn_fma(-S2.r[ei], kc.inv_c, rn_mul((T)2, CSe)), rn_mul(kc.one_m_omega, v2[r]));
+          }
+          const unsigned idx = (unsigned)z2 * NN + (unsigned)cl.off[r];
+          if (LAST) Ug[idx] = __fma_rn((double)en, inv_scale, S2.u[tid + r * kThreads]);
+          dst[idx] = en;
+        }
+        S2e[r] = rn_add(m, T2e[r]);
+        T2e[r] = t;
+        if (HET) {
+          S2s[r] = rn_add(ms, T2s[r]);
+          T2s[r] = ts;
+        }
+        v2[r] = v[r];
+        s2[r] = sgc[r];
+      }
+    }
+  }
+  cp_async_wait<0>();
+  __syncthreads();
+}
+
+// Dynamic shared memory of the cycle kernel: the largest phase (fused sweep pairs: FP32 only).
+template <typename T>
+constexpr size_t phase_smem_bytes() {
+  constexpr size_t a = sweep_smem_bytes<T>() > outer_smem_bytes() ? sweep_smem_bytes<T>() : outer_smem_bytes();
+  constexpr size_t b = a > prolong_smem_bytes<T>() ? a : prolong_smem_bytes<T>() + 64;
+  return (sizeof(T) == 4 && pair_smem_bytes<T>() > b) ? pair_smem_bytes<T>() : b;
 }
 
 template <typename T, int DIM>
@@ -1049,6 +1375,20 @@ __device__ void phase_sweep(const KernelParams& p, const Phase& ph, int c, unsig
     const SweepCtl sc = sweep_ctl(p, ph, tk.b);
     if (!sc.active) return;
     const bool het = p.probs[tk.b].hetero != 0;
+    if constexpr (sizeof(T) == 4) {
+      if (ph.flags & kPair) {
+        PairStage<T>* pst = (PairStage<T>*)smem;
+        T* ebuf = (T*)(smem + sizeof(PairStage<T>) * kPairStages);
+        if (sc.last) {
+          if (het) sweep3_pair<T, true, true>(p, ph, c, tk, pst, ebuf, sc);
+          else sweep3_pair<T, false, true>(p, ph, c, tk, pst, ebuf, sc);
+        } else {
+          if (het) sweep3_pair<T, true, false>(p, ph, c, tk, pst, ebuf, sc);
+          else sweep3_pair<T, false, false>(p, ph, c, tk, pst, ebuf, sc);
+        }
+        return;
+      }
+    }
     if (sc.last) {
       if (het) sweep3<T, true, true>(p, ph, c, tk, st, sc);
       else sweep3<T, false, true>(p, ph, c, tk, st, sc);
@@ -1098,12 +1438,12 @@ __device__ void phase_restrict(const KernelParams& p, int l) {
   });
 }
 
-// Buffer holding the result of a visit of tooth `tooth` at a level (E if the visit did an even
-// number of sweeps, E2 otherwise).
+// Buffer holding the result of a visit of tooth `tooth` at a level (E if the visit flipped the
+// ping-pong buffers an even number of times, E2 otherwise).
 template <typename T>
 __device__ __forceinline__ T* visit_result(const KernelParams& p, const ProblemDesc& P, int tooth, int l) {
   const int k = visit_sweeps(p.n_r, P.n, tooth, false);
-  return ((k & 1) ? (T*)p.E2 : (T*)p.E) + P.off_lvl[l];
+  return ((visit_flips(p, l, k) & 1) ? (T*)p.E2 : (T*)p.E) + P.off_lvl[l];
 }
 
 // Moving one level finer: E_l (+)= I(E_{l+1} - B_{l+1}) on every level-l node (hat-function

@@ -128,7 +128,7 @@ extern "C" int sgml_solve_noalloc(int dim, int n, int precision, const double* f
   const size_t o_E = bump.take(lvl_bytes), o_E2 = bump.take(lvl_bytes), o_B = bump.take(lvl_bytes);
   const size_t o_R = bump.take(lvl_bytes);
   const size_t o_SIG = sigma ? bump.take(lvl_bytes) : 0, o_Q = sigma ? bump.take(lvl_bytes) : 0;
-  const size_t o_RES = mixed ? bump.take(sizeof(double) * M0) : 0;
+  const size_t o_RES = mixed ? bump.take(sizeof(float2) * M0) : 0;
   size_t o_tmp[kMaxLevels] = {0};
   if (sigma)
     for (int l = 1; l <= n - 1; ++l) o_tmp[l] = bump.take(sizeof(double) * nodes(dim, n, l));
@@ -265,7 +265,7 @@ extern "C" int sgml_solve_noalloc(int dim, int n, int precision, const double* f
   p.F = const_cast<double*>(f);
   p.SIG64 = const_cast<double*>(sigma);
   p.A64 = nullptr;
-  p.RES64 = mixed ? (double*)(base + o_RES) : nullptr;
+  p.RESP = mixed ? (float2*)(base + o_RES) : nullptr;
   p.E = base + o_E;
   p.E2 = base + o_E2;
   p.B = base + o_B;

@@ -53,7 +53,9 @@ _SIGNATURES = {
                          ctypes.POINTER(ctypes.c_int)],
     "sgml_residual": [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p],
     "sgml_sigma_gradient": [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
-    "sgml_set_launch": [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int],
+    "sgml_set_fusion": [ctypes.c_void_p, ctypes.c_int],
+    "sgml_get_phases": [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.POINTER(ctypes.c_int)],
+    "sgml_set_launch": [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int],
     "sgml_launch_count": [ctypes.c_void_p, ctypes.POINTER(ctypes.c_longlong)],
     "sgml_set_trace": [ctypes.c_void_p, ctypes.c_int],
     "sgml_get_trace": [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int, ctypes.POINTER(ctypes.c_int),
@@ -226,10 +228,24 @@ class Grid:
         _check(load().sgml_sigma_gradient(self._h, problem, _addr(lam, m), _addr(u, m), _addr(out, m)))
         return out
 
-    def set_launch(self, ctas_per_sm=0, z_waves=1, mode=0, tile_x=64):
+    def set_fusion(self, pair_levels=0):
+        """Levels 0 .. pair_levels - 1 run their sweeps in fused pairs (3-D mixed form; 0: off)."""
+        _check(load().sgml_set_fusion(self._h, pair_levels))
+
+    def get_phases(self):
+        """The cycle's phase table: list of (op, level, first sweep, sweeps performed)."""
+        lib = load()
+        cnt = ctypes.c_int(0)
+        _check(lib.sgml_get_phases(self._h, None, 0, ctypes.byref(cnt)))
+        buf = (ctypes.c_int * (4 * max(cnt.value, 1)))()
+        _check(lib.sgml_get_phases(self._h, buf, cnt.value, ctypes.byref(cnt)))
+        return [tuple(buf[4 * q:4 * q + 4]) for q in range(cnt.value)]
+
+    def set_launch(self, ctas_per_sm=0, z_waves=1, mode=0, tile_x=64, slab_z=32):
         """mode 0: one persistent cooperative launch per call; mode 1: one launch per phase;
-        tile_x 32 (32 x 16 column tiles) or 64 (64 x 8)."""
-        _check(load().sgml_set_launch(self._h, ctas_per_sm, z_waves, mode, tile_x))
+        tile_x 32 (32 x 16 column tiles) or 64 (64 x 8); slab_z: z-slab height of the slab cut of
+        large 3-D levels (0: contiguous runs)."""
+        _check(load().sgml_set_launch(self._h, ctas_per_sm, z_waves, mode, tile_x, slab_z))
 
     def set_trace(self, cycles):
         _check(load().sgml_set_trace(self._h, cycles))

@@ -44,7 +44,7 @@ def test_cuda_graph_capture_of_run_cycle():
         g2 = sgml.Grid(2, [d["n"] for d in probs], precision=sgml.MIXED, stream=stream)
         for b, d in enumerate(probs):
             sgml.problem_into_grid(g2, b, d)
-        g2.set_launch(0, 1, mode, 64)
+        g2.set_launch(0, 1, mode, 64, 32)
         with torch.cuda.stream(stream):
             g2.run_cycle(2)  # warm-up: builds every table outside the capture
         torch.cuda.synchronize()
@@ -54,7 +54,7 @@ def test_cuda_graph_capture_of_run_cycle():
         graph.replay()
         graph.replay()
         torch.cuda.synchronize()
-        ref.set_launch(0, 1, mode, 64)
+        ref.set_launch(0, 1, mode, 64, 32)
         ref.run_cycle(2)
         ref.run_cycle(2)
         ref.run_cycle(2)

@@ -175,7 +175,7 @@ def test_phased_launch_mode_matches_persistent_mode():
         g1 = gpu_grid([d], prec)
         g1.run_cycle(3)
         g2 = gpu_grid([d], prec)
-        g2.set_launch(0, 1, 1, 64)
+        g2.set_launch(0, 1, 1, 64, 32)
         g2.run_cycle(3)
         assert np.array_equal(g1.get_solution(0), g2.get_solution(0))
         s1 = g1.solve_to_tol(1e-11)
@@ -184,14 +184,17 @@ def test_phased_launch_mode_matches_persistent_mode():
         assert np.array_equal(g1.get_solution(0), g2.get_solution(0))
 
 
-@pytest.mark.parametrize("dim,ctas,waves,tile", [(2, 1, 1, 64), (3, 1, 3, 64), (3, 2, 8, 32), (3, 0, 2, 32),
-                                                 (2, 0, 1, 32), (3, 0, 1, 32)])
-def test_launch_shapes_give_identical_results(dim, ctas, waves, tile):
-    d = inputs.random_problem(dim, 6 if dim == 2 else 5, seed=321)
+@pytest.mark.parametrize("dim,n,ctas,waves,tile,slab", [
+    (2, 6, 1, 1, 64, 0), (3, 5, 1, 3, 64, 0), (3, 5, 2, 8, 32, 0), (3, 5, 0, 2, 32, 0), (2, 6, 0, 1, 32, 16),
+    (3, 5, 0, 1, 32, 16),
+    # 129^3: slab_z = 4 puts level 0 on the slab cut
+    (3, 7, 0, 1, 64, 4), (3, 7, 1, 1, 32, 4), (3, 7, 0, 1, 64, 0)])
+def test_launch_shapes_give_identical_results(dim, n, ctas, waves, tile, slab):
+    d = inputs.random_problem(dim, n, seed=321)
     g1 = gpu_grid([d], sgml.MIXED)
     g1.run_cycle(2)
     g2 = gpu_grid([d], sgml.MIXED)
-    g2.set_launch(ctas, waves, 0, tile)
+    g2.set_launch(ctas, waves, 0, tile, slab)
     g2.run_cycle(2)
     assert np.array_equal(g1.get_solution(0), g2.get_solution(0))
 
