@@ -326,7 +326,7 @@ def run_gpu(args):
             "vs_baseline": None, "dtype": "f32+f64" if forms[0] == "mixed" else "f64", "data": "synthetic",
             "config": {"workload": workload_name(n), "form": forms[0], "nodes": M, "cycles": main["cycles"],
                        "rel_residual": main["rel"], "l2": "inputs larger than L2 (working set > 1 GB per replica)",
-                       "tile": f"{args.tile_x}x{512 // args.tile_x}", "slab_z": args.slab_z,
+                       "tile": f"{args.tile_x}x{512 // args.tile_x}",
                        "fused_pair_levels": args.pair_levels,
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
             "roofline": main["roofline"], "cpu_baseline": cpu, "e2e": e2e,
@@ -420,7 +420,8 @@ def main():
     ap.add_argument("--ncu-solve", action="store_true", help="ncu case: one full solve instead of --ncu-cycles")
     ap.add_argument("--phased", action="store_true")
     ap.add_argument("--tile-x", type=int, default=64, choices=[32, 64], help="column tiles 32 x 16 or 64 x 8")
-    ap.add_argument("--slab-z", type=int, default=32, help="z-slab height of the work partition (0: contiguous runs)")
+    ap.add_argument("--slab-z", type=int, default=None,
+                    help="z-slab height of the work partition (0: contiguous runs; default: the library's)")
     ap.add_argument("--pair-levels", type=int, default=0, help="levels whose sweeps run in fused pairs (0: none)")
     ap.add_argument("--trace", action="store_true", help="with --ncu-case: per-phase times from the kernel's trace")
     ap.add_argument("--trace-cycles", type=int, default=64)

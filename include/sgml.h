@@ -142,7 +142,7 @@ int sgml_sigma_gradient(sgml_grid_t g, int problem, const double* lambda, const 
  *     one ordinary launch per phase (for profiling single phases; run_cycle then needs no host
  *     synchronisation and can be captured in a CUDA graph).
  *   tile_x: the column tiles of the tiled phases, 32 (32 x 16 columns) or 64 (64 x 8, the default).
- *   slab_z (default 32): 3-D levels large enough to give every CTA two slabs of work are cut into
+ *   slab_z (default 32 for SGML_MIXED, 0 for SGML_FP64): 3-D levels large enough to give every CTA two slabs of work are cut into
  *     z-slabs of about slab_z planes; the (slab, tile) pieces are dealt to the CTAs in turn, so that
  *     neighbouring tiles are processed at the same time and their shared halo cells are read from
  *     HBM once.  0: contiguous runs on every level.

@@ -437,6 +437,7 @@ int sgml_create_grid(int dim, int batch, const int* n_levels, int precision, voi
   g->dim = dim;
   g->batch = batch;
   g->mixed = precision == SGML_MIXED;
+  g->slab_z = g->mixed ? 32 : 0;  // the FP64 form is FP64-pipe bound: the slab cut's halo planes cost more than it saves
   g->elem = g->mixed ? 4 : 8;
   g->stream = (cudaStream_t)cuda_stream;
   g->P.resize(batch);

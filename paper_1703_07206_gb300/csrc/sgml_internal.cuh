@@ -79,10 +79,9 @@ struct Accum {
 };
 
 struct GridSync {
-  unsigned int count;
-  unsigned int gen;
-  int error;       // 1: a barrier timed out
-  int active[2];   // any problem still active after the check of cycle c (slot c & 1)
+  unsigned long long arrive;  // CTAs arrived at grid barriers so far (round r: r G .. (r + 1) G - 1)
+  int error;                  // 1: a barrier timed out
+  int active[2];              // any problem still active after the check of cycle c (slot c & 1)
   int pad[3];
 };
 

@@ -112,11 +112,6 @@ __device__ __forceinline__ unsigned long long globaltimer() {
   return t;
 }
 
-__device__ __forceinline__ unsigned int ld_acquire(const unsigned int* p) {
-  unsigned int v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
 
 __device__ __forceinline__ int ld_volatile(const int* p) { return *(const volatile int*)p; }
 
@@ -130,29 +125,33 @@ __device__ bool grid_sync(GridSync* gs, unsigned long long timeout_ns) {
   __syncthreads();
   if (threadIdx.x == 0) {
     int ok = 1;
-    unsigned int g = ld_acquire(&gs->gen);
-    __threadfence();
-    unsigned int prev = atomicAdd(&gs->count, 1u);
-    if (prev == gridDim.x - 1) {
-      atomicExch(&gs->count, 0u);
-      __threadfence();
-      atomicAdd(&gs->gen, 1u);
-    } else {
-      unsigned long long t0 = globaltimer();
-      while (ld_acquire(&gs->gen) == g) {
-        if (ld_volatile(&gs->error)) {
-          ok = 0;
-          break;
+    const unsigned long long G = gridDim.x;
+    unsigned long long old;
+    // arrival: release (the CTA's writes, ordered before by the CTA barrier, become visible)
+    asm volatile("atom.add.release.gpu.u64 %0, [%1], 1;" : "=l"(old) : "l"(&gs->arrive) : "memory");
+    const unsigned long long target = (old / G + 1) * G;  // every CTA of this round has arrived
+    unsigned long long seen;
+    asm volatile("ld.relaxed.gpu.u64 %0, [%1];" : "=l"(seen) : "l"(&gs->arrive) : "memory");
+    if (seen < target) {
+      const unsigned long long t0 = globaltimer();
+      unsigned spins = 0;
+      for (;;) {
+        asm volatile("ld.relaxed.gpu.u64 %0, [%1];" : "=l"(seen) : "l"(&gs->arrive) : "memory");
+        if (seen >= target) break;
+        if ((++spins & 31u) == 0u) {
+          if (ld_volatile(&gs->error)) {
+            ok = 0;
+            break;
+          }
+          if (globaltimer() - t0 > timeout_ns) {
+            atomicExch(&gs->error, 1);
+            ok = 0;
+            break;
+          }
         }
-        if (globaltimer() - t0 > timeout_ns) {
-          atomicExch(&gs->error, 1);
-          ok = 0;
-          break;
-        }
-        __nanosleep(64);
       }
     }
-    __threadfence();
+    asm volatile("fence.acq_rel.gpu;" ::: "memory");  // acquire: the other CTAs' writes are visible
     if (ld_volatile(&gs->error)) ok = 0;
     s_ok = ok;
   }

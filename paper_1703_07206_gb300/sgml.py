@@ -241,10 +241,12 @@ class Grid:
         _check(lib.sgml_get_phases(self._h, buf, cnt.value, ctypes.byref(cnt)))
         return [tuple(buf[4 * q:4 * q + 4]) for q in range(cnt.value)]
 
-    def set_launch(self, ctas_per_sm=0, z_waves=1, mode=0, tile_x=64, slab_z=32):
+    def set_launch(self, ctas_per_sm=0, z_waves=1, mode=0, tile_x=64, slab_z=None):
         """mode 0: one persistent cooperative launch per call; mode 1: one launch per phase;
         tile_x 32 (32 x 16 column tiles) or 64 (64 x 8); slab_z: z-slab height of the slab cut of
-        large 3-D levels (0: contiguous runs)."""
+        large 3-D levels (0: contiguous runs; None: 32 for the mixed form, 0 for FP64)."""
+        if slab_z is None:
+            slab_z = 32 if self.precision == MIXED else 0
         _check(load().sgml_set_launch(self._h, ctas_per_sm, z_waves, mode, tile_x, slab_z))
 
     def set_trace(self, cycles):
