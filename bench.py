@@ -193,6 +193,7 @@ def make_grid(d, precision, stream):
     g.set_params(max_cycles=args_global.max_cycles)
     g.set_launch(0, 1, 0, args_global.tile_x, args_global.slab_z)
     g.set_fusion(args_global.pair_levels)
+    g.set_quad(args_global.quad_levels)
     return g
 
 
@@ -269,8 +270,10 @@ def run_gpu(args):
         value = world * M / (ms / 1e3)
         achieved = BYTES_PER_NODE_CYCLE[form] * M * cycles / (kernel_ms / 1e3) / 1e9
         tr = traffic.get(form)
+        ctas, threads, smem = g.launch_info()
         results[form] = {"value": value, "ms_per_step": ms, "kernel_ms": kernel_ms, "cycles": cycles, "rel": rel,
                          "launches_per_step": launches / steps, "steps": steps, "clocks": clk.summary(),
+                         "launch": {"ctas": ctas, "threads_per_cta": threads, "smem_bytes_per_cta": smem},
                          "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                                       "frac": achieved / peak,
                                       "traffic": (tr * M * cycles if tr is not None else None),
@@ -327,7 +330,8 @@ def run_gpu(args):
             "config": {"workload": workload_name(n), "form": forms[0], "nodes": M, "cycles": main["cycles"],
                        "rel_residual": main["rel"], "l2": "inputs larger than L2 (working set > 1 GB per replica)",
                        "tile": f"{args.tile_x}x{512 // args.tile_x}",
-                       "fused_pair_levels": args.pair_levels,
+                       "fused_pair_levels": args.pair_levels, "four_row_levels": args.quad_levels,
+                       "launch": main["launch"],
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
             "roofline": main["roofline"], "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": int(round(main["launches_per_step"] * main["steps"])), "clocks": main["clocks"]}
@@ -380,6 +384,7 @@ def run_ncu_case(args):
     g = sgml.Grid(3, [args.n], precision=prec)
     g.set_launch(0, 1, 1 if args.phased else 0, args.tile_x, args.slab_z)
     g.set_fusion(args.pair_levels)
+    g.set_quad(args.quad_levels)
     sgml.problem_into_grid(g, 0, d)
     g.run_cycle(1)  # warm-up launch (and setup)
     if args.trace:
@@ -423,6 +428,7 @@ def main():
     ap.add_argument("--slab-z", type=int, default=None,
                     help="z-slab height of the work partition (0: contiguous runs; default: the library's)")
     ap.add_argument("--pair-levels", type=int, default=0, help="levels whose sweeps run in fused pairs (0: none)")
+    ap.add_argument("--quad-levels", type=int, default=0, help="levels whose sweeps run four rows per thread")
     ap.add_argument("--trace", action="store_true", help="with --ncu-case: per-phase times from the kernel's trace")
     ap.add_argument("--trace-cycles", type=int, default=64)
     args = ap.parse_args()

@@ -158,6 +158,14 @@ int sgml_set_launch(sgml_grid_t g, int ctas_per_sm, int z_waves, int mode, int t
  * the next cycle. */
 int sgml_set_fusion(sgml_grid_t g, int pair_levels);
 
+/* Four-row sweeps (3-D, SGML_MIXED): on levels 0 .. quad_levels - 1 (default 0: off) the
+ * relaxation sweeps run on tiles of 64 x 16 (or 32 x 32) columns with four nodes per thread,
+ * instead of 64 x 8 (32 x 16) with two: fewer shared-memory loads and less pipeline overhead per
+ * node.  The same Jacobi sweep (Eq. 2 with Eq. 5); only the rounding order of the neighbour sums
+ * differs.  0 turns it off; ignored for 2-D grids and the FP64 form.  Takes effect at the next
+ * cycle. */
+int sgml_set_quad(sgml_grid_t g, int quad_levels);
+
 /* The cycle's phase table as the library runs it (Algorithm 3's schedule: restriction passes, then
  * the visits with their interpolation / injection steps).  Writes 4 ints per phase to out
  * (op: 0 restrict, 1 sweep, 2 interpolate to the finer level, 3 inject to the coarser level; the
@@ -175,6 +183,11 @@ int sgml_set_trace(sgml_grid_t g, int cycles);
  * slot 2 the convergence check, slots 3 .. the phases of the cycle's schedule in order.  Each span
  * includes the grid barrier that ends it.  cap bounds the doubles written.  Synchronises. */
 int sgml_get_trace(sgml_grid_t g, double* us, int cap, int* nphases, int* ncycles);
+
+/* Launch geometry of the cycle kernel for the grid's current settings: CTAs (all co-resident:
+ * SMs x CTAs per SM from the occupancy calculator), threads per CTA, dynamic shared memory per CTA
+ * in bytes.  Builds the work tables if needed (synchronises). */
+int sgml_get_launch_info(sgml_grid_t g, int* ctas, int* threads_per_cta, int* smem_bytes);
 
 /* Number of kernel launches the library issued on this grid since creation (every kernel,
  * setup included). */

@@ -50,6 +50,8 @@ struct sgml_grid {
   long long* d_rows = nullptr;
   TileTask* d_tasks = nullptr;
   int* d_task_off = nullptr;
+  TileTask* d_tasks4 = nullptr;  // tiles of the four-row sweep
+  int* d_task_off4 = nullptr;
   double* d_hist = nullptr;
   int hist_cap = 0;
   double *U = nullptr, *F = nullptr, *SIG64 = nullptr, *A64 = nullptr;
@@ -66,6 +68,7 @@ struct sgml_grid {
   int tile_x = 64;  // 32 (32 x 16 tiles) or 64 (64 x 8 tiles)
   int slab_z = 32;  // slab height of the slab cut of large 3-D levels (0: contiguous runs only)
   int pair_levels = 0;  // levels whose sweeps run in fused pairs (3-D mixed form only; off by default)
+  int quad_levels = 0;  // levels whose sweeps run four rows per thread (3-D mixed form only; off by default)
   int mode = 0;  // 0: one persistent cooperative launch per call, 1: one launch per phase
   bool dirty_coeffs = true, dirty_desc = true, dirty_phases = true, dirty_tiles = true, fresh = true;
   long long launches = 0;
@@ -162,6 +165,7 @@ static std::vector<Phase> build_phases(int n_max, int n_r, int pair_levels) {
 }
 
 static int effective_pair_levels(const sgml_grid* g) { return (g->dim == 3 && g->mixed) ? g->pair_levels : 0; }
+static int effective_quad_levels(const sgml_grid* g) { return (g->dim == 3 && g->mixed) ? g->quad_levels : 0; }
 
 static int upload_phases(sgml_grid* g) {
   std::vector<Phase> ph = build_phases(g->n_max, g->n_r, effective_pair_levels(g));
@@ -199,38 +203,55 @@ static int upload_tiles(sgml_grid* g) {
   // z_waves equal pieces per CTA: piece j goes to CTA j mod G (z_waves = 1: one contiguous share each)
   // (the slab cut deals its pieces to the CTAs itself: z_waves does not apply)
   const int G = g->blocks, W = g->slab_z > 0 ? 1 : g->z_waves, Gp = G * W;
-  const int tx = g->tile_x, ty = 2 * kThreads / g->tile_x;
-  std::vector<TileTask> pieces((size_t)partition_bound(g->dim, nb.data(), g->batch, Gp, tx, ty, g->slab_z));
-  std::vector<int> poff((size_t)kMaxLevels * (Gp + 1));
-  pieces.resize(build_partition(g->dim, nb.data(), dir_hi.data(), g->batch, Gp, tx, ty, pieces.data(), poff.data(),
-                                g->slab_z));
-  std::vector<TileTask> tasks;
-  tasks.reserve(pieces.size());
-  std::vector<int> toff((size_t)kMaxLevels * (G + 1));
-  for (int l = 0; l < kMaxLevels; ++l) {
-    const int* po = poff.data() + (size_t)l * (Gp + 1);
-    int* o = toff.data() + (size_t)l * (G + 1);
-    for (int c = 0; c < G; ++c) {
-      o[c] = (int)tasks.size();
-      for (int w = 0; w < W; ++w) {
-        const int j = c + w * G;
-        for (int t = po[j]; t < po[j + 1]; ++t) tasks.push_back(pieces[t]);
+  auto partition = [&](int tx, int ty, std::vector<TileTask>& tasks, std::vector<int>& toff) {
+    std::vector<TileTask> pieces((size_t)partition_bound(g->dim, nb.data(), g->batch, Gp, tx, ty, g->slab_z));
+    std::vector<int> poff((size_t)kMaxLevels * (Gp + 1));
+    pieces.resize(build_partition(g->dim, nb.data(), dir_hi.data(), g->batch, Gp, tx, ty, pieces.data(),
+                                  poff.data(), g->slab_z));
+    tasks.clear();
+    tasks.reserve(pieces.size());
+    toff.assign((size_t)kMaxLevels * (G + 1), 0);
+    for (int l = 0; l < kMaxLevels; ++l) {
+      const int* po = poff.data() + (size_t)l * (Gp + 1);
+      int* o = toff.data() + (size_t)l * (G + 1);
+      for (int c = 0; c < G; ++c) {
+        o[c] = (int)tasks.size();
+        for (int w = 0; w < W; ++w) {
+          const int j = c + w * G;
+          for (int t = po[j]; t < po[j + 1]; ++t) tasks.push_back(pieces[t]);
+        }
       }
+      o[G] = (int)tasks.size();
     }
-    o[G] = (int)tasks.size();
-  }
+  };
+  std::vector<TileTask> tasks, tasks4;
+  std::vector<int> toff, toff4;
+  partition(g->tile_x, 2 * kThreads / g->tile_x, tasks, toff);
+  if (effective_quad_levels(g) > 0) partition(g->tile_x, 4 * kThreads / g->tile_x, tasks4, toff4);
   if (g->d_rows) SGML_CUDA(cudaFree(g->d_rows));
   if (g->d_tasks) SGML_CUDA(cudaFree(g->d_tasks));
   if (g->d_task_off) SGML_CUDA(cudaFree(g->d_task_off));
+  if (g->d_tasks4) SGML_CUDA(cudaFree(g->d_tasks4));
+  if (g->d_task_off4) SGML_CUDA(cudaFree(g->d_task_off4));
   g->d_rows = nullptr;
   g->d_tasks = nullptr;
   g->d_task_off = nullptr;
+  g->d_tasks4 = nullptr;
+  g->d_task_off4 = nullptr;
   SGML_CUDA(cudaMalloc(&g->d_rows, sizeof(long long) * rp.size()));
   SGML_CUDA(cudaMalloc(&g->d_tasks, sizeof(TileTask) * std::max<size_t>(tasks.size(), 1)));
   SGML_CUDA(cudaMalloc(&g->d_task_off, sizeof(int) * toff.size()));
   SGML_CUDA(cudaMemcpyAsync(g->d_rows, rp.data(), sizeof(long long) * rp.size(), cudaMemcpyHostToDevice, g->stream));
   SGML_CUDA(cudaMemcpyAsync(g->d_tasks, tasks.data(), sizeof(TileTask) * tasks.size(), cudaMemcpyHostToDevice, g->stream));
   SGML_CUDA(cudaMemcpyAsync(g->d_task_off, toff.data(), sizeof(int) * toff.size(), cudaMemcpyHostToDevice, g->stream));
+  if (!tasks4.empty()) {
+    SGML_CUDA(cudaMalloc(&g->d_tasks4, sizeof(TileTask) * tasks4.size()));
+    SGML_CUDA(cudaMalloc(&g->d_task_off4, sizeof(int) * toff4.size()));
+    SGML_CUDA(cudaMemcpyAsync(g->d_tasks4, tasks4.data(), sizeof(TileTask) * tasks4.size(), cudaMemcpyHostToDevice,
+                              g->stream));
+    SGML_CUDA(cudaMemcpyAsync(g->d_task_off4, toff4.data(), sizeof(int) * toff4.size(), cudaMemcpyHostToDevice,
+                              g->stream));
+  }
   SGML_CUDA(cudaStreamSynchronize(g->stream));
   g->dirty_tiles = false;
   return SGML_OK;
@@ -348,6 +369,9 @@ static int launch(sgml_grid* g, int max_cycles, double tol) {
   p.nphases = g->nphases;
   p.tasks = g->d_tasks;
   p.task_off = g->d_task_off;
+  p.tasks4 = g->d_tasks4;
+  p.task_off4 = g->d_task_off4;
+  p.quad_levels = g->d_tasks4 ? effective_quad_levels(g) : 0;
   p.row_prefix = g->d_rows;
   p.fresh = fresh ? 1 : 0;
   p.max_cycles = max_cycles;
@@ -705,6 +729,14 @@ int sgml_set_fusion(sgml_grid_t g, int pair_levels) {
   return SGML_OK;
 }
 
+int sgml_set_quad(sgml_grid_t g, int quad_levels) {
+  if (!valid(g)) return fail(SGML_ERR_ARG, "invalid grid");
+  if (quad_levels < 0 || quad_levels > kMaxLevels) return fail(SGML_ERR_ARG, "quad_levels must be in 0..13");
+  g->quad_levels = quad_levels;
+  g->dirty_tiles = true;
+  return SGML_OK;
+}
+
 int sgml_get_phases(sgml_grid_t g, int* out, int cap, int* count) {
   if (!valid(g) || !count || (cap > 0 && !out)) return fail(SGML_ERR_ARG, "invalid grid or output");
   const std::vector<Phase> ph = build_phases(g->n_max, g->n_r, effective_pair_levels(g));
@@ -754,6 +786,16 @@ int sgml_get_trace(sgml_grid_t g, double* us, int cap, int* nphases, int* ncycle
   return SGML_OK;
 }
 
+int sgml_get_launch_info(sgml_grid_t g, int* ctas, int* threads_per_cta, int* smem_bytes) {
+  if (!valid(g) || !ctas || !threads_per_cta || !smem_bytes) return fail(SGML_ERR_ARG, "invalid grid or NULL output");
+  int st;
+  if ((st = prepare(g)) != SGML_OK) return st;
+  *ctas = g->blocks;
+  *threads_per_cta = kThreads;
+  *smem_bytes = (int)(g->tile_x == 32 ? sgml_t32::cycle_kernel_smem(g->mixed) : sgml_t64::cycle_kernel_smem(g->mixed));
+  return SGML_OK;
+}
+
 int sgml_launch_count(sgml_grid_t g, long long* count) {
   if (!valid(g) || !count) return fail(SGML_ERR_ARG, "invalid grid or count NULL");
   *count = g->launches;
@@ -765,7 +807,7 @@ int sgml_destroy(sgml_grid_t g) {
   cudaStreamSynchronize(g->stream);
   void* ptrs[] = {g->U, g->F, g->SIG64, g->A64, g->RESP, g->A0, g->E, g->E2, g->B, g->R, g->SIG, g->Q,
                   g->d_probs, g->d_state, g->d_accum, g->d_sync, g->d_phases, g->d_rows, g->d_tasks,
-                  g->d_task_off, g->d_hist, g->d_trace};
+                  g->d_task_off, g->d_tasks4, g->d_task_off4, g->d_hist, g->d_trace};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (g->h_state) cudaFreeHost(g->h_state);

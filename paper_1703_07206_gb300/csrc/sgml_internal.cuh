@@ -106,6 +106,9 @@ struct KernelParams {
   int nphases;
   const TileTask* tasks;         // column-tile pieces of every level
   const int* task_off;           // [kMaxLevels][gridDim.x + 1]: CTA c owns tasks[off[c] .. off[c + 1])
+  const TileTask* tasks4;        // the same for the tiles of the four-row sweep (kTX x 4 kThreads / kTX)
+  const int* task_off4;
+  int quad_levels;               // levels 0 .. quad_levels - 1 sweep with four rows per thread
   const long long* row_prefix;   // [kMaxLevels][batch + 1] cumulative node-row counts per level
   int fresh;                     // lift u and measure f first
   int max_cycles;
@@ -149,6 +152,7 @@ cudaError_t launch_fill(double* dst, long long n, double v, cudaStream_t s);
   cudaError_t launch_phase_kernel(const sgml::KernelParams& p, int precision_mixed, int dim, int blocks,  \
                                   int threads, int which, int c, cudaStream_t s);                        \
   int cycle_kernel_occupancy(int precision_mixed, int dim, int threads, int* blocks_per_sm);            \
+  size_t cycle_kernel_smem(int precision_mixed);                                                        \
   }
 SGML_TILED_LAUNCHERS(sgml_t32)
 SGML_TILED_LAUNCHERS(sgml_t64)

@@ -54,9 +54,12 @@ _SIGNATURES = {
     "sgml_residual": [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p],
     "sgml_sigma_gradient": [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
     "sgml_set_fusion": [ctypes.c_void_p, ctypes.c_int],
+    "sgml_set_quad": [ctypes.c_void_p, ctypes.c_int],
     "sgml_get_phases": [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.POINTER(ctypes.c_int)],
     "sgml_set_launch": [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int],
     "sgml_launch_count": [ctypes.c_void_p, ctypes.POINTER(ctypes.c_longlong)],
+    "sgml_get_launch_info": [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                             ctypes.POINTER(ctypes.c_int)],
     "sgml_set_trace": [ctypes.c_void_p, ctypes.c_int],
     "sgml_get_trace": [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                        ctypes.POINTER(ctypes.c_int)],
@@ -232,6 +235,10 @@ class Grid:
         """Levels 0 .. pair_levels - 1 run their sweeps in fused pairs (3-D mixed form; 0: off)."""
         _check(load().sgml_set_fusion(self._h, pair_levels))
 
+    def set_quad(self, quad_levels=1):
+        """Levels 0 .. quad_levels - 1 sweep with four rows per thread (3-D mixed form; 0: off)."""
+        _check(load().sgml_set_quad(self._h, quad_levels))
+
     def get_phases(self):
         """The cycle's phase table: list of (op, level, first sweep, sweeps performed)."""
         lib = load()
@@ -258,6 +265,12 @@ class Grid:
         npx, ncy = ctypes.c_int(), ctypes.c_int()
         _check(load().sgml_get_trace(self._h, buf, cap, ctypes.byref(npx), ctypes.byref(ncy)))
         return np.array(buf[: npx.value * ncy.value]).reshape(ncy.value, npx.value)
+
+    def launch_info(self):
+        """(CTAs, threads per CTA, dynamic shared memory bytes per CTA) of the cycle kernel."""
+        a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(load().sgml_get_launch_info(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+        return a.value, b.value, c.value
 
     def launch_count(self):
         c = ctypes.c_longlong()

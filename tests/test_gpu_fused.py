@@ -1,4 +1,4 @@
-"""Fused sweep pairs (3-D, mixed form) against the FP64 oracle.
+"""Fused sweep pairs and four-row sweeps (3-D, mixed form) against the FP64 oracle.
 
 With fusion the k sweeps of a visit (Algorithm 2) run two at a time: the first sweep is evaluated on
 each tile widened by one cell and kept on chip for the second.  It is the same Jacobi iteration, so
@@ -101,3 +101,52 @@ def test_phase_table_pairs_sweeps_on_fused_levels():
     g3 = gpu_grid([d], sgml.FP64)
     g3.set_fusion(13)
     assert all(q[3] <= 1 for q in g3.get_phases())
+
+
+# --- four-row sweeps (tiles of 64 x 16 / 32 x 32 columns, four nodes per thread) ---------------
+
+def quad_grid(problems, quad_levels, tile_x=64, **params):
+    g = gpu_grid(problems, sgml.MIXED, **params)
+    g.set_fusion(0)
+    g.set_quad(quad_levels)
+    g.set_launch(0, 1, 0, tile_x, 32)
+    return g
+
+
+@pytest.mark.parametrize("name,make", CASES, ids=[c[0] for c in CASES])
+@pytest.mark.parametrize("quad_levels", [1, 13])
+@pytest.mark.parametrize("n_r", [1, 2, 3])
+def test_four_row_sweeps_match_oracle(name, make, quad_levels, n_r):
+    d = make()
+    p = oracle_problem(d, n_r=n_r)
+    u_ref = oracle_cycles(p, d["f"], 2)
+    g = quad_grid([d], quad_levels, n_r=n_r)
+    g.run_cycle(2)
+    u = g.get_solution(0)
+    assert rel_l2(u, u_ref) <= 2e-5, rel_l2(u, u_ref)
+    g0 = quad_grid([d], 0, n_r=n_r)
+    g0.run_cycle(2)
+    assert rel_l2(u, g0.get_solution(0)) <= 1e-5
+
+
+@pytest.mark.parametrize("flux", [False, True])
+def test_four_row_sweeps_ragged_65cubed_and_tile_shapes(flux):
+    """65^3 with edge tiles one node wide; 64 x 16 and 32 x 32 tiles give identical results."""
+    d = inputs.random_problem(3, 6, seed=650 + int(flux), flux=flux)
+    u_ref = oracle_cycles(oracle_problem(d), d["f"], 1)
+    sols = []
+    for tile_x in (64, 32):
+        g = quad_grid([d], 13, tile_x=tile_x)
+        g.run_cycle(1)
+        sols.append(g.get_solution(0))
+        assert rel_l2(sols[-1], u_ref) <= 2e-5
+    assert np.array_equal(sols[0], sols[1])
+
+
+def test_four_row_sweeps_batch_with_uneven_sweep_counts():
+    probs = [inputs.random_problem(3, n, seed=660 + n, flux=(n == 4)) for n in (5, 3, 4)]
+    g = quad_grid(probs, 13, n_r=4)
+    g.run_cycle(2)
+    for b, d in enumerate(probs):
+        u_ref = oracle_cycles(oracle_problem(d, n_r=4), d["f"], 2)
+        assert rel_l2(g.get_solution(b), u_ref) <= 2e-5, b
