@@ -163,11 +163,41 @@ __device__ bool grid_sync(GridSync* gs, unsigned long long timeout_ns) {
 // Work distribution.  Tiled phases take column tiles (TileTask) of one level, CTA c handling tasks
 // c, c + G, ...; row phases take node rows (fixed y, z) of one level, one row per warp.
 // ---------------------------------------------------------------------------------------------
+// Per-CTA copies of the launch-constant tables, loaded once at kernel start: the first
+// kPhaseCache phases of the schedule, this CTA's task range of every level and its first
+// kTaskCache tasks per level.  A phase then starts without a chain of dependent global loads
+// (the coarse levels' phases are short enough for those latencies to matter).
+constexpr int kPhaseCache = 128, kTaskCache = 2;
+__shared__ Phase s_phase[kPhaseCache];
+__shared__ int s_toff[kMaxLevels][2];
+__shared__ TileTask s_task[kMaxLevels][kTaskCache];
+
+__device__ void load_tables(const KernelParams& p) {
+  for (int i = threadIdx.x; i < p.nphases && i < kPhaseCache; i += blockDim.x) s_phase[i] = p.phases[i];
+  if (threadIdx.x < kMaxLevels) {
+    const int l = threadIdx.x;
+    const int* o = p.task_off + (long long)l * (gridDim.x + 1) + blockIdx.x;
+    const int t0 = o[0], t1 = o[1];
+    s_toff[l][0] = t0;
+    s_toff[l][1] = t1;
+    for (int j = 0; j < kTaskCache && t0 + j < t1; ++j) s_task[l][j] = p.tasks[t0 + j];
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ Phase phase_at(const KernelParams& p, int q) {
+  return q < kPhaseCache ? s_phase[q] : p.phases[q];
+}
+
+__device__ __forceinline__ TileTask task_at(const KernelParams& p, int l, int t) {
+  const int j = t - s_toff[l][0];
+  return j < kTaskCache ? s_task[l][j] : p.tasks[t];
+}
+
 template <class Body>
 __device__ __forceinline__ void for_tasks(const KernelParams& p, int l, Body&& body) {
-  const int* o = p.task_off + (long long)l * (gridDim.x + 1) + blockIdx.x;
-  const int t0 = o[0], t1 = o[1];
-  for (int t = t0; t < t1; ++t) body(p.tasks[t]);
+  const int t0 = s_toff[l][0], t1 = s_toff[l][1];
+  for (int t = t0; t < t1; ++t) body(task_at(p, l, t));
 }
 
 // Rows of level l of all problems; body(b, N, y, z) runs on one warp (lanes cover x).
@@ -664,8 +694,7 @@ __device__ __forceinline__ ResSrc<T> recur_src(const KernelParams& p, const Prob
 template <typename T, typename V>
 __device__ void residual2(const KernelParams& p, int c, ResStage<V>* st, bool anchor) {
   constexpr int D = kOuterStages;
-  const int* o = p.task_off + blockIdx.x;  // level 0
-  const int t0 = o[0], J = o[1] - o[0];
+  const int t0 = s_toff[0][0], J = s_toff[0][1] - s_toff[0][0];  // level 0
   const int tid = threadIdx.x;
   const int b0 = (2 * (tid / kTX)) * kHX + (tid % kTX);
   auto task = [&](int j) -> const TileTask& { return p.tasks[t0 + j]; };
@@ -1022,8 +1051,7 @@ template <typename T, bool LAST>
 __device__ void sweep2(const KernelParams& p, const Phase& ph, int c, SweepStage<T>* st) {
   constexpr int D = kSweepStages;
   const int l = ph.level;
-  const int* o = p.task_off + (long long)l * (gridDim.x + 1) + blockIdx.x;
-  const int t0 = o[0], J = o[1] - o[0];
+  const int t0 = s_toff[l][0], J = s_toff[l][1] - s_toff[l][0];
   const int tid = threadIdx.x;
   const int b0 = (2 * (tid / kTX)) * kHX + (tid % kTX);
   auto task = [&](int j) -> const TileTask& { return p.tasks[t0 + j]; };
@@ -1860,6 +1888,7 @@ __device__ __forceinline__ void run_phase(const KernelParams& p, const Phase& ph
 template <typename T, int DIM>
 __global__ void __launch_bounds__(kThreads, SGML_MIN_CTAS) cycle_kernel(const KernelParams p) {
   extern __shared__ __align__(16) unsigned char sm[];
+  load_tables(p);
   if (p.fresh) {
     phase_lift<T, DIM>(p);
     if (!grid_sync(p.sync, p.timeout_ns)) return;
@@ -1879,7 +1908,7 @@ __global__ void __launch_bounds__(kThreads, SGML_MIN_CTAS) cycle_kernel(const Ke
     stamp(c, 2);
     if (!ld_volatile(&p.sync->active[c & 1])) break;
     for (int q = 0; q < p.nphases; ++q) {
-      const Phase ph = p.phases[q];
+      const Phase ph = phase_at(p, q);
       run_phase<T, DIM>(p, ph, c, sm);
       if (!grid_sync(p.sync, p.timeout_ns)) return;
       stamp(c, 3 + q);
@@ -1892,6 +1921,7 @@ __global__ void __launch_bounds__(kThreads, SGML_MIN_CTAS) cycle_kernel(const Ke
 template <typename T, int DIM>
 __global__ void __launch_bounds__(kThreads, SGML_MIN_CTAS) phase_kernel(const KernelParams p, int which, int c) {
   extern __shared__ __align__(16) unsigned char sm[];
+  load_tables(p);
   if (which == -3) {
     phase_lift<T, DIM>(p);
   } else if (which == -2) {
@@ -1899,7 +1929,7 @@ __global__ void __launch_bounds__(kThreads, SGML_MIN_CTAS) phase_kernel(const Ke
   } else if (which == -1) {
     if (blockIdx.x == 0) phase_check<T, DIM>(p, c);
   } else {
-    const Phase ph = p.phases[which];
+    const Phase ph = phase_at(p, which);
     run_phase<T, DIM>(p, ph, c, sm);
   }
 }
