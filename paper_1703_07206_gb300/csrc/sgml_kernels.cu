@@ -653,6 +653,139 @@ __device__ void residual3(const KernelParams& p, const TileTask& tk, int c, ResS
   block_flush((double)mx, (double)s2, &p.accum[tk.b].rmax_bits[c & 1], &p.accum[tk.b].rsum2[c & 1]);
 }
 
+// The FP32 recurrence with each plane's 4 x 3 block read from shared memory once: the block stays
+// in registers for the next plane step, where it is the lower neighbour plane.  The node at plane
+// m accumulates its class sums in the order dz = -1, 0 (step m), +1 (step m + 1) -- the order and
+// arithmetic of residual3, so results are identical to it bit for bit, with a third of its
+// shared-memory loads.
+template <typename V, bool HET>
+__device__ __forceinline__ void res_part(const V a[4][3], const V s[4][3], int dz, const V uc[2], const V sc[2],
+                                         V cls[2][3]) {
+#pragma unroll
+  for (int r = 0; r < 2; ++r)
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        const int dy = i - 1, dx = j - 1;
+        if (dx == 0 && dy == 0 && dz == 0) continue;
+        const int nz = (dx != 0) + (dy != 0) + (dz != 0);
+        const V du = a[r + i][j] - uc[r];
+        if (HET) cls[r][nz - 1] = fma(sc[r] + s[r + i][j], du, cls[r][nz - 1]);
+        else cls[r][nz - 1] += du;
+      }
+}
+
+template <typename T, bool HET>
+__device__ void residual3r(const KernelParams& p, const TileTask& tk, int c, ResStage<T>* st, const ResSrc<T>& src) {
+  using V = T;
+  constexpr int D = kOuterStages;
+  const ProblemDesc& P = p.probs[tk.b];
+  const int N = level_side(P.n, 0);
+  const int tid = threadIdx.x;
+  const Columns cl = own_columns(P, N, tk.x0, tk.y0);
+  const double scale = cast_scale(p, tk.b, c);
+  const float scale32 = (float)scale;
+  T* R0 = (T*)p.R + P.off_lvl[0];
+  float2* RES = p.RESP + P.off_full;
+  const HaloCells hc = halo_cells(P, N, tk.x0, tk.y0, false);
+  const V c0v = (V)(p.kappa / (2.0 * P.h * P.h) * (HET ? 1.0 : 2.0));
+  const V a_s = (V)src.a_scalar;
+  const V w_e = (V)p.w_edge, w_c = (V)p.w_corner;
+  const int b0 = (2 * (tid / kTX)) * kHX + (tid % kTX);
+  const int nplanes = tk.nz + 2;
+  const long long NN = (long long)N * N;
+  V mx = (V)0, s2 = (V)0;
+  auto issue = [&](int k) {
+    if (k < nplanes) {
+      ResStage<V>& S = st[k % D];
+      const long long base = (long long)refl(tk.z0 - 1 + k, N) * NN;
+#pragma unroll
+      for (int q = 0; q < kCells; ++q)
+        if (hc.off[q] >= 0) {
+          cp_async_t(&S.u[tid + q * kThreads], src.u + base + hc.off[q]);
+          if (HET) cp_async_t(&S.s[tid + q * kThreads], src.s + base + hc.off[q]);
+        }
+      if (k >= 1 && k <= tk.nz) {
+#pragma unroll
+        for (int r = 0; r < 2; ++r)
+          if (cl.in[r]) {
+            cp_async_t(&S.f[tid + r * kThreads], src.rhs + base + cl.off[r]);
+            if (src.a) cp_async_t(&S.a[tid + r * kThreads], src.a + base + cl.off[r]);
+          }
+      }
+    }
+    cp_async_commit();
+  };
+  for (int k = 0; k < D - 3; ++k) issue(k);
+  V pu[4][3], ps[4][3], puc[2], psc[2], pcls[2][3];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) pu[i][j] = ps[i][j] = (V)0;
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    puc[r] = psc[r] = (V)0;
+    pcls[r][0] = pcls[r][1] = pcls[r][2] = (V)0;
+  }
+  for (int k = 0; k < nplanes; ++k) {
+    cp_async_wait<D - 4>();
+    __syncthreads();
+    issue(k + D - 3);
+    const ResStage<V>& S = st[k % D];
+    V a[4][3], sg[4][3], uc[2], sc[2];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        a[i][j] = S.u[b0 + i * kHX + j];
+        sg[i][j] = HET ? S.s[b0 + i * kHX + j] : (V)0;
+      }
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      uc[r] = a[r + 1][1];
+      sc[r] = HET ? sg[r + 1][1] : (V)1;
+    }
+    if (k >= 2) {  // the nodes of plane k - 1 receive this plane (dz = +1) and are finished
+      res_part<V, HET>(a, sg, 1, puc, psc, pcls);
+      const int z = tk.z0 + k - 2;
+      const bool zf = z_fixed(cl, z, N);
+      const ResStage<V>& S1 = st[(k - 1) % D];
+#pragma unroll
+      for (int r = 0; r < 2; ++r) {
+        if (!cl.in[r] || cl.fixed_xy[r] || zf) continue;
+        const V sum = rn_fma(w_c, pcls[r][2], rn_fma(w_e, pcls[r][1], pcls[r][0]));
+        const V av = src.a ? S1.a[tid + r * kThreads] : a_s;
+        res_finish<T, V>(src, c0v, sum, puc[r], av, S1.f[tid + r * kThreads], scale, scale32, R0, RES,
+                         (long long)z * NN + cl.off[r], mx, s2);
+      }
+    }
+    V cls[2][3];
+#pragma unroll
+    for (int r = 0; r < 2; ++r) cls[r][0] = cls[r][1] = cls[r][2] = (V)0;
+    if (k >= 1) res_part<V, HET>(pu, ps, -1, uc, sc, cls);
+    res_part<V, HET>(a, sg, 0, uc, sc, cls);
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        pu[i][j] = a[i][j];
+        ps[i][j] = sg[i][j];
+      }
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      puc[r] = uc[r];
+      psc[r] = sc[r];
+      pcls[r][0] = cls[r][0];
+      pcls[r][1] = cls[r][1];
+      pcls[r][2] = cls[r][2];
+    }
+  }
+  cp_async_wait<0>();
+  __syncthreads();
+  block_flush((double)mx, (double)s2, &p.accum[tk.b].rmax_bits[c & 1], &p.accum[tk.b].rsum2[c & 1]);
+}
+
 // Residual sources of problem b in cycle c: the anchor (FP64 solution) or the recurrence (FP32
 // correction of the previous cycle).
 template <typename T>
@@ -790,8 +923,13 @@ __device__ void phase_outer(const KernelParams& p, int c, unsigned char* smem) {
       else residual3<T, double, false>(p, tk, c, (ResStage<double>*)smem, src);
     } else {
       const ResSrc<T> src = recur_src<T>(p, P, tk.b, c);
-      if (P.hetero) residual3<T, T, true>(p, tk, c, (ResStage<T>*)smem, src);
-      else residual3<T, T, false>(p, tk, c, (ResStage<T>*)smem, src);
+      if constexpr (sizeof(T) == 4) {
+        if (P.hetero) residual3r<T, true>(p, tk, c, (ResStage<T>*)smem, src);
+        else residual3r<T, false>(p, tk, c, (ResStage<T>*)smem, src);
+      } else {
+        if (P.hetero) residual3<T, T, true>(p, tk, c, (ResStage<T>*)smem, src);
+        else residual3<T, T, false>(p, tk, c, (ResStage<T>*)smem, src);
+      }
     }
   });
 }
@@ -845,12 +983,12 @@ __device__ void phase_check(const KernelParams& p, int c) {
       stop = 1;
     }
     // Mixed form: the next residual is the FP64 anchor when the recurrence may have drifted by a few
-    // per cent of the current residual (it fell a hundred-fold since the last anchor, 32 cycles
+    // per cent of the current residual (it fell a hundred-fold since the last anchor, 64 cycles
     // passed, or the cycle contracts fast), when the tolerance may have been reached, and before
     // the last cycle of the launch.  The FP32 stencil's error is ~1e-7 of the stencil's terms, which
     // exceed |delta L e| by up to ~1/h for smooth e, so the drift grows like 3e-5 * sum |r_i|.
     S.anchor_next = !p.mixed || rho < 0.2 || rel <= 0.01 * S.anchor_rel || rel <= p.tol ||
-                    c + 1 >= p.max_cycles || c + 1 - S.last_anchor >= 32;
+                    c + 1 >= p.max_cycles || c + 1 - S.last_anchor >= 64;
     S.status = st;
     A.done = stop;
     A.rmax_bits[(c + 1) & 1] = 0ull;
