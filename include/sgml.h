@@ -193,6 +193,28 @@ int sgml_get_launch_info(sgml_grid_t g, int* ctas, int* threads_per_cta, int* sm
  * setup included). */
 int sgml_launch_count(sgml_grid_t g, long long* count);
 
+/* ---- Post-processing of the vortex application (Sec. 3.3) -------------------------------------
+ * Velocity from the stream vector potential, v = curl psi (Eq. 14), on the unit cube with
+ * N = 2^n + 1 nodes per side (1 <= n <= 10).  psi and v: device arrays of 3 N^3 doubles, the x, y
+ * and z components one after the other, each row-major [z][y][x]; caller-owned, must not alias.
+ * The paper leaves the differences to its visualisation tool; read here as second-order central
+ * differences inside and second-order one-sided differences (-3 f0 + 4 f1 - f2) / (2h) on the
+ * faces.  Asynchronous on cuda_stream.  SGML_ERR_ARG for a bad n, NULL, aliasing or host arrays. */
+int sgml_curl(int n, const double* psi, double* v, void* cuda_stream);
+
+/* Streamlines of a node velocity field (Sec. 3.3: "a RK-marching scheme"): the classical
+ * fourth-order Runge-Kutta method with fixed step dt, the velocity interpolated trilinearly between
+ * the nodes of v (layout as for sgml_curl), from nseeds seed points (device array, x y z per seed)
+ * for at most nsteps steps.  paths (device, nseeds x (nsteps + 1) x 3 doubles) receives the
+ * positions, seed first; lengths (device, nseeds ints) the number written.  A path ends before a
+ * stage point or its next position would leave the closed unit cube (length 0 for a seed outside
+ * it).  One thread per seed; asynchronous on cuda_stream. */
+int sgml_streamlines(int n, const double* v, const double* seeds, int nseeds, double dt, int nsteps, double* paths,
+                     int* lengths, void* cuda_stream);
+
+/* Message of the last failed sgml_curl / sgml_streamlines call on this thread. */
+const char* sgml_post_last_error(void);
+
 int sgml_destroy(sgml_grid_t g);
 const char* sgml_last_error(void);
 

@@ -77,6 +77,8 @@ def _load():
         lib.orc_solve.argtypes = [P, D, ctypes.c_double, I, D, D]
         lib.orc_solve.restype = I
         lib.orc_sigma_gradient.argtypes = [P, D, D, D]
+        lib.orc_curl.argtypes = [I, D, D]
+        lib.orc_streamlines.argtypes = [I, D, D, I, ctypes.c_double, I, D, ctypes.POINTER(I)]
         _lib = lib
     return _lib
 
@@ -262,3 +264,34 @@ class Problem:
             if self.faces[2 * k + 1] == DIRICHLET:
                 m[tuple(hi)] = False
         return m
+
+
+# --- post-processing of Sec. 3.3 (velocity from the stream vector potential, streamlines) ------
+def curl(psi):
+    """v = curl psi (Eq. 14) on the unit cube: psi of shape (3, N, N, N) (components x, y, z; each
+    indexed [z, y, x]); second-order central differences inside, one-sided on the faces."""
+    psi = np.ascontiguousarray(np.asarray(psi, dtype=np.float64))
+    if psi.ndim != 4 or psi.shape[0] != 3 or psi.shape[1] != psi.shape[2] or psi.shape[2] != psi.shape[3]:
+        raise ValueError("psi must have shape (3, N, N, N)")
+    N = psi.shape[1]
+    n = int(round(np.log2(N - 1)))
+    if 2 ** n + 1 != N:
+        raise ValueError("N must be 2^n + 1")
+    v = np.empty_like(psi)
+    _load().orc_curl(n, _ptr(psi), _ptr(v))
+    return v
+
+
+def streamlines(v, seeds, dt, nsteps):
+    """RK4 streamlines of the node field v (3, N, N, N), trilinear between nodes, from seeds (S, 3)
+    (x, y, z); returns (paths (S, nsteps + 1, 3), lengths (S,)): positions until the path leaves
+    the unit cube or nsteps steps are done."""
+    v = np.ascontiguousarray(np.asarray(v, dtype=np.float64))
+    N = v.shape[1]
+    n = int(round(np.log2(N - 1)))
+    seeds = np.ascontiguousarray(np.asarray(seeds, dtype=np.float64).reshape(-1, 3))
+    S = seeds.shape[0]
+    paths = np.full((S, nsteps + 1, 3), np.nan)
+    lengths = (ctypes.c_int * S)()
+    _load().orc_streamlines(n, _ptr(v), _ptr(seeds), S, float(dt), int(nsteps), _ptr(paths), lengths)
+    return paths, np.array(lengths[:], dtype=np.int64)

@@ -561,3 +561,118 @@ void orc_sigma_gradient(const orc_problem* p, const double* lambda, const double
     g[i] = c0 * acc;
   }
 }
+
+/* ------------------------------------------------------------------------------------------------
+ * Post-processing of Sec. 3.3: velocity v = curl psi (Eq. 14) of the stream vector potential, and
+ * streamlines of v.  The paper leaves the discretisation to its visualisation tool; the readings
+ * taken here: derivatives by second-order central differences at interior nodes and second-order
+ * one-sided differences (-3 f0 + 4 f1 - f2) / (2h) on the faces; streamlines by the classical
+ * fourth-order Runge-Kutta method with a fixed step in the velocity field interpolated trilinearly
+ * between nodes, stopped when a stage point or the next position leaves the unit cube.
+ * ---------------------------------------------------------------------------------------------- */
+
+/* d f / d x_axis at node (i, j, k) of an N^3 array (axis 0: x, 1: y, 2: z). */
+static double orc_deriv(const double* f, int N, double h, int i, int j, int k, int axis) {
+  int idx[3] = {i, j, k};
+  const int m = idx[axis];
+  double a, b, c;
+  int q[3] = {i, j, k};
+#define ORC_AT(t) (q[axis] = (t), f[((long)q[2] * N + q[1]) * N + q[0]])
+  if (m == 0) {
+    a = ORC_AT(0), b = ORC_AT(1), c = ORC_AT(2);
+    return (-3.0 * a + 4.0 * b - c) / (2.0 * h);
+  }
+  if (m == N - 1) {
+    a = ORC_AT(N - 1), b = ORC_AT(N - 2), c = ORC_AT(N - 3);
+    return (3.0 * a - 4.0 * b + c) / (2.0 * h);
+  }
+  a = ORC_AT(m + 1), b = ORC_AT(m - 1);
+  return (a - b) / (2.0 * h);
+#undef ORC_AT
+}
+
+/* psi, v: three components, each an N^3 array, stored one after the other (x, y, z). */
+void orc_curl(int n, const double* psi, double* v) {
+  const int N = (1 << n) + 1;
+  const double h = 1.0 / (double)(N - 1);
+  const long M = (long)N * N * N;
+  const double* px = psi;
+  const double* py = psi + M;
+  const double* pz = psi + 2 * M;
+  for (int k = 0; k < N; ++k)
+    for (int j = 0; j < N; ++j)
+      for (int i = 0; i < N; ++i) {
+        const long c = ((long)k * N + j) * N + i;
+        v[c] = orc_deriv(pz, N, h, i, j, k, 1) - orc_deriv(py, N, h, i, j, k, 2);
+        v[M + c] = orc_deriv(px, N, h, i, j, k, 2) - orc_deriv(pz, N, h, i, j, k, 0);
+        v[2 * M + c] = orc_deriv(py, N, h, i, j, k, 0) - orc_deriv(px, N, h, i, j, k, 1);
+      }
+}
+
+/* Trilinear interpolation of the three components of v at x (inside the closed unit cube). */
+static void orc_interp_v(const double* v, int N, const double x[3], double out[3]) {
+  const long M = (long)N * N * N;
+  const double s = (double)(N - 1);
+  int i0[3];
+  double t[3];
+  for (int a = 0; a < 3; ++a) {
+    double g = x[a] * s;
+    int i = (int)floor(g);
+    if (i < 0) i = 0;
+    if (i > N - 2) i = N - 2;
+    i0[a] = i;
+    t[a] = g - (double)i;
+  }
+  for (int comp = 0; comp < 3; ++comp) {
+    const double* f = v + comp * M;
+    double acc = 0.0;
+    for (int dz = 0; dz < 2; ++dz)
+      for (int dy = 0; dy < 2; ++dy)
+        for (int dx = 0; dx < 2; ++dx) {
+          const double w = (dx ? t[0] : 1.0 - t[0]) * (dy ? t[1] : 1.0 - t[1]) * (dz ? t[2] : 1.0 - t[2]);
+          acc += w * f[((long)(i0[2] + dz) * N + (i0[1] + dy)) * N + (i0[0] + dx)];
+        }
+    out[comp] = acc;
+  }
+}
+
+static int orc_inside(const double x[3]) {
+  for (int a = 0; a < 3; ++a)
+    if (!(x[a] >= 0.0 && x[a] <= 1.0)) return 0;
+  return 1;
+}
+
+/* RK4 streamlines from nseeds seed points (x, y, z each), nsteps steps of size dt.  paths holds
+ * nseeds x (nsteps + 1) x 3 positions (unused entries untouched); lengths[s] = positions written
+ * (1 + completed steps). */
+void orc_streamlines(int n, const double* v, const double* seeds, int nseeds, double dt, int nsteps, double* paths,
+                     int* lengths) {
+  const int N = (1 << n) + 1;
+  for (int sd = 0; sd < nseeds; ++sd) {
+    double x[3] = {seeds[3 * sd], seeds[3 * sd + 1], seeds[3 * sd + 2]};
+    double* out = paths + (long)sd * (nsteps + 1) * 3;
+    int len = 0;
+    if (orc_inside(x)) {
+      out[0] = x[0], out[1] = x[1], out[2] = x[2];
+      len = 1;
+      for (int st = 0; st < nsteps; ++st) {
+        double k1[3], k2[3], k3[3], k4[3], y[3], xn[3];
+        orc_interp_v(v, N, x, k1);
+        for (int a = 0; a < 3; ++a) y[a] = x[a] + 0.5 * dt * k1[a];
+        if (!orc_inside(y)) break;
+        orc_interp_v(v, N, y, k2);
+        for (int a = 0; a < 3; ++a) y[a] = x[a] + 0.5 * dt * k2[a];
+        if (!orc_inside(y)) break;
+        orc_interp_v(v, N, y, k3);
+        for (int a = 0; a < 3; ++a) y[a] = x[a] + dt * k3[a];
+        if (!orc_inside(y)) break;
+        orc_interp_v(v, N, y, k4);
+        for (int a = 0; a < 3; ++a) xn[a] = x[a] + dt / 6.0 * (k1[a] + 2.0 * k2[a] + 2.0 * k3[a] + k4[a]);
+        if (!orc_inside(xn)) break;
+        for (int a = 0; a < 3; ++a) x[a] = xn[a], out[3 * len + a] = xn[a];
+        ++len;
+      }
+    }
+    lengths[sd] = len;
+  }
+}

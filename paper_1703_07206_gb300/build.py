@@ -1,7 +1,7 @@
 """Build libsgml.so (CUDA, sm_103a) in-tree with nvcc.
 
 The kernel unit is compiled once per column-tile width (32 x 16 and 64 x 8 tiles, namespaces
-``sgml_t32`` / ``sgml_t64``), the host units once; the four objects are compiled in parallel and
+``sgml_t32`` / ``sgml_t64``), the host units once; the objects are compiled in parallel and
 linked into ``paper_1703_07206_gb300/_build/libsgml.so``.  Cross-compiles without a GPU.
 """
 from __future__ import annotations
@@ -23,6 +23,7 @@ UNITS = [
     ("sgml_kernels.cu", "k64", ["SGML_TILE_X=64", "SGML_KNS=sgml_t64", "SGML_DEFINE_COMMON"]),
     ("sgml_api.cu", "api", []),
     ("sgml_noalloc.cu", "noalloc", []),
+    ("sgml_post.cu", "post", []),
 ]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -70,6 +70,10 @@ _SIGNATURES = {
                            ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(ctypes.c_int),
                            ctypes.POINTER(ctypes.c_double), ctypes.c_void_p],
     "sgml_noalloc_last_error": [],
+    "sgml_curl": [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
+    "sgml_streamlines": [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                         ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
+    "sgml_post_last_error": [],
 }
 
 
@@ -298,6 +302,54 @@ def solve_noalloc(dim, n, f, u, sigma=None, a_scalar=0.0, faces=None, values=Non
     if st in (ERR_ARG, ERR_CUDA, ERR_BARRIER_TIMEOUT):
         raise SGMLError(st, lib.sgml_noalloc_last_error().decode())
     return st, cyc.value, rel.value
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def curl(psi, stream=None):
+    """v = curl psi (Sec. 3.3, Eq. 14) of a CUDA float64 tensor psi of shape (3, N, N, N) (components
+    x, y, z; each [z, y, x]); returns a new CUDA tensor of the same shape (asynchronous on stream)."""
+    import torch
+    if not (hasattr(psi, "is_cuda") and psi.is_cuda) or psi.dtype != torch.float64:
+        raise TypeError("psi must be a CUDA float64 tensor")
+    psi = psi.contiguous()
+    if psi.dim() != 4 or psi.shape[0] != 3 or not (psi.shape[1] == psi.shape[2] == psi.shape[3]):
+        raise ValueError("psi must have shape (3, N, N, N)")
+    N = psi.shape[1]
+    n = int(round(np.log2(N - 1)))
+    if 2 ** n + 1 != N:
+        raise ValueError("N must be 2^n + 1")
+    v = torch.empty_like(psi)
+    lib = load()
+    st = lib.sgml_curl(n, psi.data_ptr(), v.data_ptr(), _stream_ptr(stream))
+    if st != OK:
+        raise SGMLError(st, lib.sgml_post_last_error().decode())
+    return v
+
+
+def streamlines(v, seeds, dt, nsteps, stream=None):
+    """RK4 streamlines (Sec. 3.3) of the CUDA float64 node field v (3, N, N, N) from seeds (S, 3)
+    (x, y, z); returns CUDA tensors (paths (S, nsteps + 1, 3), lengths (S,) int32)."""
+    import torch
+    if not (hasattr(v, "is_cuda") and v.is_cuda) or v.dtype != torch.float64:
+        raise TypeError("v must be a CUDA float64 tensor")
+    v = v.contiguous()
+    N = v.shape[1]
+    n = int(round(np.log2(N - 1)))
+    seeds = torch.as_tensor(seeds, dtype=torch.float64, device=v.device).reshape(-1, 3).contiguous()
+    S = seeds.shape[0]
+    paths = torch.full((S, nsteps + 1, 3), float("nan"), dtype=torch.float64, device=v.device)
+    lengths = torch.zeros(S, dtype=torch.int32, device=v.device)
+    lib = load()
+    st = lib.sgml_streamlines(n, v.data_ptr(), seeds.data_ptr(), S, float(dt), int(nsteps), paths.data_ptr(),
+                              lengths.data_ptr(), _stream_ptr(stream))
+    if st != OK:
+        raise SGMLError(st, lib.sgml_post_last_error().decode())
+    return paths, lengths
 
 
 def problem_into_grid(grid, b, prob):

@@ -12,6 +12,7 @@ import numpy as np
 import pytest
 from scipy.fft import dstn, idstn
 
+from oracle import oracle
 from oracle.oracle import DIRICHLET, NEUMANN, Problem
 from paper_1703_07206_gb300 import inputs
 
@@ -482,3 +483,73 @@ def test_sampled_residual_equals_full_residual():
     full = p.residual(u, d["f"]).ravel()
     idx = np.random.default_rng(63).choice(full.size, size=50, replace=False)
     assert np.array_equal(p.residual_at(u, d["f"], idx), full[idx])
+
+
+# --- post-processing of Sec. 3.3: v = curl psi (Eq. 14) and streamlines --------------------------
+
+def _axes3(n):
+    N = 2 ** n + 1
+    x = np.linspace(0.0, 1.0, N)
+    Z, Y, X = np.meshgrid(x, x, x, indexing="ij")
+    return X, Y, Z
+
+
+def test_curl_exact_on_quadratic_potentials():
+    """Second-order differences (central inside, one-sided on faces) are exact on quadratics."""
+    X, Y, Z = _axes3(3)
+    psi = np.stack([Y ** 2 + 0.3 * X * Z, Z ** 2 - 0.7 * X * Y, X ** 2 + Y * Z])
+    v = oracle.curl(psi)
+    # curl = (d psi_z/dy - d psi_y/dz, d psi_x/dz - d psi_z/dx, d psi_y/dx - d psi_x/dy)
+    want = np.stack([Z - 2 * Z, 0.3 * X - 2 * X, -0.7 * Y - 2 * Y])
+    assert np.abs(v - want).max() <= 1e-11
+
+
+def test_curl_agrees_with_numpy_gradient():
+    rng = np.random.default_rng(7)
+    N = 17
+    psi = rng.standard_normal((3, N, N, N))
+    h = 1.0 / (N - 1)
+    d = [[np.gradient(psi[c], h, axis=ax, edge_order=2) for ax in range(3)] for c in range(3)]  # axis 0 = z
+    want = np.stack([d[2][1] - d[1][0], d[0][0] - d[2][2], d[1][2] - d[0][1]])
+    assert np.abs(oracle.curl(psi) - want).max() <= 1e-10 * np.abs(want).max()
+
+
+def test_curl_is_divergence_free_inside():
+    rng = np.random.default_rng(8)
+    N = 17
+    psi = rng.standard_normal((3, N, N, N))
+    v = oracle.curl(psi)
+    h = 1.0 / (N - 1)
+    div = sum(np.gradient(v[c], h, axis=2 - c) for c in range(3))
+    assert np.abs(div[2:-2, 2:-2, 2:-2]).max() <= 1e-9 * np.abs(v).max() / h
+
+
+def test_streamline_of_constant_field_is_straight():
+    N = 9
+    c = np.array([0.11, -0.05, 0.07])
+    v = np.stack([np.full((N, N, N), c[k]) for k in range(3)])
+    seeds = np.array([[0.2, 0.5, 0.3], [0.9, 0.1, 0.95]])
+    paths, lengths = oracle.streamlines(v, seeds, dt=0.1, nsteps=40)
+    for s in range(2):
+        L = lengths[s]
+        t = 0.1 * np.arange(L)[:, None]
+        assert np.abs(paths[s, :L] - (seeds[s] + t * c)).max() <= 1e-13
+        # stopped exactly when the next position would leave the cube
+        nxt = seeds[s] + 0.1 * L * c
+        assert L == 41 or not np.all((nxt >= 0) & (nxt <= 1))
+
+
+def test_streamline_of_rigid_rotation_closes():
+    """v = (-(y - 1/2), x - 1/2, 0): trilinear interpolation is exact for linear fields, and RK4
+    closes one revolution (T = 2 pi) to its fourth-order error."""
+    X, Y, Z = _axes3(3)
+    v = np.stack([-(Y - 0.5), X - 0.5, 0.0 * Z])
+    steps = 1000
+    dt = 2 * np.pi / steps
+    seed = np.array([[0.8, 0.5, 0.4]])
+    paths, lengths = oracle.streamlines(v, seed, dt=dt, nsteps=steps)
+    assert lengths[0] == steps + 1
+    r = np.hypot(paths[0, :, 0] - 0.5, paths[0, :, 1] - 0.5)
+    assert np.abs(r - 0.3).max() <= 1e-10
+    assert np.abs(paths[0, -1] - seed[0]).max() <= 1e-9
+    assert np.abs(paths[0, :, 2] - 0.4).max() == 0.0
