@@ -184,6 +184,20 @@ int sgml_set_trace(sgml_grid_t g, int cycles);
  * includes the grid barrier that ends it.  cap bounds the doubles written.  Synchronises. */
 int sgml_get_trace(sgml_grid_t g, double* us, int cap, int* nphases, int* ncycles);
 
+/* Diagnostic pseudo-residual (Sec. 3.1: "the coarsened residual computed while applying the
+ * relaxation at every level with restricted sources and coefficients"): with cycles > 0 the next
+ * launches record, for each problem, each of the first `cycles` cycles of the launch and each level
+ * l, the largest |delta L_l e - r_l| met by that level's sweeps (|e_new - e| / delta tau at a node),
+ * in the units of the residual f - delta L u.  At level 0 it is the residual of the correction
+ * equation itself.  Costs a maximum and a division per node and sweep while on; fused pairs and
+ * four-row tiles are not used meanwhile.  0 turns it off.  Synchronises. */
+int sgml_set_diagnostics(sgml_grid_t g, int cycles);
+
+/* The recorded pseudo-residuals of problem `problem` from the last launch: out[c * 13 + l] for
+ * cycle c and level l (0 for levels the problem does not have or cycles not run); at most cap
+ * doubles; *cycles_out = rows written.  Synchronises. */
+int sgml_get_diagnostics(sgml_grid_t g, int problem, double* out, int cap, int* cycles_out);
+
 /* Launch geometry of the cycle kernel for the grid's current settings: CTAs (all co-resident:
  * SMs x CTAs per SM from the occupancy calculator), threads per CTA, dynamic shared memory per CTA
  * in bytes.  Builds the work tables if needed (synchronises). */

@@ -65,7 +65,8 @@ def _load():
         lib.orc_restriction.argtypes = [P, I, D, D]
         lib.orc_local_step.argtypes = [P, I, D, D, D]
         lib.orc_interpolate_add.argtypes = [P, I, D, D]
-        lib.orc_visit.argtypes = [P, I, I, D, D, D, D]
+        lib.orc_visit.argtypes = [P, I, I, D, D, D, D, D]
+        lib.orc_cycle_diag.argtypes = [P, D, D, D]
         lib.orc_cycle.argtypes = [P, D, D]
         lib.orc_schedule.argtypes = [P, ctypes.POINTER(I), ctypes.POINTER(I), I]
         lib.orc_schedule.restype = I
@@ -183,7 +184,7 @@ class Problem:
         e = self._arr(e).copy()
         r_nu = self.restriction(r, nu)
         sig, a = self.restricted_coeffs(nu)
-        lib.orc_visit(ctypes.byref(self._c), nu, k, _ptr(r_nu), _ptr(sig), _ptr(a), _ptr(e))
+        lib.orc_visit(ctypes.byref(self._c), nu, k, _ptr(r_nu), _ptr(sig), _ptr(a), _ptr(e), None)
         return e
 
     def cycle(self, r):
@@ -192,6 +193,16 @@ class Problem:
         e = self._new()
         lib.orc_cycle(ctypes.byref(self._c), _ptr(r), _ptr(e))
         return e
+
+    def cycle_diag(self, r):
+        """The cycle and its diagnostic pseudo-residuals: (e, d) with d[nu] the largest
+        |delta L_nu e - r_nu| met by the level-nu sweeps of the cycle (Sec. 3.1)."""
+        lib = _load()
+        r = self._arr(r)
+        e = self._new()
+        d = np.zeros(self.n)
+        lib.orc_cycle_diag(ctypes.byref(self._c), _ptr(r), _ptr(e), _ptr(d))
+        return e, d
 
     def schedule(self):
         lib = _load()

@@ -349,9 +349,12 @@ void orc_interpolate_add(const orc_problem* p, int nu, const double* delta, doub
 
 /* One visit of level nu: k forward-Euler (Jacobi) steps of Eq. 2 on the level-nu unknowns with the
  * restricted source r_nu and coefficients, then the change of the visit is interpolated to every
- * node outside the level-nu subset.  e holds the level-nu values in place on the single grid. */
+ * node outside the level-nu subset.  e holds the level-nu values in place on the single grid.
+ * If diag is given, diag[nu] is raised to the largest |delta L_nu e - r_nu| met by the sweeps: the
+ * diagnostic pseudo-residual of Sec. 3.1 ("the coarsened residual computed while applying the
+ * relaxation at every level with restricted sources and coefficients"). */
 void orc_visit(const orc_problem* p, int nu, int k, const double* r_nu, const double* sig_nu,
-               const double* a_nu, double* e) {
+               const double* a_nu, double* e, double* diag) {
   long M = nnodes(p);
   double* saved = (double*)malloc(sizeof(double) * M);
   double* next = (double*)malloc(sizeof(double) * M);
@@ -363,7 +366,9 @@ void orc_visit(const orc_problem* p, int nu, int k, const double* r_nu, const do
       coords(p, i, c);
       if (!on_level(c, p->dim, nu) || is_dirichlet(p, c)) continue;
       double dtau = step_at(p, nu, sig_nu, a_nu, c);
-      next[i] = e[i] + dtau * (op_at(p, nu, sig_nu, a_nu, e, c, 0) - r_nu[i]);
+      double pseudo = op_at(p, nu, sig_nu, a_nu, e, c, 0) - r_nu[i];
+      next[i] = e[i] + dtau * pseudo;
+      if (diag && fabs(pseudo) > diag[nu]) diag[nu] = fabs(pseudo);
     }
     memcpy(e, next, sizeof(double) * M);
   }
@@ -390,17 +395,17 @@ static int sweeps_for(const orc_problem* p, int nu1_exp) {
 /* One visit of Algorithm 3: restriction(nu) of the cycle's source and of the coefficients
  * (lines 4, 7), then k relaxation-interpolations (lines 5, 8, 10). */
 static void restrict_and_visit(const orc_problem* p, int nu, int k, const double* r, double* e,
-                               double* r_nu, double* sig_nu, double* a_nu) {
+                               double* r_nu, double* sig_nu, double* a_nu, double* diag) {
   orc_restriction(p, nu, r, r_nu);
   if (p->sigma) orc_restriction(p, nu, p->sigma, sig_nu);
   if (p->a) orc_restriction(p, nu, p->a, a_nu);
-  orc_visit(p, nu, k, r_nu, p->sigma ? sig_nu : NULL, p->a ? a_nu : NULL, e);
+  orc_visit(p, nu, k, r_nu, p->sigma ? sig_nu : NULL, p->a ? a_nu : NULL, e, diag);
 }
 
 /* The single cycle (Algorithm 3) solving delta L e = r from e = 0.  Teeth nu1 = n-1 .. 0 each visit
  * nu1, nu1-1 (skipped when negative) and nu1 again with min(n_r, 2^(n-nu1)) sweeps per visit; the
  * cycle ends with min(n_r, 2^n) sweeps on level 0. */
-void orc_cycle(const orc_problem* p, const double* r, double* e) {
+static void cycle_impl(const orc_problem* p, const double* r, double* e, double* diag) {
   long M = nnodes(p);
   double* r_nu = (double*)malloc(sizeof(double) * M);
   double* sig_nu = (double*)malloc(sizeof(double) * M);
@@ -410,14 +415,23 @@ void orc_cycle(const orc_problem* p, const double* r, double* e) {
     int k = sweeps_for(p, p->n - nu1);
     for (int nu = nu1; nu >= nu1 - 1; --nu) {
       if (nu < 0) continue;
-      restrict_and_visit(p, nu, k, r, e, r_nu, sig_nu, a_nu);
+      restrict_and_visit(p, nu, k, r, e, r_nu, sig_nu, a_nu, diag);
     }
-    restrict_and_visit(p, nu1, k, r, e, r_nu, sig_nu, a_nu);
+    restrict_and_visit(p, nu1, k, r, e, r_nu, sig_nu, a_nu, diag);
   }
-  restrict_and_visit(p, 0, sweeps_for(p, p->n), r, e, r_nu, sig_nu, a_nu);
+  restrict_and_visit(p, 0, sweeps_for(p, p->n), r, e, r_nu, sig_nu, a_nu, diag);
   free(r_nu);
   free(sig_nu);
   free(a_nu);
+}
+
+void orc_cycle(const orc_problem* p, const double* r, double* e) { cycle_impl(p, r, e, NULL); }
+
+/* The cycle, also returning diag[nu] (nu = 0 .. n-1): the largest diagnostic pseudo-residual
+ * |delta L_nu e - r_nu| over the sweeps of level nu in this cycle. */
+void orc_cycle_diag(const orc_problem* p, const double* r, double* e, double* diag) {
+  for (int nu = 0; nu < p->n; ++nu) diag[nu] = 0.0;
+  cycle_impl(p, r, e, diag);
 }
 
 /* Visit sequence of one cycle (levels, in order); returns the count.  Used to check the schedule. */

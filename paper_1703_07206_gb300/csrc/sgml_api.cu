@@ -73,6 +73,8 @@ struct sgml_grid {
   bool dirty_coeffs = true, dirty_desc = true, dirty_phases = true, dirty_tiles = true, fresh = true;
   long long launches = 0;
   ProblemState* h_state = nullptr;  // pinned
+  unsigned long long* d_diag = nullptr;   // diagnostic pseudo-residuals (sgml_set_diagnostics)
+  int diag_cycles = 0;
   unsigned long long* d_trace = nullptr;  // per-phase timestamps (sgml_set_trace)
   int trace_cycles = 0;
   int trace_last_cycles = 0;
@@ -164,8 +166,14 @@ static std::vector<Phase> build_phases(int n_max, int n_r, int pair_levels) {
   return ph;
 }
 
-static int effective_pair_levels(const sgml_grid* g) { return (g->dim == 3 && g->mixed) ? g->pair_levels : 0; }
-static int effective_quad_levels(const sgml_grid* g) { return (g->dim == 3 && g->mixed) ? g->quad_levels : 0; }
+// Fused pairs and four-row tiles: 3-D mixed form only, and not while diagnostics are recorded
+// (only the single-sweep kernels compute the pseudo-residual).
+static int effective_pair_levels(const sgml_grid* g) {
+  return (g->dim == 3 && g->mixed && !g->d_diag) ? g->pair_levels : 0;
+}
+static int effective_quad_levels(const sgml_grid* g) {
+  return (g->dim == 3 && g->mixed && !g->d_diag) ? g->quad_levels : 0;
+}
 
 static int upload_phases(sgml_grid* g) {
   std::vector<Phase> ph = build_phases(g->n_max, g->n_r, effective_pair_levels(g));
@@ -388,6 +396,11 @@ static int launch(sgml_grid* g, int max_cycles, double tol) {
   p.hist_cap = g->hist_cap;
   p.trace = g->d_trace;
   p.trace_cycles = g->d_trace ? g->trace_cycles : 0;
+  p.diag = g->d_diag;
+  p.diag_cycles = g->d_diag ? g->diag_cycles : 0;
+  if (g->d_diag)
+    SGML_CUDA(cudaMemsetAsync(g->d_diag, 0, sizeof(unsigned long long) * (size_t)g->batch * g->diag_cycles * kMaxLevels,
+                              g->stream));
   if (g->d_trace) {
     SGML_CUDA(cudaMemsetAsync(g->d_trace, 0, sizeof(unsigned long long) * (size_t)g->trace_cycles * (g->nphases + 3), g->stream));
     g->trace_last_cycles = std::min(g->trace_cycles, max_cycles + 1);
@@ -786,6 +799,41 @@ int sgml_get_trace(sgml_grid_t g, double* us, int cap, int* nphases, int* ncycle
   return SGML_OK;
 }
 
+int sgml_set_diagnostics(sgml_grid_t g, int cycles) {
+  if (!valid(g) || cycles < 0 || cycles > 100000) return fail(SGML_ERR_ARG, "invalid grid or cycles");
+  SGML_CUDA(cudaStreamSynchronize(g->stream));
+  if (g->d_diag) SGML_CUDA(cudaFree(g->d_diag));
+  g->d_diag = nullptr;
+  g->diag_cycles = cycles;
+  if (cycles > 0) {
+    const size_t bytes = sizeof(unsigned long long) * (size_t)g->batch * cycles * kMaxLevels;
+    SGML_CUDA(cudaMalloc(&g->d_diag, bytes));
+    SGML_CUDA(cudaMemsetAsync(g->d_diag, 0, bytes, g->stream));
+  }
+  g->dirty_phases = true;  // pairs are not built while diagnostics are on
+  g->dirty_tiles = true;
+  return SGML_OK;
+}
+
+int sgml_get_diagnostics(sgml_grid_t g, int problem, double* out, int cap, int* cycles_out) {
+  if (!valid(g) || problem < 0 || problem >= g->batch || !out || !cycles_out)
+    return fail(SGML_ERR_ARG, "invalid grid, problem or output");
+  if (!g->d_diag) return fail(SGML_ERR_ARG, "diagnostics are off (sgml_set_diagnostics)");
+  SGML_CUDA(cudaStreamSynchronize(g->stream));
+  std::vector<unsigned long long> bits((size_t)g->diag_cycles * kMaxLevels);
+  SGML_CUDA(cudaMemcpy(bits.data(), g->d_diag + (size_t)problem * g->diag_cycles * kMaxLevels,
+                       sizeof(unsigned long long) * bits.size(), cudaMemcpyDeviceToHost));
+  const int n = std::min(g->diag_cycles, cap / kMaxLevels);
+  for (int k = 0; k < n * kMaxLevels; ++k) {
+    unsigned long long b = bits[k];
+    double v;
+    std::memcpy(&v, &b, sizeof(v));
+    out[k] = v;
+  }
+  *cycles_out = n;
+  return SGML_OK;
+}
+
 int sgml_get_launch_info(sgml_grid_t g, int* ctas, int* threads_per_cta, int* smem_bytes) {
   if (!valid(g) || !ctas || !threads_per_cta || !smem_bytes) return fail(SGML_ERR_ARG, "invalid grid or NULL output");
   int st;
@@ -807,7 +855,7 @@ int sgml_destroy(sgml_grid_t g) {
   cudaStreamSynchronize(g->stream);
   void* ptrs[] = {g->U, g->F, g->SIG64, g->A64, g->RESP, g->A0, g->E, g->E2, g->B, g->R, g->SIG, g->Q,
                   g->d_probs, g->d_state, g->d_accum, g->d_sync, g->d_phases, g->d_rows, g->d_tasks,
-                  g->d_task_off, g->d_tasks4, g->d_task_off4, g->d_hist, g->d_trace};
+                  g->d_task_off, g->d_tasks4, g->d_task_off4, g->d_hist, g->d_trace, g->d_diag};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (g->h_state) cudaFreeHost(g->h_state);

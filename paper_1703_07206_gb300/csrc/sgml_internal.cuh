@@ -122,6 +122,8 @@ struct KernelParams {
   unsigned long long timeout_ns;
   double* hist;
   int hist_cap;
+  unsigned long long* diag;   // optional: diagnostic pseudo-residual bits, [batch][diag_cycles][kMaxLevels]
+  int diag_cycles;
   unsigned long long* trace;  // optional: globaltimer after each barrier, [cycle][2 + nphases]
   int trace_cycles;
   double *U, *F, *SIG64, *A64;

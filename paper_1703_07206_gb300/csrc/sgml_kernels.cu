@@ -95,6 +95,26 @@ __device__ __forceinline__ double nan_max(double a, double b) {
   return a > b ? a : b;
 }
 
+// Diagnostic pseudo-residual (Sec. 3.1): the largest |delta L_l e - r_l| met by the sweeps of a
+// level, recorded per problem, cycle and level when the grid asks for it.  At a node it is
+// |e_new - e| / dtau; the CTA's maximum, in the units of the unscaled residual, is merged into
+// diag[(b * diag_cycles + c) * kMaxLevels + l] (non-negative doubles order like their bits).
+__device__ void diag_flush(const KernelParams& p, int b, int c, int l, double mx) {
+  __shared__ double s_dmx[32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if (lane == 0) s_dmx[warp] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double m = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, s_dmx[w]);
+    if (c < p.diag_cycles && m > 0.0)
+      atomicMax(&p.diag[((long long)b * p.diag_cycles + c) * kMaxLevels + l], (unsigned long long)__double_as_longlong(m));
+  }
+  __syncthreads();
+}
+
 // Explicitly rounded arithmetic for the stencil sums and updates: the compiler may otherwise
 // contract a * b + c into an FMA in one copy of inlined or unrolled code and not in another, which
 // would make a node's value depend on which tile, z-piece or loop iteration computed it.  With
@@ -1094,7 +1114,7 @@ __device__ __forceinline__ T sweep_update(const SweepConst<T>& k, const SweepSta
   return rn_fma(k.q_const, rn_fma(-r_i, k.inv_c, rn_mul((T)2, CSe)), rn_mul(k.one_m_omega, e_c));
 }
 
-template <typename T, bool HET, bool LAST>
+template <typename T, bool HET, bool LAST, bool DIAG = false>
 __device__ void sweep3(const KernelParams& p, const Phase& ph, int c, const TileTask& tk, SweepStage<T>* st,
                        const SweepCtl& sc) {
   constexpr int D = kSweepStages;
@@ -1143,6 +1163,7 @@ __device__ void sweep3(const KernelParams& p, const Phase& ph, int c, const Tile
     cp_async_commit();
   };
   for (int k = 0; k < D - 2; ++k) issue(k);
+  double dmx = 0.0;  // diagnostic pseudo-residual of the thread's nodes (DIAG)
   // One plane step: wait for plane k, start plane k + D - 2, form its in-plane sums into `nw`,
   // update the nodes of plane k - 1 from (m, o, nw).  The z loop is unrolled by three so that the
   // three-plane window rotates by renaming instead of moving registers.
@@ -1166,6 +1187,7 @@ __device__ void sweep3(const KernelParams& p, const Phase& ph, int c, const Tile
                            : (T)0;
         const int slot = tid + r * kThreads;
         const T e_new = sweep_update<T, HET>(kc, S, slot, b0 + (r + 1) * kHX + 1, CSe, CSse, o[r].v);
+        if (DIAG) dmx = fmax(dmx, (double)fabs(e_new - o[r].v) / ((double)(HET ? S.q[slot] : kc.q_const) * (double)kc.inv_c));
         const unsigned idx = zoff + (unsigned)cl.off[r];
         if (LAST) Ug[idx] = __fma_rn((double)e_new, inv_scale, S.u[slot]);
         if (keep) dst[idx] = e_new;
@@ -1182,10 +1204,11 @@ __device__ void sweep3(const KernelParams& p, const Phase& ph, int c, const Tile
   }
   cp_async_wait<0>();
   __syncthreads();
+  if (DIAG) diag_flush(p, tk.b, c, ph.level, dmx / p.state[tk.b].scale_used[c & 1]);
 }
 
 // 2-D: one halo tile per task, the CTA's tasks pipelined kSweepStages - 2 deep.
-template <typename T, bool LAST>
+template <typename T, bool LAST, bool DIAG = false>
 __device__ void sweep2(const KernelParams& p, const Phase& ph, int c, SweepStage<T>* st) {
   constexpr int D = kSweepStages;
   const int l = ph.level;
@@ -1230,6 +1253,7 @@ __device__ void sweep2(const KernelParams& p, const Phase& ph, int c, SweepStage
     const TileTask& tk = task(j);
     const SweepCtl sc = sweep_ctl(p, ph, tk.b);
     if (!mine(sc)) continue;
+    double dmx = 0.0;
     const ProblemDesc& P = p.probs[tk.b];
     const int N = sc.N;
     const Columns cl = own_columns(P, N, tk.x0, tk.y0);
@@ -1247,9 +1271,15 @@ __device__ void sweep2(const KernelParams& p, const Phase& ph, int c, SweepStage
       const int slot = tid + r * kThreads, cc = b0 + (r + 1) * kHX + 1;
       const T e_new = P.hetero ? sweep_update<T, true>(kc, S, slot, cc, CSe, rn_fma(kc.w_e, ps[r].sC, ps[r].sF), ps[r].v)
                                : sweep_update<T, false>(kc, S, slot, cc, CSe, (T)0, ps[r].v);
+      if (DIAG) {
+        const double pr = (double)fabs(e_new - ps[r].v) /
+                          ((double)(P.hetero ? S.q[slot] : kc.q_const) * (double)kc.inv_c);
+        if (pr > dmx) dmx = pr;
+      }
       if (LAST) p.U[P.off_full + cl.off[r]] = __fma_rn((double)e_new, inv_scale, S.u[slot]);
       if (!LAST || p.mixed) dst[cl.off[r]] = e_new;
     }
+    if (DIAG) diag_flush(p, tk.b, c, l, dmx / p.state[tk.b].scale_used[c & 1]);
   }
   cp_async_wait<0>();
   __syncthreads();
@@ -1740,12 +1770,17 @@ template <typename T, int DIM>
 __device__ void phase_sweep(const KernelParams& p, const Phase& ph, int c, unsigned char* smem) {
   SweepStage<T>* st = (SweepStage<T>*)smem;
   if (DIM == 2) {
-    if (ph.flags & kFinalVisit) sweep2<T, true>(p, ph, c, st);  // problems whose last sweep this is
-    sweep2<T, false>(p, ph, c, st);
+    if (p.diag) {
+      if (ph.flags & kFinalVisit) sweep2<T, true, true>(p, ph, c, st);
+      sweep2<T, false, true>(p, ph, c, st);
+    } else {
+      if (ph.flags & kFinalVisit) sweep2<T, true>(p, ph, c, st);  // problems whose last sweep this is
+      sweep2<T, false>(p, ph, c, st);
+    }
     return;
   }
   if constexpr (sizeof(T) == 4) {
-    if (!(ph.flags & kPair) && ph.level < p.quad_levels) {
+    if (!(ph.flags & kPair) && ph.level < p.quad_levels && !p.diag) {
       QuadStage<T>* qst = (QuadStage<T>*)smem;
       for_tasks4(p, ph.level, [&](const TileTask& tk) {
         const SweepCtl sc = sweep_ctl(p, ph, tk.b);
@@ -1779,6 +1814,16 @@ __device__ void phase_sweep(const KernelParams& p, const Phase& ph, int c, unsig
         }
         return;
       }
+    }
+    if (p.diag) {
+      if (sc.last) {
+        if (het) sweep3<T, true, true, true>(p, ph, c, tk, st, sc);
+        else sweep3<T, false, true, true>(p, ph, c, tk, st, sc);
+      } else {
+        if (het) sweep3<T, true, false, true>(p, ph, c, tk, st, sc);
+        else sweep3<T, false, false, true>(p, ph, c, tk, st, sc);
+      }
+      return;
     }
     if (sc.last) {
       if (het) sweep3<T, true, true>(p, ph, c, tk, st, sc);

@@ -54,6 +54,9 @@ _SIGNATURES = {
     "sgml_residual": [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p],
     "sgml_sigma_gradient": [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
     "sgml_set_fusion": [ctypes.c_void_p, ctypes.c_int],
+    "sgml_set_diagnostics": [ctypes.c_void_p, ctypes.c_int],
+    "sgml_get_diagnostics": [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.c_int,
+                             ctypes.POINTER(ctypes.c_int)],
     "sgml_set_quad": [ctypes.c_void_p, ctypes.c_int],
     "sgml_get_phases": [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.POINTER(ctypes.c_int)],
     "sgml_set_launch": [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int],
@@ -238,6 +241,20 @@ class Grid:
     def set_fusion(self, pair_levels=0):
         """Levels 0 .. pair_levels - 1 run their sweeps in fused pairs (3-D mixed form; 0: off)."""
         _check(load().sgml_set_fusion(self._h, pair_levels))
+
+    def set_diagnostics(self, cycles):
+        """Record the per-level diagnostic pseudo-residual of the first `cycles` cycles of each launch
+        (0: off)."""
+        _check(load().sgml_set_diagnostics(self._h, int(cycles)))
+        self.diag_cycles = int(cycles)
+
+    def get_diagnostics(self, b):
+        """(cycles, 13) array: largest |delta L_l e - r_l| of level l's sweeps in each recorded cycle."""
+        cap = 13 * max(getattr(self, "diag_cycles", 0), 1)
+        buf = (ctypes.c_double * cap)()
+        n = ctypes.c_int()
+        _check(load().sgml_get_diagnostics(self._h, b, buf, cap, ctypes.byref(n)))
+        return np.array(buf[: 13 * n.value]).reshape(n.value, 13)
 
     def set_quad(self, quad_levels=1):
         """Levels 0 .. quad_levels - 1 sweep with four rows per thread (3-D mixed form; 0: off)."""

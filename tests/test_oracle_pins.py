@@ -553,3 +553,29 @@ def test_streamline_of_rigid_rotation_closes():
     assert np.abs(r - 0.3).max() <= 1e-10
     assert np.abs(paths[0, -1] - seed[0]).max() <= 1e-9
     assert np.abs(paths[0, :, 2] - 0.4).max() == 0.0
+
+
+# --- diagnostic pseudo-residual of Sec. 3.1 -----------------------------------------------------
+
+def test_diagnostic_pseudo_residual_on_a_single_level_is_the_residual():
+    """With one level the cycle starts its level-0 sweeps from e = 0: the largest pseudo-residual
+    |delta L e - r| is max |r| ("for the full mesh, both residuals are the same")."""
+    for dim, seed in ((2, 11), (3, 12)):
+        d = inputs.random_problem(dim, 1, seed=seed, mixed_bc=False)
+        p = Problem(dim, 1, faces=d["faces"], values=d["values"], sigma=d.get("sigma"), a=d.get("a"),
+                    a_scalar=d.get("a_scalar", 0.0))
+        r = p.residual(p.lift(), d["f"])
+        _, diag = p.cycle_diag(r)
+        assert diag[0] == pytest.approx(np.abs(r[p.unknown_mask()]).max(), rel=1e-15)
+
+
+def test_diagnostic_pseudo_residual_is_homogeneous_and_matches_the_cycle():
+    d = inputs.random_problem(3, 3, seed=13)
+    p = Problem(3, 3, faces=d["faces"], values=d["values"], sigma=d.get("sigma"), a=d.get("a"),
+                a_scalar=d.get("a_scalar", 0.0))
+    r = p.residual(p.lift(), d["f"])
+    e1, d1 = p.cycle_diag(r)
+    e2, d2 = p.cycle_diag(-2.5 * r)
+    assert np.all(d1 > 0)
+    assert np.allclose(d2, 2.5 * d1, rtol=1e-12)
+    assert np.array_equal(e1, p.cycle(r))
