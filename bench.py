@@ -351,7 +351,8 @@ def schedule_labels(g):
     """Labels of the cycle's phases, from the library's own phase table (restriction passes, then
     the zig-zag visits of Algorithm 3 with their transitions; fused sweep pairs count as one)."""
     names = {0: lambda l: f"restrict ->{l}", 1: lambda l: f"sweep L{l}", 2: lambda l: f"prolong {l + 1}->{l}",
-             3: lambda l: f"inject {l - 1}->{l}"}
+             3: lambda l: f"inject {l - 1}->{l}", 4: lambda l: "mean rows", 5: lambda l: "mean reduce",
+             6: lambda l: "mean apply"}
     return [names[op](level) for op, level, _, _ in g.get_phases()]
 
 

@@ -71,9 +71,13 @@ int sgml_set_params(sgml_grid_t g, int n_r, double theta, int schedule, int sten
 
 /* Coefficients of L = div(sigma grad) + a for one problem (problem >= 0) or for all (problem = -1,
  * arrays concatenated problem after problem).  sigma: N^dim positive node values, or NULL for
- * sigma = 1.  a: N^dim node values, or NULL for the constant a_scalar.  a <= 0 is required (the
- * pseudo-time step needs D_i > 0); a < 0 everywhere makes an all-Neumann problem well posed.
- * Copies the arrays; the coefficient pyramid is rebuilt before the next cycle. */
+ * sigma = 1.  a: N^dim node values (<= 0), or NULL for the constant a_scalar (<= 1; the pseudo-time
+ * step needs D_i > 0).  a < 0 everywhere makes an all-Neumann problem well posed as given; an
+ * all-Neumann problem with a constant a >= 0 is solved in the form of Eq. 10 (Sec. 3.2):
+ * L u = f - <f> with zero normal derivatives, for the u of zero mean (<.>: trapezoid-rule mean over
+ * the unit square / cube), the constant mode projected out of u after every cycle and the residual
+ * recomputed in FP64 every cycle.  Copies the arrays; the coefficient pyramid is rebuilt before the
+ * next cycle. */
 int sgml_set_coeffs(sgml_grid_t g, int problem, const double* sigma, const double* a, double a_scalar);
 
 /* Source f of L u = f (the paper's sign: a problem -Lap u = q passes f = -q).  N^dim values for one
@@ -86,7 +90,8 @@ int sgml_set_source(sgml_grid_t g, int problem, const double* f);
  * outward normal derivative of a Neumann face (Sec. 2, boundary conditions).  A node on a Dirichlet
  * face is fixed (Dirichlet wins where faces of both kinds meet; the first Dirichlet face in face
  * order gives the value).  Neumann faces use even images (-k -> k) with u_image = u_mirror + 2 k h g.
- * Resets the solution. */
+ * All faces Neumann with a constant a >= 0: Eq. 10 (see sgml_set_coeffs); every g must then be 0
+ * (else SGML_ERR_ARG at the next solve).  Resets the solution. */
 int sgml_set_bc(sgml_grid_t g, int problem, const int* face_type, const double* face_value);
 
 /* Run exactly ncycles cycles of Algorithm 3 for every problem from the current solution (the
@@ -242,7 +247,8 @@ const char* sgml_last_error(void);
  * max_cycles cycles, with the default method parameters (n_r = 2, theta = 0.7, consistent stencil).
  * f (N^dim doubles), sigma (N^dim doubles or NULL for 1) and u (N^dim doubles, written) are DEVICE
  * pointers owned by the caller; face_type / face_value (2*dim entries, face_value may be NULL) are
- * host arrays as in sgml_set_bc; a_scalar <= 0.  cycles_out / rel_out (host, may be NULL) receive the
+ * host arrays as in sgml_set_bc; a_scalar <= 0 (all-Neumann problems need a_scalar < 0 here: the
+ * Eq. 10 projection is a grid-API feature).  cycles_out / rel_out (host, may be NULL) receive the
  * cycles run and the final relative residual.  Work runs on cuda_stream; the call synchronises it.
  *
  * All intermediate data lives in one file-scope device array of 24 MiB that every GPU loading the

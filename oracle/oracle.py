@@ -67,6 +67,10 @@ def _load():
         lib.orc_interpolate_add.argtypes = [P, I, D, D]
         lib.orc_visit.argtypes = [P, I, I, D, D, D, D, D]
         lib.orc_cycle_diag.argtypes = [P, D, D, D]
+        lib.orc_projects_mean.argtypes = [P]
+        lib.orc_projects_mean.restype = I
+        lib.orc_mean.argtypes = [P, D]
+        lib.orc_mean.restype = ctypes.c_double
         lib.orc_cycle.argtypes = [P, D, D]
         lib.orc_schedule.argtypes = [P, ctypes.POINTER(I), ctypes.POINTER(I), I]
         lib.orc_schedule.restype = I
@@ -245,6 +249,15 @@ class Problem:
         if fn == 0.0:
             fn = self.max_norm(self.residual(self.lift(), f))
         return rn / fn if fn > 0 else 0.0
+
+    def projects_mean(self):
+        """All faces Neumann and a >= 0 constant: the solve works on L u = f - <f> (Eq. 10) for the
+        zero-mean u."""
+        return bool(_load().orc_projects_mean(ctypes.byref(self._c)))
+
+    def mean(self, v):
+        """Trapezoid-rule mean over the unit square / cube."""
+        return _load().orc_mean(ctypes.byref(self._c), _ptr(self._arr(v)))
 
     def solve(self, f, tol=1e-12, max_cycles=200):
         """Outer recurrence; returns (u, cycles or -1, history of relative residuals)."""

@@ -515,10 +515,52 @@ double orc_max_norm(const orc_problem* p, const double* v) {
  * arithmetic).  u is lifted first.  Returns the number of cycles run, or -1 if max_cycles cycles did
  * not reach tol.  hist (may be NULL) receives the relative residual before each cycle and after the
  * last (max_cycles + 1 entries). */
-int orc_solve(const orc_problem* p, const double* f, double tol, int max_cycles, double* u, double* hist) {
+/* ------------------------------------------------------------------------------------------ */
+/* Pure-Neumann problems (Sec. 3.2, Eq. 10): every face Neumann with zero normal derivative and    */
+/* a >= 0 (a constant), where L u = f has no solution or an unstable constant mode.  The equation   */
+/* solved is L u = f - <f> for the zero-mean u, <v> the mean over the unit square / cube by the     */
+/* trapezoid rule (node weight 1/2 per coordinate on a face).  The constant mode is projected out   */
+/* of u after every cycle: for a = 0 it is the operator's null space, for a > 0 the pseudo-time      */
+/* iteration would let it grow.  (With a < 0 everywhere an all-Neumann problem is well posed and is */
+/* solved as given.)                                                                                 */
+/* ------------------------------------------------------------------------------------------ */
+int orc_projects_mean(const orc_problem* p) {
+  for (int k = 0; k < 2 * p->dim; ++k)
+    if (p->face_type[k] != ORC_NEUMANN) return 0;
+  return p->a == NULL && p->a_scalar >= 0.0;
+}
+
+double orc_mean(const orc_problem* p, const double* v) {
+  int N = npts(p);
+  long M = nnodes(p);
+  double sw = 0.0, s = 0.0;
+  for (long i = 0; i < M; ++i) {
+    int c[3];
+    coords(p, i, c);
+    double w = 1.0;
+    for (int k = 0; k < p->dim; ++k)
+      if (c[k] == 0 || c[k] == N - 1) w *= 0.5;
+    sw += w;
+    s += w * v[i];
+  }
+  return s / sw;
+}
+
+void orc_project_mean(const orc_problem* p, double* v) {
+  long M = nnodes(p);
+  double m = orc_mean(p, v);
+  for (long i = 0; i < M; ++i) v[i] -= m;
+}
+
+int orc_solve(const orc_problem* p, const double* f_in, double tol, int max_cycles, double* u, double* hist) {
   long M = nnodes(p);
   double* r = (double*)malloc(sizeof(double) * M);
   double* e = (double*)malloc(sizeof(double) * M);
+  double* fp = (double*)malloc(sizeof(double) * M);
+  const int project = orc_projects_mean(p);
+  memcpy(fp, f_in, sizeof(double) * M);
+  if (project) orc_project_mean(p, fp);
+  const double* f = fp;
   orc_lift(p, u);
   double scale = orc_max_norm(p, f);
   int cycles = -1;
@@ -535,9 +577,11 @@ int orc_solve(const orc_problem* p, const double* f, double tol, int max_cycles,
     if (c == max_cycles) break;
     orc_cycle(p, r, e);
     for (long i = 0; i < M; ++i) u[i] += e[i];
+    if (project) orc_project_mean(p, u);
   }
   free(r);
   free(e);
+  free(fp);
   return cycles;
 }
 

@@ -73,6 +73,11 @@ struct sgml_grid {
   bool dirty_coeffs = true, dirty_desc = true, dirty_phases = true, dirty_tiles = true, fresh = true;
   long long launches = 0;
   ProblemState* h_state = nullptr;  // pinned
+  double* d_rowsum = nullptr;             // pure-Neumann projection: level-0 row sums of u
+  double* d_umean = nullptr;              // ... mean of u per problem
+  double* d_fmean = nullptr;              // ... source projection scratch (257 doubles per problem)
+  std::vector<double> f_shift;            // mean already subtracted from each problem's F
+  std::vector<char> f_checked;            // F's projection matches the current boundary conditions
   unsigned long long* d_diag = nullptr;   // diagnostic pseudo-residuals (sgml_set_diagnostics)
   int diag_cycles = 0;
   unsigned long long* d_trace = nullptr;  // per-phase timestamps (sgml_set_trace)
@@ -131,7 +136,7 @@ static long long round_up(long long x, long long a) { return (x + a - 1) / a * a
 // ------------------------------------------------------------------------------------------------
 // Phase table of one cycle.  On levels below pair_levels the sweeps of a visit run two at a time
 // (kPair; a visit with an odd number of sweeps ends with a single one).
-static std::vector<Phase> build_phases(int n_max, int n_r, int pair_levels) {
+static std::vector<Phase> build_phases(int n_max, int n_r, int pair_levels, bool any_eq10) {
   std::vector<Phase> ph;
   for (int l = 1; l <= n_max - 1; ++l) ph.push_back(Phase{OP_RESTRICT, l, l - 1, 0, 0, 0});
   struct Visit {
@@ -163,7 +168,25 @@ static std::vector<Phase> build_phases(int n_max, int n_r, int pair_levels) {
     for (int s = 0; s < kk; s += step)
       ph.push_back(Phase{OP_SWEEP, v.level, v.tooth, s, flags | (step == 2 && s + 1 < kk ? kPair : 0), 0});
   }
+  if (any_eq10) {  // Eq. 10: project the constant mode out of u after the cycle
+    ph.push_back(Phase{OP_MEAN_ROWS, 0, 0, 0, 0, 0});
+    ph.push_back(Phase{OP_MEAN_REDUCE, 0, 0, 0, 0, 0});
+    ph.push_back(Phase{OP_MEAN_APPLY, 0, 0, 0, 0, 0});
+  }
   return ph;
+}
+
+// Eq. 10 problems: every face Neumann and a >= 0 constant (a < 0 everywhere is well posed as is).
+static bool projects_mean(const sgml_grid* g, const ProblemDesc& P) {
+  for (int k = 0; k < 2 * g->dim; ++k)
+    if (P.face_type[k] != SGML_NEUMANN) return false;
+  return !P.a_per_node && P.a_scalar >= 0.0;
+}
+
+static bool any_projects_mean(const sgml_grid* g) {
+  for (const ProblemDesc& P : g->P)
+    if (projects_mean(g, P)) return true;
+  return false;
 }
 
 // Fused pairs and four-row tiles: 3-D mixed form only, and not while diagnostics are recorded
@@ -176,7 +199,7 @@ static int effective_quad_levels(const sgml_grid* g) {
 }
 
 static int upload_phases(sgml_grid* g) {
-  std::vector<Phase> ph = build_phases(g->n_max, g->n_r, effective_pair_levels(g));
+  std::vector<Phase> ph = build_phases(g->n_max, g->n_r, effective_pair_levels(g), any_projects_mean(g));
   if (g->d_phases) SGML_CUDA(cudaFree(g->d_phases));
   g->d_phases = nullptr;
   g->nphases = (int)ph.size();
@@ -329,15 +352,57 @@ static int build_coeffs(sgml_grid* g) {
 }
 
 static int upload_desc(sgml_grid* g) {
+  for (ProblemDesc& P : g->P) P.project_mean = projects_mean(g, P) ? 1 : 0;
   SGML_CUDA(cudaMemcpyAsync(g->d_probs, g->P.data(), sizeof(ProblemDesc) * g->batch, cudaMemcpyHostToDevice, g->stream));
   SGML_CUDA(cudaStreamSynchronize(g->stream));
   g->dirty_desc = false;
   return SGML_OK;
 }
 
+// Eq. 10 problems solve L u = f - <f>: the mean of F is subtracted (and added back if the problem
+// later stops being one); their faces must carry zero derivatives.
+static int project_sources(sgml_grid* g) {
+  const bool any = any_projects_mean(g);
+  if (any && !g->d_rowsum) {
+    long long rows = 0;
+    for (const ProblemDesc& P : g->P) rows += g->dim == 3 ? (long long)side(P.n, 0) * side(P.n, 0) : side(P.n, 0);
+    SGML_CUDA(cudaMalloc(&g->d_rowsum, sizeof(double) * rows));
+    SGML_CUDA(cudaMalloc(&g->d_umean, sizeof(double) * g->batch));
+    SGML_CUDA(cudaMalloc(&g->d_fmean, sizeof(double) * 257 * g->batch));
+  }
+  for (int b = 0; b < g->batch; ++b) {
+    if (g->f_checked[b]) continue;
+    ProblemDesc& P = g->P[b];
+    const bool pn = projects_mean(g, P);
+    if (pn)
+      for (int k = 0; k < 2 * g->dim; ++k)
+        if (P.face_value[k] != 0.0)
+          return fail(SGML_ERR_ARG, "an all-Neumann problem with a >= 0 needs zero normal derivatives (Eq. 10)");
+    double* F = g->F + P.off_full;
+    double* scr = g->d_fmean + (size_t)257 * b;
+    if (pn) {
+      SGML_CUDA(launch_project_mean(g->dim, P.n, F, scr, g->stream));
+      double m = 0.0;
+      SGML_CUDA(cudaMemcpyAsync(&m, scr + 256, sizeof(double), cudaMemcpyDeviceToHost, g->stream));
+      SGML_CUDA(cudaStreamSynchronize(g->stream));
+      g->f_shift[b] += m;
+      g->launches += 3;
+    } else if (g->f_shift[b] != 0.0) {
+      SGML_CUDA(cudaMemcpyAsync(scr + 256, &g->f_shift[b], sizeof(double), cudaMemcpyHostToDevice, g->stream));
+      SGML_CUDA(launch_add_scalar(F, nodes(g->dim, P.n, 0), scr + 256, 1.0, g->stream));
+      SGML_CUDA(cudaStreamSynchronize(g->stream));
+      g->f_shift[b] = 0.0;
+      g->launches += 1;
+    }
+    g->f_checked[b] = 1;
+  }
+  return SGML_OK;
+}
+
 static int prepare(sgml_grid* g) {
   int st;
   if (g->dirty_coeffs && (st = build_coeffs(g)) != SGML_OK) return st;
+  if ((st = project_sources(g)) != SGML_OK) return st;
   if (g->dirty_desc && (st = upload_desc(g)) != SGML_OK) return st;
   if (g->dirty_phases && (st = upload_phases(g)) != SGML_OK) return st;
   if (g->dirty_tiles && (st = upload_tiles(g)) != SGML_OK) return st;
@@ -396,6 +461,8 @@ static int launch(sgml_grid* g, int max_cycles, double tol) {
   p.hist_cap = g->hist_cap;
   p.trace = g->d_trace;
   p.trace_cycles = g->d_trace ? g->trace_cycles : 0;
+  p.rowsum = g->d_rowsum;
+  p.umean = g->d_umean;
   p.diag = g->d_diag;
   p.diag_cycles = g->d_diag ? g->diag_cycles : 0;
   if (g->d_diag)
@@ -478,6 +545,8 @@ int sgml_create_grid(int dim, int batch, const int* n_levels, int precision, voi
   g->elem = g->mixed ? 4 : 8;
   g->stream = (cudaStream_t)cuda_stream;
   g->P.resize(batch);
+  g->f_shift.assign(batch, 0.0);
+  g->f_checked.assign(batch, 0);
   long long full = 0, lvl = 0;
   for (int b = 0; b < batch; ++b) {
     ProblemDesc& P = g->P[b];
@@ -548,7 +617,7 @@ int sgml_set_params(sgml_grid_t g, int n_r, double theta, int schedule, int sten
 int sgml_set_coeffs(sgml_grid_t g, int problem, const double* sigma, const double* a, double a_scalar) {
   if (!valid(g)) return fail(SGML_ERR_ARG, "invalid grid");
   if (problem < -1 || problem >= g->batch) return fail(SGML_ERR_ARG, "problem out of range");
-  if (!(a_scalar <= 0.0)) return fail(SGML_ERR_ARG, "a_scalar must be <= 0");
+  if (!(a_scalar <= 1.0)) return fail(SGML_ERR_ARG, "a_scalar must be <= 1");
   int st;
   if ((sigma || a) && (st = ensure_hetero_pools(g, a != nullptr)) != SGML_OK) return st;
   long long src = 0;
@@ -558,6 +627,7 @@ int sgml_set_coeffs(sgml_grid_t g, int problem, const double* sigma, const doubl
     P.hetero = (sigma || a) ? 1 : 0;
     P.a_per_node = a ? 1 : 0;
     P.a_scalar = a ? 0.0 : a_scalar;
+    g->f_checked[b] = 0;
     if (sigma) SGML_CUDA(cudaMemcpyAsync(g->SIG64 + P.off_full, sigma + src, sizeof(double) * M, cudaMemcpyDefault, g->stream));
     else if (a) {
       SGML_CUDA(launch_fill(g->SIG64 + P.off_full, M, 1.0, g->stream));
@@ -568,6 +638,7 @@ int sgml_set_coeffs(sgml_grid_t g, int problem, const double* sigma, const doubl
   }
   g->dirty_coeffs = true;
   g->dirty_desc = true;
+  g->dirty_phases = true;  // the Eq. 10 projection phases depend on a
   g->fresh = true;
   return SGML_OK;
 }
@@ -580,6 +651,8 @@ int sgml_set_source(sgml_grid_t g, int problem, const double* f) {
     const long long M = nodes(g->dim, g->P[b].n, 0);
     SGML_CUDA(cudaMemcpyAsync(g->F + g->P[b].off_full, f + src, sizeof(double) * M, cudaMemcpyDefault, g->stream));
     src += M;
+    g->f_shift[b] = 0.0;
+    g->f_checked[b] = 0;
   }
   g->fresh = true;
   return SGML_OK;
@@ -597,9 +670,19 @@ int sgml_set_bc(sgml_grid_t g, int problem, const int* face_type, const double* 
       P.face_type[k] = k < nf ? face_type[k] : SGML_DIRICHLET;
       P.face_value[k] = (k < nf && face_value) ? face_value[k] : 0.0;
     }
+    g->f_checked[b] = 0;
+    // Nodes that become fixed must hold a zero correction and a zero residual (the sweeps and the
+    // residual never write fixed nodes, and the stencils and restrictions of their neighbours read
+    // them): clear the problem's level arrays.
+    long long lvl = 0;
+    for (int l = 0; l <= P.n - 1; ++l) lvl += round_up(nodes(g->dim, P.n, l), 64);
+    const size_t off = (size_t)g->elem * P.off_lvl[0], bytes = (size_t)g->elem * lvl;
+    for (void* a : {g->E, g->E2, g->B, g->R})
+      SGML_CUDA(cudaMemsetAsync((char*)a + off, 0, bytes, g->stream));
   }
   g->dirty_desc = true;
   g->dirty_tiles = true;
+  g->dirty_phases = true;  // the pure-Neumann projection phases
   g->fresh = true;
   return SGML_OK;
 }
@@ -679,6 +762,7 @@ int sgml_residual(sgml_grid_t g, int problem, const double* u, double* r) {
   if (!valid(g)) return fail(SGML_ERR_ARG, "invalid grid");
   if (problem < 0 || problem >= g->batch || !u || !r) return fail(SGML_ERR_ARG, "bad arguments");
   int st;
+  if ((st = project_sources(g)) != SGML_OK) return st;
   if (g->dirty_desc && (st = upload_desc(g)) != SGML_OK) return st;
   const ProblemDesc& P = g->P[problem];
   const long long M = nodes(g->dim, P.n, 0);
@@ -752,7 +836,7 @@ int sgml_set_quad(sgml_grid_t g, int quad_levels) {
 
 int sgml_get_phases(sgml_grid_t g, int* out, int cap, int* count) {
   if (!valid(g) || !count || (cap > 0 && !out)) return fail(SGML_ERR_ARG, "invalid grid or output");
-  const std::vector<Phase> ph = build_phases(g->n_max, g->n_r, effective_pair_levels(g));
+  const std::vector<Phase> ph = build_phases(g->n_max, g->n_r, effective_pair_levels(g), any_projects_mean(g));
   *count = (int)ph.size();
   for (int q = 0; q < (int)ph.size() && q < cap; ++q) {
     out[4 * q + 0] = ph[q].op;
@@ -855,7 +939,8 @@ int sgml_destroy(sgml_grid_t g) {
   cudaStreamSynchronize(g->stream);
   void* ptrs[] = {g->U, g->F, g->SIG64, g->A64, g->RESP, g->A0, g->E, g->E2, g->B, g->R, g->SIG, g->Q,
                   g->d_probs, g->d_state, g->d_accum, g->d_sync, g->d_phases, g->d_rows, g->d_tasks,
-                  g->d_task_off, g->d_tasks4, g->d_task_off4, g->d_hist, g->d_trace, g->d_diag};
+                  g->d_task_off, g->d_tasks4, g->d_task_off4, g->d_hist, g->d_trace, g->d_diag,
+                  g->d_rowsum, g->d_umean, g->d_fmean};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (g->h_state) cudaFreeHost(g->h_state);

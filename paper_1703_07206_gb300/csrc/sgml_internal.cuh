@@ -20,7 +20,15 @@ namespace sgml {
 
 constexpr int kMaxLevels = 13;  // n <= 12
 
-enum Op : int { OP_RESTRICT = 0, OP_SWEEP = 1, OP_PROLONG = 2, OP_INJECT = 3 };
+enum Op : int {
+  OP_RESTRICT = 0,
+  OP_SWEEP = 1,
+  OP_PROLONG = 2,
+  OP_INJECT = 3,
+  OP_MEAN_ROWS = 4,    // Eq. 10 problems: weighted row sums of u (trapezoid rule)
+  OP_MEAN_REDUCE = 5,  // ... their total per problem, in a fixed order -> mean of u
+  OP_MEAN_APPLY = 6    // ... u -= mean (Eq. 10's zero-mean solution)
+};
 
 // Phase flags
 constexpr int kFinalVisit = 1;   // SWEEP: merged last level-0 visit (tooth 0 and the final visit)
@@ -49,6 +57,7 @@ struct ProblemDesc {
   long long off_full;              // element offset in the FP64 full-grid pools
   long long off_lvl[kMaxLevels];   // element offset of level l in the level pools
   double q_const[kMaxLevels];      // homogeneous problems: delta_tau * kappa / (2 H^2) per level
+  int project_mean;                // every face Neumann, a >= 0 constant: Eq. 10, zero-mean u
 };
 
 // Per-problem running state, written by CTA 0 of the cycle kernel between barriers.
@@ -122,6 +131,8 @@ struct KernelParams {
   unsigned long long timeout_ns;
   double* hist;
   int hist_cap;
+  double* rowsum;             // Eq. 10 projection: weighted level-0 row sums of u (row_prefix order)
+  double* umean;              // ... and the mean of u per problem
   unsigned long long* diag;   // optional: diagnostic pseudo-residual bits, [batch][diag_cycles][kMaxLevels]
   int diag_cycles;
   unsigned long long* trace;  // optional: globaltimer after each barrier, [cycle][2 + nphases]
@@ -143,6 +154,10 @@ cudaError_t launch_residual64(int dim, const ProblemDesc& P, const double* U, co
 cudaError_t launch_sigma_gradient(int dim, const ProblemDesc& P, const double* lam, const double* U,
                                   double kappa, double w_edge, double w_corner, double* g, cudaStream_t s);
 cudaError_t launch_fill(double* dst, long long n, double v, cudaStream_t s);
+// Pure-Neumann sources: v -= trapezoid mean of v (scratch: 257 device doubles; scratch[256] = the
+// mean); v += sign * (*d_value).
+cudaError_t launch_project_mean(int dim, int n, double* v, double* scratch, cudaStream_t s);
+cudaError_t launch_add_scalar(double* v, long long n, const double* d_value, double sign, cudaStream_t s);
 
 }  // namespace sgml
 

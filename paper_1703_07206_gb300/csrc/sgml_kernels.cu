@@ -810,7 +810,9 @@ __device__ void residual3r(const KernelParams& p, const TileTask& tk, int c, Res
 // correction of the previous cycle).
 template <typename T>
 __device__ __forceinline__ bool use_anchor(const KernelParams& p, int b, int c) {
-  return !p.mixed || c == 0 || p.state[b].anchor_next;
+  // Eq. 10 problems: every residual from the projected u (the FP32 recurrence does not follow the
+  // projection's constant shift)
+  return !p.mixed || c == 0 || p.state[b].anchor_next || p.probs[b].project_mean;
 }
 
 __device__ __forceinline__ ResSrc<double> anchor_src(const KernelParams& p, const ProblemDesc& P) {
@@ -2056,6 +2058,67 @@ __device__ void phase_inject(const KernelParams& p, const Phase& ph) {
 }
 
 // ---------------------------------------------------------------------------------------------
+// Pure-Neumann problems with a >= 0 (Sec. 3.2, Eq. 10): after the cycle's last sweep the constant mode is
+// projected out of u, u -= <u> with <u> the trapezoid-rule mean -- for a = 0 it spans the
+// operator's null space, for a > 0 the pseudo-time iteration would let it grow.  Deterministic:
+// weighted row sums by warps (a fixed shuffle tree), one CTA per problem adds them in a fixed
+// order, then every node is shifted.
+// ---------------------------------------------------------------------------------------------
+template <int DIM>
+__device__ void phase_mean_rows(const KernelParams& p) {
+  const int lane = threadIdx.x & 31;
+  for_rows<DIM>(p, 0, [&](int b, const ProblemDesc& P, int N, int y, int z) {
+    if (!P.project_mean || p.accum[b].done) return;
+    const double* u = p.U + P.off_full + ((long long)z * N + y) * N;
+    double s = 0.0;
+    for (int x = lane; x < N; x += 32) s += (x == 0 || x == N - 1) ? 0.5 * u[x] : u[x];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) {
+      const double wy = (y == 0 || y == N - 1) ? 0.5 : 1.0;
+      const double wz = DIM == 3 ? ((z == 0 || z == N - 1) ? 0.5 : 1.0) : 1.0;
+      p.rowsum[p.row_prefix[b] + (DIM == 3 ? (long long)z * N + y : y)] = s * wy * wz;
+    }
+  });
+}
+
+// (the partial sums live in the dynamic shared memory: static shared memory is kept small so that two
+// CTAs per SM fit the 196 KB shared-memory carveout and leave L1 its 60 KB)
+__device__ void phase_mean_reduce(const KernelParams& p, int dim, unsigned char* smem) {
+  double* s_part = (double*)smem;
+  for (int b = blockIdx.x; b < p.batch; b += gridDim.x) {
+    const ProblemDesc& P = p.probs[b];
+    if (!P.project_mean || p.accum[b].done) continue;
+    const long long r0 = p.row_prefix[b], rows = p.row_prefix[b + 1] - r0;
+    const long long chunk = (rows + kThreads - 1) / kThreads;
+    double s = 0.0;
+    for (long long r = threadIdx.x * chunk; r < (threadIdx.x + 1) * chunk && r < rows; ++r) s += p.rowsum[r0 + r];
+    s_part[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = kThreads / 2; w > 0; w >>= 1) {
+      if ((int)threadIdx.x < w) s_part[threadIdx.x] += s_part[threadIdx.x + w];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+      const double cells = dim == 3 ? (double)(1LL << (3 * P.n)) : (double)(1LL << (2 * P.n));  // sum of the weights
+      p.umean[b] = s_part[0] / cells;
+    }
+    __syncthreads();
+  }
+}
+
+template <int DIM>
+__device__ void phase_mean_apply(const KernelParams& p) {
+  const int lane = threadIdx.x & 31;
+  for_rows<DIM>(p, 0, [&](int b, const ProblemDesc& P, int N, int y, int z) {
+    if (!P.project_mean || p.accum[b].done) return;
+    double* u = p.U + P.off_full + ((long long)z * N + y) * N;
+    const double m = p.umean[b];
+    for (int x = lane; x < N; x += 32) u[x] -= m;
+  });
+}
+
+// ---------------------------------------------------------------------------------------------
 // The persistent cycle kernel
 // ---------------------------------------------------------------------------------------------
 template <typename T, int DIM>
@@ -2064,7 +2127,10 @@ __device__ __forceinline__ void run_phase(const KernelParams& p, const Phase& ph
     case OP_RESTRICT: phase_restrict<T, DIM>(p, ph.level); break;
     case OP_SWEEP: phase_sweep<T, DIM>(p, ph, c, sm); break;
     case OP_PROLONG: phase_prolong<T, DIM>(p, ph, sm); break;
-    default: phase_inject<T, DIM>(p, ph); break;
+    case OP_INJECT: phase_inject<T, DIM>(p, ph); break;
+    case OP_MEAN_ROWS: phase_mean_rows<DIM>(p); break;
+    case OP_MEAN_REDUCE: phase_mean_reduce(p, DIM, sm); break;
+    default: phase_mean_apply<DIM>(p); break;
   }
 }
 
@@ -2369,6 +2435,61 @@ cudaError_t launch_sigma_gradient(int dim, const ProblemDesc& P, const double* l
   const long long M = dim == 3 ? (long long)N * N * N : (long long)N * N;
   if (dim == 3) sigma_gradient_kernel<3><<<grid_for(M), 256, 0, s>>>(P, lam, U, kappa, w_edge, w_corner, g);
   else sigma_gradient_kernel<2><<<grid_for(M), 256, 0, s>>>(P, lam, U, kappa, w_edge, w_corner, g);
+  return cudaGetLastError();
+}
+
+// Trapezoid-rule mean of one problem's full-grid array (pure-Neumann source projection), in a
+// fixed order: per-block sums of contiguous ranges, then one block adds them.
+__global__ void mean_partial_kernel(int dim, int N, const double* __restrict__ v, double* __restrict__ part) {
+  __shared__ double s_part[256];
+  const long long M = dim == 3 ? (long long)N * N * N : (long long)N * N;
+  const long long chunk = (M + gridDim.x - 1) / gridDim.x;
+  const long long i0 = (long long)blockIdx.x * chunk, i1 = i0 + chunk < M ? i0 + chunk : M;
+  double s = 0.0;
+  for (long long i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+    const int x = (int)(i % N), y = (int)((i / N) % N), z = dim == 3 ? (int)(i / ((long long)N * N)) : 0;
+    double w = (x == 0 || x == N - 1) ? 0.5 : 1.0;
+    if (y == 0 || y == N - 1) w *= 0.5;
+    if (dim == 3 && (z == 0 || z == N - 1)) w *= 0.5;
+    s += w * v[i];
+  }
+  s_part[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) s_part[threadIdx.x] += s_part[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = s_part[0];
+}
+
+__global__ void mean_finish_kernel(int parts, double cells, const double* __restrict__ part, double* out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double s = 0.0;
+    for (int k = 0; k < parts; ++k) s += part[k];
+    *out = s / cells;
+  }
+}
+
+__global__ void add_scalar_kernel(double* v, long long n, const double* __restrict__ d, double sign) {
+  const double a = sign * *d;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    v[i] += a;
+}
+
+cudaError_t launch_project_mean(int dim, int n, double* v, double* scratch, cudaStream_t s) {
+  // scratch: 257 doubles; scratch[256] receives the mean, which is then subtracted from v.
+  const int N = (1 << n) + 1;
+  const long long M = dim == 3 ? (long long)N * N * N : (long long)N * N;
+  const int parts = 256;
+  mean_partial_kernel<<<parts, 256, 0, s>>>(dim, N, v, scratch);
+  mean_finish_kernel<<<1, 32, 0, s>>>(parts, dim == 3 ? (double)(1LL << (3 * n)) : (double)(1LL << (2 * n)), scratch,
+                                       scratch + 256);
+  add_scalar_kernel<<<grid_for(M), 256, 0, s>>>(v, M, scratch + 256, -1.0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_add_scalar(double* v, long long n, const double* d_value, double sign, cudaStream_t s) {
+  add_scalar_kernel<<<grid_for(n), 256, 0, s>>>(v, n, d_value, sign);
   return cudaGetLastError();
 }
 

@@ -187,6 +187,34 @@ def capacitor_3d(n=7, sign=+1.0):
     return _problem(3, n, np.zeros_like(X), sigma=sigma, faces=faces, values=values)
 
 
+def circle_source_2d(n=6, radius=0.25, centre=(0.5, 0.5)):
+    """Sec. 3.2: a finite delta function along a circle -- the curve resampled at equidistant points
+    a mesh spacing apart, each depositing its arc length times a tensor product of hat functions
+    (bilinear, support 2h x 2h) of unit integral."""
+    N = 2 ** n + 1
+    h = 1.0 / (N - 1)
+    count = int(math.ceil(2 * np.pi * radius / h))
+    ds = 2 * np.pi * radius / count
+    f = np.zeros((N, N))
+    for j in range(count):
+        t = 2 * np.pi * j / count
+        px, py = centre[0] + radius * np.cos(t), centre[1] + radius * np.sin(t)
+        i0, j0 = int(np.floor(px / h)), int(np.floor(py / h))
+        tx, ty = px / h - i0, py / h - j0
+        for dj, wy in ((0, 1 - ty), (1, ty)):
+            for di, wx in ((0, 1 - tx), (1, tx)):
+                f[j0 + dj, i0 + di] += ds * wx * wy / (h * h)
+    return f
+
+
+def neumann_helmholtz_2d(n=6, a=0.1, radius=0.25):
+    """Sec. 3.2, Eq. 10: Lap u + a u = f - <f> with zero normal derivative on every side (the
+    force potential of the grid deformation), f the circle source of `circle_source_2d`; a = 0.1 as
+    in the paper's Fig. 5.  The solver subtracts the mean <f> itself and returns the zero-mean u."""
+    f = circle_source_2d(n, radius)
+    return _problem(2, n, f, a_scalar=a, faces=[NEUMANN] * 4, values=[0.0] * 4)
+
+
 def random_problem(dim, n, seed, hetero=True, helmholtz=True, mixed_bc=True, flux=False):
     """Small random problem for parity tests: smooth random source, optional log-normal-ish sigma,
     optional per-node a <= 0, random Dirichlet/Neumann faces (at least one Dirichlet unless a < 0

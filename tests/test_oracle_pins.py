@@ -579,3 +579,49 @@ def test_diagnostic_pseudo_residual_is_homogeneous_and_matches_the_cycle():
     assert np.all(d1 > 0)
     assert np.allclose(d2, 2.5 * d1, rtol=1e-12)
     assert np.array_equal(e1, p.cycle(r))
+
+
+# --- pure-Neumann problems (Sec. 3.2, Eq. 10) ----------------------------------------------------
+
+def trapezoid_weights(p):
+    w = np.ones(p.shape)
+    for ax in range(p.dim):
+        sl = [slice(None)] * p.dim
+        sl[ax] = 0
+        w[tuple(sl)] *= 0.5
+        sl[ax] = -1
+        w[tuple(sl)] *= 0.5
+    return w
+
+
+@pytest.mark.parametrize("dim,n,a,hetero", [(2, 4, 0.1, False), (2, 3, 0.0, True), (3, 2, 0.1, True), (3, 3, 0.0, False)])
+def test_pure_neumann_solve_equals_projected_dense_solve(dim, n, a, hetero):
+    """L u = f - <f>, zero normal derivative everywhere: the oracle's converged solution equals the
+    dense solve (a != 0) or the dense least-squares solve with the zero-mean constraint (a = 0),
+    and has zero trapezoid mean."""
+    rng = np.random.default_rng(40 + n)
+    N = 2 ** n + 1
+    shape = (N,) * dim
+    f = rng.standard_normal(shape)
+    sigma = np.exp(0.4 * rng.standard_normal(shape)) if hetero else None
+    p = Problem(dim, n, faces=[NEUMANN] * (2 * dim), values=[0.0] * (2 * dim), sigma=sigma, a_scalar=a)
+    assert p.projects_mean()
+    A, b, idx = assemble(p)
+    assert idx.size == f.size and np.abs(b).max() == 0.0
+    w = trapezoid_weights(p).ravel()
+    rhs = f.ravel() - np.dot(w, f.ravel()) / w.sum()
+    if a != 0.0:
+        u_ref = np.linalg.solve(A, rhs)
+    else:
+        K = np.vstack([A, w[None, :]])
+        u_ref = np.linalg.lstsq(K, np.concatenate([rhs, [0.0]]), rcond=None)[0]
+    u, cycles, hist = p.solve(f, tol=1e-13, max_cycles=400)
+    assert cycles > 0
+    assert np.linalg.norm(u.ravel() - u_ref) <= 1e-10 * np.linalg.norm(u_ref)
+    assert abs(p.mean(u)) <= 1e-13 * np.abs(u).max()
+
+
+def test_circle_source_has_the_circle_length_as_integral():
+    f = inputs.circle_source_2d(6, radius=0.25)
+    h = 1.0 / 64
+    assert np.sum(f) * h * h == pytest.approx(2 * np.pi * 0.25, rel=1e-12)
