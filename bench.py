@@ -136,6 +136,28 @@ def dist_env():
     return world, rank, local
 
 
+def max_over_ranks(x, device):
+    """The largest value of x over the ranks of the initialised process group (x itself alone)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_seed(rank):
+    """Seed of the workload replica a rank solves (replicas only: no data is exchanged)."""
+    return 2000 + rank
+
+
+def whole_job_rate(world, nodes_per_replica, ms_per_step):
+    """Solved nodes per second of all replicas: every rank solves its own replica per step; the step
+    time is the slowest rank's."""
+    return world * nodes_per_replica / (ms_per_step / 1e3)
+
+
 # ------------------------------------------------------------------------------------------------
 # CPU oracle sample (the cpu_baseline leg and the reference arm)
 # ------------------------------------------------------------------------------------------------
@@ -237,7 +259,7 @@ def run_gpu(args):
     n = args.n
     N = 2 ** n + 1
     M = N ** 3
-    d = inputs.dielectric_spheres_3d(n=n, seed=2000 + rank)
+    d = inputs.dielectric_spheres_3d(n=n, seed=replica_seed(rank))
     f = np.ascontiguousarray(d["f"])
     sig = np.ascontiguousarray(d["sigma"])
     f_dev = torch.from_numpy(f).to(f"cuda:{local}")
@@ -262,12 +284,9 @@ def run_gpu(args):
         torch.cuda.synchronize()
         with ClockSampler(local) as clk:
             total_ms, kernel_ms, cycles, rel, launches = time_solves(torch, g, stream, steps, args.warmup)
-        if world > 1:
-            t = torch.tensor([total_ms], device=f"cuda:{local}")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            total_ms = float(t.item())
+        total_ms = max_over_ranks(total_ms, f"cuda:{local}")
         ms = total_ms / steps
-        value = world * M / (ms / 1e3)
+        value = whole_job_rate(world, M, ms)
         achieved = BYTES_PER_NODE_CYCLE[form] * M * cycles / (kernel_ms / 1e3) / 1e9
         tr = traffic.get(form)
         ctas, threads, smem = g.launch_info()
@@ -307,10 +326,7 @@ def run_gpu(args):
             g.get_solution(0, u_h)
         torch.cuda.synchronize()
         el = time.perf_counter() - t0
-        if world > 1:
-            t = torch.tensor([el], device=f"cuda:{local}")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            el = float(t.item())
+        el = max_over_ranks(el, f"cuda:{local}")
         e2e = {"value": world * M * args.steps / el, "unit": "nodes/s", "h2d_bytes_per_step": 2 * M * 8,
                "d2h_bytes_per_step": M * 8}
     cpu = None
