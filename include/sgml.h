@@ -231,7 +231,29 @@ int sgml_curl(int n, const double* psi, double* v, void* cuda_stream);
 int sgml_streamlines(int n, const double* v, const double* seeds, int nseeds, double dt, int nsteps, double* paths,
                      int* lengths, void* cuda_stream);
 
-/* Message of the last failed sgml_curl / sgml_streamlines call on this thread. */
+/* ---- Grid motion of the grid-deformation application (Sec. 3.2, Eq. 11) ----------------------
+ * Moves points (normally the grid's nodes) by forward Euler in a pseudo-time t along
+ * dx/dt = v = -grad u / (t f + int f dOmega), u the force potential of Eq. 10 (zero normal
+ * derivative on every face; e.g. a solution of an all-Neumann grid) and f its source, both
+ * N^dim node arrays (N = 2^n + 1; 2-D: 1 <= n <= 14, 3-D: 1 <= n <= 10) on the unit square /
+ * cube, row-major ([y][x] or [z][y][x]), device memory.  The paper gives only the formula and
+ * "finite differences of the potential"; read here as:
+ *   - grad u at the nodes by central differences with the Neumann images u(-1) = u(1),
+ *     u(N) = u(N-2) (zero normal component on the faces: face nodes slide along their faces);
+ *   - grad u and f at a point by multilinear interpolation in the grid cell holding it;
+ *   - int f dOmega by the trapezoid rule (V = 1);
+ *   - nsteps equal steps from t0 to t1 (the paper's deformation runs t from 0 to 1), every
+ *     coordinate clamped to [0, 1] before the first step and after each step.
+ * x (device, in/out): dim x N^dim doubles, x[a * N^dim + node] the a-th coordinate (a = 0: x) of
+ * the point that starts at node `node`; initialise it to the node coordinates for the paper's grid
+ * deformation.  x must not alias u or f.  Synchronises cuda_stream (reads back int f and min f).
+ * SGML_ERR_ARG for a bad dim or n, NULL, aliasing or host arrays, t0 < 0, t1 < t0, nsteps < 0, or
+ * a denominator that could reach zero (int f <= 0 or int f + t1 min f <= 0; a non-negative source
+ * such as the paper's delta function along a curve always passes). */
+int sgml_grid_motion(int dim, int n, const double* u, const double* f, double t0, double t1, int nsteps, double* x,
+                     void* cuda_stream);
+
+/* Message of the last failed sgml_curl / sgml_streamlines / sgml_grid_motion call on this thread. */
 const char* sgml_post_last_error(void);
 
 int sgml_destroy(sgml_grid_t g);

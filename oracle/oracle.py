@@ -84,6 +84,10 @@ def _load():
         lib.orc_sigma_gradient.argtypes = [P, D, D, D]
         lib.orc_curl.argtypes = [I, D, D]
         lib.orc_streamlines.argtypes = [I, D, D, I, ctypes.c_double, I, D, ctypes.POINTER(I)]
+        lib.orc_trapezoid.argtypes = [I, I, D]
+        lib.orc_trapezoid.restype = ctypes.c_double
+        lib.orc_neumann_gradient.argtypes = [I, I, D, D]
+        lib.orc_grid_motion.argtypes = [I, I, D, D, ctypes.c_double, ctypes.c_double, I, D]
         _lib = lib
     return _lib
 
@@ -319,3 +323,50 @@ def streamlines(v, seeds, dt, nsteps):
     lengths = (ctypes.c_int * S)()
     _load().orc_streamlines(n, _ptr(v), _ptr(seeds), S, float(dt), int(nsteps), _ptr(paths), lengths)
     return paths, np.array(lengths[:], dtype=np.int64)
+
+
+# --- grid motion of Sec. 3.2 (Eq. 11) ------------------------------------------------------------
+def _square_field(v, name):
+    v = np.ascontiguousarray(np.asarray(v, dtype=np.float64))
+    dim = v.ndim
+    N = v.shape[0]
+    n = int(round(np.log2(N - 1))) if N > 2 else 0
+    if dim not in (2, 3) or any(s != N for s in v.shape) or n < 1 or 2 ** n + 1 != N:
+        raise ValueError(f"{name} must be an N^2 or N^3 array with N = 2^n + 1")
+    return v, dim, n
+
+
+def grid_nodes(dim, N):
+    """Node positions of the unit grid: array (dim, N, ..., N), component a = coordinate x_a."""
+    x = np.linspace(0.0, 1.0, N)
+    mesh = np.meshgrid(*([x] * dim), indexing="ij")  # mesh[k] varies along array axis k
+    return np.stack([mesh[dim - 1 - a] for a in range(dim)])
+
+
+def trapezoid(f):
+    """Trapezoid-rule integral of the node field f over the unit square / cube."""
+    f, dim, n = _square_field(f, "f")
+    return _load().orc_trapezoid(dim, n, _ptr(f))
+
+
+def neumann_gradient(u):
+    """grad u at the nodes (dim, N, ...), central differences with the Neumann images."""
+    u, dim, n = _square_field(u, "u")
+    g = np.empty((dim,) + u.shape)
+    _load().orc_neumann_gradient(dim, n, _ptr(u), _ptr(g))
+    return g
+
+
+def grid_motion(u, f, nsteps, t0=0.0, t1=1.0, x=None):
+    """Node positions after nsteps forward-Euler steps of dx/dt = -grad u / (t f + int f) (Eq. 11)
+    from pseudo-time t0 to t1, starting from x (default: the grid nodes); array (dim, N, ..., N)."""
+    u, dim, n = _square_field(u, "u")
+    f = np.ascontiguousarray(np.asarray(f, dtype=np.float64))
+    if f.shape != u.shape:
+        raise ValueError("f and u must have the same shape")
+    x = grid_nodes(dim, u.shape[0]) if x is None else np.array(x, dtype=np.float64, copy=True)
+    x = np.ascontiguousarray(x)
+    if x.shape != (dim,) + u.shape:
+        raise ValueError("x must have shape (dim,) + u.shape")
+    _load().orc_grid_motion(dim, n, _ptr(u), _ptr(f), float(t0), float(t1), int(nsteps), _ptr(x))
+    return x

@@ -734,3 +734,114 @@ void orc_streamlines(int n, const double* v, const double* seeds, int nseeds, do
     lengths[sd] = len;
   }
 }
+
+/* ------------------------------------------------------------------------------------------ */
+/* Grid motion of Sec. 3.2: the nodes of the grid are advanced by forward Euler in a pseudo-time t */
+/* along dx/dt = v with v = -grad u / (t f + int f dOmega) (Eq. 11), u the force potential of      */
+/* Eq. 10 (zero normal derivative on every face) and f its source.  Readings (the paper gives only */
+/* the formula and "finite differences of the potential"):                                        */
+/*   - grad u at the nodes by central differences with the Neumann images u(-1) = u(1),            */
+/*     u(N) = u(N-2), so its normal component is zero on the faces;                               */
+/*   - grad u and f at a moving node by multilinear interpolation of their node values in the     */
+/*     cell that holds it (cells clamped to the grid);                                            */
+/*   - int f dOmega by the trapezoid rule on the unit square / cube (V = 1);                       */
+/*   - nsteps equal steps from t0 to t1 (the paper's deformation runs t from 0 to 1); every      */
+/*     coordinate is clamped to [0, 1] before the first step and after each step.                 */
+/* Positions: x[a * M + node], a = 0 .. dim-1 the coordinate, node row-major [z][y][x].            */
+/* ------------------------------------------------------------------------------------------ */
+static long orc_node_index(int dim, int N, const int c[3]) {
+  long i = 0;
+  for (int a = dim - 1; a >= 0; --a) i = i * N + c[a];
+  return i;
+}
+
+double orc_trapezoid(int dim, int n, const double* f) {
+  const int N = (1 << n) + 1;
+  const double h = 1.0 / (double)(N - 1);
+  long M = 1;
+  for (int a = 0; a < dim; ++a) M *= N;
+  double s = 0.0;
+  for (long i = 0; i < M; ++i) {
+    long r = i;
+    double w = 1.0;
+    for (int a = 0; a < dim; ++a) {
+      const int c = (int)(r % N);
+      r /= N;
+      w *= (c == 0 || c == N - 1) ? 0.5 * h : h;
+    }
+    s += w * f[i];
+  }
+  return s;
+}
+
+/* grad u at every node: g[a * M + node] = (u(c + e_a) - u(c - e_a)) / (2h), Neumann images. */
+void orc_neumann_gradient(int dim, int n, const double* u, double* g) {
+  const int N = (1 << n) + 1;
+  const double h = 1.0 / (double)(N - 1);
+  long M = 1;
+  for (int a = 0; a < dim; ++a) M *= N;
+  for (long i = 0; i < M; ++i) {
+    int c[3] = {0, 0, 0};
+    long r = i;
+    for (int a = 0; a < dim; ++a) c[a] = (int)(r % N), r /= N;
+    for (int a = 0; a < dim; ++a) {
+      int cp[3] = {c[0], c[1], c[2]}, cm[3] = {c[0], c[1], c[2]};
+      cp[a] = c[a] + 1 > N - 1 ? N - 2 : c[a] + 1;
+      cm[a] = c[a] - 1 < 0 ? 1 : c[a] - 1;
+      g[a * M + i] = (u[orc_node_index(dim, N, cp)] - u[orc_node_index(dim, N, cm)]) / (2.0 * h);
+    }
+  }
+}
+
+/* Multilinear interpolation of the node field v (N^dim values) at the point x. */
+static double orc_interp_nodes(int dim, int N, const double* v, const double* x) {
+  int i0[3] = {0, 0, 0};
+  double t[3] = {0.0, 0.0, 0.0};
+  for (int a = 0; a < dim; ++a) {
+    const double gx = x[a] * (double)(N - 1);
+    int i = (int)floor(gx);
+    if (i < 0) i = 0;
+    if (i > N - 2) i = N - 2;
+    i0[a] = i;
+    t[a] = gx - (double)i;
+  }
+  double acc = 0.0;
+  for (int corner = 0; corner < (1 << dim); ++corner) {
+    int c[3] = {0, 0, 0};
+    double w = 1.0;
+    for (int a = 0; a < dim; ++a) {
+      const int up = (corner >> a) & 1;
+      c[a] = i0[a] + up;
+      w *= up ? t[a] : 1.0 - t[a];
+    }
+    acc += w * v[orc_node_index(dim, N, c)];
+  }
+  return acc;
+}
+
+void orc_grid_motion(int dim, int n, const double* u, const double* f, double t0, double t1, int nsteps, double* x) {
+  const int N = (1 << n) + 1;
+  long M = 1;
+  for (int a = 0; a < dim; ++a) M *= N;
+  double* g = (double*)malloc(sizeof(double) * dim * M);
+  orc_neumann_gradient(dim, n, u, g);
+  const double F = orc_trapezoid(dim, n, f);
+  const double dt = nsteps > 0 ? (t1 - t0) / (double)nsteps : 0.0;
+  for (long i = 0; i < M; ++i) {
+    double p[3] = {0.0, 0.0, 0.0};
+    for (int a = 0; a < dim; ++a) p[a] = x[a * M + i] < 0.0 ? 0.0 : (x[a * M + i] > 1.0 ? 1.0 : x[a * M + i]);
+    for (int k = 0; k < nsteps; ++k) {
+      const double t = t0 + (double)k * dt;
+      double v[3];
+      const double den = t * orc_interp_nodes(dim, N, f, p) + F;
+      for (int a = 0; a < dim; ++a) v[a] = -orc_interp_nodes(dim, N, g + a * M, p) / den;
+      for (int a = 0; a < dim; ++a) {
+        p[a] = p[a] + dt * v[a];
+        if (p[a] < 0.0) p[a] = 0.0;
+        if (p[a] > 1.0) p[a] = 1.0;
+      }
+    }
+    for (int a = 0; a < dim; ++a) x[a * M + i] = p[a];
+  }
+  free(g);
+}

@@ -1,13 +1,17 @@
 // sgml_post.cu -- post-processing of the vortex application (Sec. 3.3): the velocity v = curl psi
-// of a solved stream vector potential (Eq. 14) and streamlines of v.
+// of a solved stream vector potential (Eq. 14) and streamlines of v; and the grid motion of the
+// grid-deformation application (Sec. 3.2, Eq. 11).
 //
-// The paper leaves both to its visualisation tool.  Readings: second-order central differences at
+// The paper leaves curl and streamlines to its visualisation tool.  Readings: second-order central differences at
 // interior nodes, second-order one-sided differences (-3 f0 + 4 f1 - f2) / (2h) on the faces;
 // streamlines by the classical fourth-order Runge-Kutta method with a fixed step, the velocity
 // interpolated trilinearly between nodes, a path ending when a stage point or its next position
-// leaves the unit cube.
+// leaves the unit cube.  Grid motion: read as in the header (forward Euler over nsteps equal steps
+// of pseudo-time, central differences with Neumann images, multilinear interpolation, trapezoid
+// integral of f, coordinates clamped to the unit square / cube).
 #include <cuda_runtime.h>
 
+#include <cmath>
 #include <string>
 
 #include "sgml.h"
@@ -117,6 +121,128 @@ __global__ void streamline_kernel(int N, const double* __restrict__ v, const dou
   lengths[sd] = len;
 }
 
+// ---- Grid motion of the grid-deformation application (Sec. 3.2, Eq. 11) ----------------------
+// Trapezoid-rule integral over the unit square / cube and minimum of the node field f: per-block
+// partials (grid-stride over the nodes, warp shuffles, one shared slot per warp), folded in a
+// fixed order by one block.
+constexpr int kRedThreads = 256;
+
+__device__ __forceinline__ void block_fold(double& s, double& m, double* sh_s, double* sh_m) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    s += __shfl_xor_sync(0xffffffffu, s, o);
+    m = fmin(m, __shfl_xor_sync(0xffffffffu, m, o));
+  }
+  const int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) sh_s[w] = s, sh_m[w] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    s = sh_s[0], m = sh_m[0];
+    for (int k = 1; k < (int)(blockDim.x >> 5); ++k) s += sh_s[k], m = fmin(m, sh_m[k]);
+  }
+}
+
+__global__ void __launch_bounds__(kRedThreads) integral_partial_kernel(int dim, int N, long long M,
+                                                                       const double* __restrict__ f,
+                                                                       double* __restrict__ part) {
+  __shared__ double sh_s[kRedThreads / 32], sh_m[kRedThreads / 32];
+  const double h = 1.0 / (double)(N - 1);
+  double s = 0.0, m = INFINITY;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < M; i += (long long)gridDim.x * blockDim.x) {
+    long long r = i;
+    double w = 1.0;
+    for (int a = 0; a < dim; ++a) {
+      const int c = (int)(r % N);
+      r /= N;
+      w *= (c == 0 || c == N - 1) ? 0.5 * h : h;
+    }
+    const double v = f[i];
+    s += w * v;
+    m = fmin(m, v);
+  }
+  block_fold(s, m, sh_s, sh_m);
+  if (threadIdx.x == 0) part[2 * blockIdx.x] = s, part[2 * blockIdx.x + 1] = m;
+}
+
+__global__ void __launch_bounds__(kRedThreads) integral_finish_kernel(int nparts, const double* __restrict__ part,
+                                                                      double* __restrict__ out) {
+  __shared__ double sh_s[kRedThreads / 32], sh_m[kRedThreads / 32];
+  double s = 0.0, m = INFINITY;
+  for (int k = threadIdx.x; k < nparts; k += blockDim.x) s += part[2 * k], m = fmin(m, part[2 * k + 1]);
+  block_fold(s, m, sh_s, sh_m);
+  if (threadIdx.x == 0) out[0] = s, out[1] = m;
+}
+
+// d u / d x_a at node c by central differences with the Neumann images u(-1) = u(1), u(N) = u(N-2).
+template <int DIM>
+__device__ __forceinline__ double neumann_deriv(const double* __restrict__ u, int N, double two_h, const int c[DIM],
+                                                int a) {
+  long long stride = 1, base = 0;
+  for (int b = DIM - 1; b >= 0; --b) base = base * N + c[b];
+  for (int b = 0; b < a; ++b) stride *= N;
+  const int up = c[a] + 1 > N - 1 ? N - 2 : c[a] + 1;
+  const int dn = c[a] - 1 < 0 ? 1 : c[a] - 1;
+  return (__ldg(u + base + (long long)(up - c[a]) * stride) - __ldg(u + base + (long long)(dn - c[a]) * stride)) /
+         two_h;
+}
+
+// One thread per node: nsteps forward-Euler steps of dx/dt = -grad u / (t f + F), grad u and f
+// interpolated multilinearly from the node values of the cell holding the moving node (the node
+// values of grad u formed on the fly from u), every coordinate clamped to [0, 1].
+template <int DIM>
+__global__ void __launch_bounds__(256) grid_motion_kernel(int N, long long M, const double* __restrict__ u,
+                                                          const double* __restrict__ f, double F, double t0,
+                                                          double dt, int nsteps, double* __restrict__ x) {
+  const double h = 1.0 / (double)(N - 1);
+  const double two_h = 2.0 * h;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < M; i += (long long)gridDim.x * blockDim.x) {
+    double p[DIM];
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) p[a] = fmin(fmax(x[a * M + i], 0.0), 1.0);
+    for (int k = 0; k < nsteps; ++k) {
+      const double t = t0 + (double)k * dt;
+      int i0[DIM];
+      double w[DIM];
+#pragma unroll
+      for (int a = 0; a < DIM; ++a) {
+        const double g = p[a] * (double)(N - 1);
+        int c = (int)floor(g);
+        c = c < 0 ? 0 : (c > N - 2 ? N - 2 : c);
+        i0[a] = c;
+        w[a] = g - (double)c;
+      }
+      double fi = 0.0, gi[DIM];
+#pragma unroll
+      for (int a = 0; a < DIM; ++a) gi[a] = 0.0;
+#pragma unroll
+      for (int corner = 0; corner < (1 << DIM); ++corner) {
+        int c[DIM];
+        double wt = 1.0;
+        long long idx = 0;
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) {
+          const int up = (corner >> a) & 1;
+          c[a] = i0[a] + up;
+          wt *= up ? w[a] : 1.0 - w[a];
+        }
+#pragma unroll
+        for (int a = DIM - 1; a >= 0; --a) idx = idx * N + c[a];
+        fi += wt * __ldg(f + idx);
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) gi[a] += wt * neumann_deriv<DIM>(u, N, two_h, c, a);
+      }
+      const double den = t * fi + F;
+#pragma unroll
+      for (int a = 0; a < DIM; ++a) {
+        const double v = -gi[a] / den;
+        p[a] = fmin(fmax(p[a] + dt * v, 0.0), 1.0);
+      }
+    }
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) x[a * M + i] = p[a];
+  }
+}
+
 bool device_pointer(const void* p) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
@@ -159,6 +285,50 @@ int sgml_streamlines(int n, const double* v, const double* seeds, int nseeds, do
   streamline_kernel<<<(nseeds + 127) / 128, 128, 0, (cudaStream_t)cuda_stream>>>(N, v, seeds, nseeds, dt, nsteps,
                                                                                  paths, lengths);
   const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? SGML_OK : post_fail(SGML_ERR_CUDA, cudaGetErrorString(e));
+}
+
+int sgml_grid_motion(int dim, int n, const double* u, const double* f, double t0, double t1, int nsteps, double* x,
+                     void* cuda_stream) {
+  if (dim != 2 && dim != 3) return post_fail(SGML_ERR_ARG, "dim must be 2 or 3");
+  if (n < 1 || n > (dim == 2 ? 14 : 10)) return post_fail(SGML_ERR_ARG, "n must be in 1..14 (2-D) or 1..10 (3-D)");
+  if (!(t0 >= 0.0) || !(t1 >= t0) || nsteps < 0) return post_fail(SGML_ERR_ARG, "need 0 <= t0 <= t1 and nsteps >= 0");
+  if (!u || !f || !x) return post_fail(SGML_ERR_ARG, "NULL array");
+  if ((const void*)x == (const void*)u || (const void*)x == (const void*)f)
+    return post_fail(SGML_ERR_ARG, "x must not alias u or f");
+  if (!device_pointer(u) || !device_pointer(f) || !device_pointer(x))
+    return post_fail(SGML_ERR_ARG, "u, f and x must be device arrays");
+  const cudaStream_t s = (cudaStream_t)cuda_stream;
+  const int N = (1 << n) + 1;
+  long long M = 1;
+  for (int a = 0; a < dim; ++a) M *= N;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const long long want = (M + kRedThreads - 1) / kRedThreads;
+  const int parts = (int)(want < 4LL * sms ? want : 4LL * sms);
+  double* scratch = nullptr;
+  cudaError_t e = cudaMallocAsync((void**)&scratch, sizeof(double) * (2 * (size_t)parts + 2), s);
+  if (e != cudaSuccess) return post_fail(SGML_ERR_CUDA, cudaGetErrorString(e));
+  integral_partial_kernel<<<parts, kRedThreads, 0, s>>>(dim, N, M, f, scratch);
+  integral_finish_kernel<<<1, kRedThreads, 0, s>>>(parts, scratch, scratch + 2 * parts);
+  double Fm[2] = {0.0, 0.0};
+  e = cudaMemcpyAsync(Fm, scratch + 2 * parts, sizeof(Fm), cudaMemcpyDeviceToHost, s);
+  const cudaError_t e_sync = e == cudaSuccess ? cudaStreamSynchronize(s) : e;
+  cudaFreeAsync(scratch, s);
+  if (e_sync != cudaSuccess) return post_fail(SGML_ERR_CUDA, cudaGetErrorString(e_sync));
+  const double F = Fm[0], fmin_v = Fm[1];
+  // t f + F >= min(F, F + t1 min f) for an interpolated f inside the domain
+  if (!(F > 0.0) || !(F + t1 * fmin_v > 0.0))
+    return post_fail(SGML_ERR_ARG, "the velocity denominator t f + int f must stay positive (int f = " +
+                                       std::to_string(F) + ", min f = " + std::to_string(fmin_v) + ")");
+  const double dt = nsteps > 0 ? (t1 - t0) / (double)nsteps : 0.0;
+  const long long blocks = (M + 255) / 256;
+  if (dim == 2)
+    grid_motion_kernel<2><<<(unsigned)blocks, 256, 0, s>>>(N, M, u, f, F, t0, dt, nsteps, x);
+  else
+    grid_motion_kernel<3><<<(unsigned)blocks, 256, 0, s>>>(N, M, u, f, F, t0, dt, nsteps, x);
+  e = cudaGetLastError();
   return e == cudaSuccess ? SGML_OK : post_fail(SGML_ERR_CUDA, cudaGetErrorString(e));
 }
 

@@ -76,6 +76,8 @@ _SIGNATURES = {
     "sgml_curl": [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
     "sgml_streamlines": [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_int,
                          ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
+    "sgml_grid_motion": [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double,
+                         ctypes.c_double, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p],
     "sgml_post_last_error": [],
 }
 
@@ -367,6 +369,39 @@ def streamlines(v, seeds, dt, nsteps, stream=None):
     if st != OK:
         raise SGMLError(st, lib.sgml_post_last_error().decode())
     return paths, lengths
+
+
+def grid_motion(u, f, nsteps, t0=0.0, t1=1.0, x=None, stream=None):
+    """Grid motion of Sec. 3.2 (Eq. 11): nsteps forward-Euler steps of dx/dt = -grad u / (t f + int f)
+    from pseudo-time t0 to t1.  u, f: CUDA float64 tensors of shape (N, N) or (N, N, N) (the force
+    potential and its source); x: start positions (dim,) + u.shape, default the grid's nodes
+    (component a = coordinate x_a).  Returns the moved positions (a new CUDA tensor)."""
+    import torch
+    for name, t in (("u", u), ("f", f)):
+        if not (hasattr(t, "is_cuda") and t.is_cuda) or t.dtype != torch.float64:
+            raise TypeError(f"{name} must be a CUDA float64 tensor")
+    u, f = u.contiguous(), f.contiguous()
+    dim = u.dim()
+    N = u.shape[0]
+    n = int(round(np.log2(N - 1))) if N > 2 else 0
+    if dim not in (2, 3) or any(s != N for s in u.shape) or n < 1 or 2 ** n + 1 != N:
+        raise ValueError("u must have shape (N, N) or (N, N, N) with N = 2^n + 1")
+    if tuple(f.shape) != tuple(u.shape):
+        raise ValueError("f and u must have the same shape")
+    if x is None:
+        g = torch.linspace(0.0, 1.0, N, dtype=torch.float64, device=u.device)
+        mesh = torch.meshgrid(*([g] * dim), indexing="ij")
+        x = torch.stack([mesh[dim - 1 - a] for a in range(dim)]).contiguous()
+    else:
+        x = torch.as_tensor(x, dtype=torch.float64, device=u.device).clone().contiguous()
+        if tuple(x.shape) != (dim,) + tuple(u.shape):
+            raise ValueError("x must have shape (dim,) + u.shape")
+    lib = load()
+    st = lib.sgml_grid_motion(dim, n, u.data_ptr(), f.data_ptr(), float(t0), float(t1), int(nsteps), x.data_ptr(),
+                              _stream_ptr(stream))
+    if st != OK:
+        raise SGMLError(st, lib.sgml_post_last_error().decode())
+    return x
 
 
 def problem_into_grid(grid, b, prob):
