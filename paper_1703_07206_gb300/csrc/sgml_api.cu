@@ -313,9 +313,11 @@ static int build_coeffs(sgml_grid* g) {
   std::vector<double*> tmp;
   for (int b = 0; b < g->batch; ++b) {
     ProblemDesc& P = g->P[b];
-    for (int l = 0; l < kMaxLevels; ++l) P.q_const[l] = 0.0;
+    for (int l = 0; l < kMaxLevels; ++l) P.q_const[l] = 0.0, P.inv_c[l] = 0.0;
+    P.c0 = kap / (2.0 * P.h * P.h);
     for (int l = 0; l <= P.n - 1; ++l) {
       const double H = P.h * (double)(1LL << l);
+      P.inv_c[l] = 2.0 * H * H / kap;
       const double c = kap / (2.0 * H * H);
       const double D = c * 2.0 * weight_sum(g->dim) - P.a_scalar;
       P.q_const[l] = tg / D * c;

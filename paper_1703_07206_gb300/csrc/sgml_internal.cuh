@@ -57,6 +57,8 @@ struct ProblemDesc {
   long long off_full;              // element offset in the FP64 full-grid pools
   long long off_lvl[kMaxLevels];   // element offset of level l in the level pools
   double q_const[kMaxLevels];      // homogeneous problems: delta_tau * kappa / (2 H^2) per level
+  double inv_c[kMaxLevels];        // 2 H^2 / kappa per level (the sweep's 1 / c)
+  double c0;                       // kappa / (2 h^2) (the level-0 residual's factor)
   int project_mean;                // every face Neumann, a >= 0 constant: Eq. 10, zero-mean u
 };
 
@@ -66,6 +68,7 @@ struct ProblemState {
   double fnorm2;          // L2 normaliser
   double rmax_prev;       // max-norm of the latest residual (sets the next cast scale)
   double scale_used[2];   // scale of the residual cast in cycle c (slot c & 1)
+  double inv_scale[2];    // 1 / scale_used (no FP64 division per tile)
   double rel, rel_l2;     // latest relative residuals
   double rel_prev;
   int cycles;             // cycles completed since the last reset

@@ -192,7 +192,31 @@ __shared__ Phase s_phase[kPhaseCache];
 __shared__ int s_toff[kMaxLevels][2];
 __shared__ TileTask s_task[kMaxLevels][kTaskCache];
 
+// Also cached: problem 0's descriptor, the number of node rows of every level (row phases), and,
+// once per cycle, the problems' stop flags (written by the convergence check between two barriers):
+// every phase reads them, and after a grid barrier each would be an L2 round trip.
+constexpr int kDoneCache = 256;
+__shared__ ProblemDesc s_prob0;
+__shared__ long long s_rows[kMaxLevels];
+__shared__ unsigned char s_done[kDoneCache];
+
+__device__ __forceinline__ const ProblemDesc& prob_at(const KernelParams& p, int b) {
+  return b == 0 ? s_prob0 : p.probs[b];
+}
+
+__device__ __forceinline__ bool done_at(const KernelParams& p, int b) {
+  return b < kDoneCache ? s_done[b] != 0 : p.accum[b].done != 0;
+}
+
+__device__ void load_done(const KernelParams& p) {
+  for (int b = threadIdx.x; b < p.batch && b < kDoneCache; b += blockDim.x)
+    s_done[b] = (unsigned char)(ld_volatile(&p.accum[b].done) != 0);
+  __syncthreads();
+}
+
 __device__ void load_tables(const KernelParams& p) {
+  if (threadIdx.x == 0) s_prob0 = p.probs[0];
+  if (threadIdx.x < kMaxLevels) s_rows[threadIdx.x] = p.row_prefix[(long long)threadIdx.x * (p.batch + 1) + p.batch];
   for (int i = threadIdx.x; i < p.nphases && i < kPhaseCache; i += blockDim.x) s_phase[i] = p.phases[i];
   if (threadIdx.x < kMaxLevels) {
     const int l = threadIdx.x;
@@ -224,12 +248,13 @@ __device__ __forceinline__ void for_tasks(const KernelParams& p, int l, Body&& b
 template <int DIM, class Body>
 __device__ __forceinline__ void for_rows(const KernelParams& p, int l, Body&& body) {
   const long long* rp = p.row_prefix + (long long)l * (p.batch + 1);
-  const long long total = rp[p.batch];
+  const long long total = s_rows[l];
   const int warps = blockDim.x >> 5;
   int b = 0;
   for (long long r = (long long)blockIdx.x * warps + (threadIdx.x >> 5); r < total; r += (long long)gridDim.x * warps) {
-    while (rp[b + 1] <= r) ++b;
-    const ProblemDesc& P = p.probs[b];
+    if (p.batch > 1)
+      while (rp[b + 1] <= r) ++b;
+    const ProblemDesc& P = prob_at(p, b);
     const int N = level_side(P.n, l);
     const int local = (int)(r - rp[b]);
     body(b, P, N, DIM == 3 ? local % N : local, DIM == 3 ? local / N : 0);
@@ -591,7 +616,7 @@ __device__ __forceinline__ void res_finish(const ResSrc<V>& src, V c0v, V sum, V
 template <typename T, typename V, bool HET>
 __device__ void residual3(const KernelParams& p, const TileTask& tk, int c, ResStage<V>* st, const ResSrc<V>& src) {
   constexpr int D = kOuterStages;
-  const ProblemDesc& P = p.probs[tk.b];
+  const ProblemDesc& P = prob_at(p, tk.b);
   const int N = level_side(P.n, 0);
   const int tid = threadIdx.x;
   const Columns cl = own_columns(P, N, tk.x0, tk.y0);
@@ -601,7 +626,7 @@ __device__ void residual3(const KernelParams& p, const TileTask& tk, int c, ResS
   float2* RES = p.RESP ? p.RESP + P.off_full : nullptr;
   const bool flux = src.images && tile_has_flux(P, N, tk.x0, tk.y0, 3);
   const HaloCells hc = halo_cells(P, N, tk.x0, tk.y0, flux);
-  const V c0v = (V)(p.kappa / (2.0 * P.h * P.h) * (HET ? 1.0 : 2.0));
+  const V c0v = (V)(P.c0 * (HET ? 1.0 : 2.0));
   const V a_s = (V)src.a_scalar;
   const V w_e = (V)p.w_edge, w_c = (V)p.w_corner;
   const int b0 = (2 * (tid / kTX)) * kHX + (tid % kTX);  // top-left of the thread's 4 x 3 block
@@ -700,7 +725,7 @@ template <typename T, bool HET>
 __device__ void residual3r(const KernelParams& p, const TileTask& tk, int c, ResStage<T>* st, const ResSrc<T>& src) {
   using V = T;
   constexpr int D = kOuterStages;
-  const ProblemDesc& P = p.probs[tk.b];
+  const ProblemDesc& P = prob_at(p, tk.b);
   const int N = level_side(P.n, 0);
   const int tid = threadIdx.x;
   const Columns cl = own_columns(P, N, tk.x0, tk.y0);
@@ -709,7 +734,7 @@ __device__ void residual3r(const KernelParams& p, const TileTask& tk, int c, Res
   T* R0 = (T*)p.R + P.off_lvl[0];
   float2* RES = p.RESP + P.off_full;
   const HaloCells hc = halo_cells(P, N, tk.x0, tk.y0, false);
-  const V c0v = (V)(p.kappa / (2.0 * P.h * P.h) * (HET ? 1.0 : 2.0));
+  const V c0v = (V)(P.c0 * (HET ? 1.0 : 2.0));
   const V a_s = (V)src.a_scalar;
   const V w_e = (V)p.w_edge, w_c = (V)p.w_corner;
   const int b0 = (2 * (tid / kTX)) * kHX + (tid % kTX);
@@ -812,7 +837,7 @@ template <typename T>
 __device__ __forceinline__ bool use_anchor(const KernelParams& p, int b, int c) {
   // Eq. 10 problems: every residual from the projected u (the FP32 recurrence does not follow the
   // projection's constant shift)
-  return !p.mixed || c == 0 || p.state[b].anchor_next || p.probs[b].project_mean;
+  return !p.mixed || c == 0 || p.state[b].anchor_next || prob_at(p, b).project_mean;
 }
 
 __device__ __forceinline__ ResSrc<double> anchor_src(const KernelParams& p, const ProblemDesc& P) {
@@ -838,7 +863,7 @@ __device__ __forceinline__ ResSrc<T> recur_src(const KernelParams& p, const Prob
   s.rhs = reinterpret_cast<const double*>(p.RESP + P.off_full);
   s.a = P.a_per_node ? (const T*)p.A0 + P.off_lvl[0] : nullptr;
   s.a_scalar = P.a_scalar;
-  s.opscale = 1.0 / p.state[b].scale_used[(c - 1) & 1];
+  s.opscale = p.state[b].inv_scale[(c - 1) & 1];
   s.opscale32 = (float)s.opscale;
   s.images = false;
   return s;
@@ -853,16 +878,16 @@ __device__ void residual2(const KernelParams& p, int c, ResStage<V>* st, bool an
   const int tid = threadIdx.x;
   const int b0 = (2 * (tid / kTX)) * kHX + (tid % kTX);
   auto task = [&](int j) -> const TileTask& { return p.tasks[t0 + j]; };
-  auto mine = [&](int b) { return !p.accum[b].done && use_anchor<T>(p, b, c) == anchor; };
+  auto mine = [&](int b) { return !done_at(p, b) && use_anchor<T>(p, b, c) == anchor; };
   auto source = [&](int b) -> ResSrc<V> {
-    if constexpr (sizeof(V) == 8) return anchor_src(p, p.probs[b]);
-    else return recur_src<T>(p, p.probs[b], b, c);
+    if constexpr (sizeof(V) == 8) return anchor_src(p, prob_at(p, b));
+    else return recur_src<T>(p, prob_at(p, b), b, c);
   };
   auto issue = [&](int j) {
     if (j < J) {
       const TileTask& tk = task(j);
       if (mine(tk.b)) {
-        const ProblemDesc& P = p.probs[tk.b];
+        const ProblemDesc& P = prob_at(p, tk.b);
         const int N = level_side(P.n, 0);
         const HaloCells hc = halo_cells(P, N, tk.x0, tk.y0, false);
         const Columns cl = own_columns(P, N, tk.x0, tk.y0);
@@ -891,7 +916,7 @@ __device__ void residual2(const KernelParams& p, int c, ResStage<V>* st, bool an
     issue(j + D - 2);
     const TileTask& tk = task(j);
     if (!mine(tk.b)) continue;  // uniform over the CTA
-    const ProblemDesc& P = p.probs[tk.b];
+    const ProblemDesc& P = prob_at(p, tk.b);
     const ResSrc<V> src = source(tk.b);
     ResStage<V>& S = st[j % D];
     const int N = level_side(P.n, 0);
@@ -913,7 +938,7 @@ __device__ void residual2(const KernelParams& p, int c, ResStage<V>* st, bool an
     }
     if (src.s) res_plane<V, true>(S, b0, 0, uc, sc, cls);
     else res_plane<V, false>(S, b0, 0, uc, sc, cls);
-    const V c0v = (V)(p.kappa / (2.0 * P.h * P.h) * (src.s ? 1.0 : 2.0));
+    const V c0v = (V)(P.c0 * (src.s ? 1.0 : 2.0));
     const double scale = cast_scale(p, tk.b, c);
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
@@ -937,8 +962,8 @@ __device__ void phase_outer(const KernelParams& p, int c, unsigned char* smem) {
     return;
   }
   for_tasks(p, 0, [&](const TileTask& tk) {
-    if (p.accum[tk.b].done) return;
-    const ProblemDesc& P = p.probs[tk.b];
+    if (done_at(p, tk.b)) return;
+    const ProblemDesc& P = prob_at(p, tk.b);
     if (use_anchor<T>(p, tk.b, c)) {
       const ResSrc<double> src = anchor_src(p, P);
       if (P.hetero) residual3<T, double, true>(p, tk, c, (ResStage<double>*)smem, src);
@@ -975,6 +1000,7 @@ __device__ void phase_check(const KernelParams& p, int c) {
       S.grow = 0;
     }
     S.scale_used[c & 1] = cast_scale(p, b, c);
+    S.inv_scale[c & 1] = 1.0 / S.scale_used[c & 1];
     const double rel = S.fnorm > 0.0 ? rmax / S.fnorm : 0.0;
     const double rel2 = S.fnorm2 > 0.0 ? sqrt(rs2) / S.fnorm2 : 0.0;
     S.rel = rel;
@@ -1047,11 +1073,11 @@ struct SweepCtl {
 
 __device__ __forceinline__ SweepCtl sweep_ctl(const KernelParams& p, const Phase& ph, int b) {
   SweepCtl s;
-  const ProblemDesc& P = p.probs[b];
+  const ProblemDesc& P = prob_at(p, b);
   const bool final_visit = (ph.flags & kFinalVisit) != 0;
   const int k_b = visit_sweeps(p.n_r, P.n, ph.tooth, final_visit);
   const int span = (ph.flags & kPair) ? 2 : 1;  // sweeps this phase performs
-  s.active = !p.accum[b].done && ph.tooth <= P.n - 1 && ph.sweep + span - 1 < k_b;
+  s.active = !done_at(p, b) && ph.tooth <= P.n - 1 && ph.sweep + span - 1 < k_b;
   s.zero_in = ph.sweep == 0 && (ph.flags & kFirstOfTooth) && ph.tooth == P.n - 1;
   s.last = final_visit && ph.sweep + span - 1 == k_b - 1;
   s.N = level_side(P.n, ph.level);
@@ -1090,7 +1116,8 @@ __device__ __forceinline__ void plane_sums2(const SweepStage<T>& S, int b0, bool
   }
 }
 
-// Per-task constants of the update: 1 - omega, 1 / c = 2 H^2 / kappa, and q for a homogeneous problem.
+// Per-task constants of the update: 1 - omega, 1 / c = 2 H^2 / kappa, and q for a homogeneous problem
+// (precomputed per level on the host: an FP64 division per tile costs the FP64 pipe ~1 us per phase).
 template <typename T>
 struct SweepConst {
   T one_m_omega, inv_c, q_const, w_e, w_c;
@@ -1099,9 +1126,8 @@ struct SweepConst {
 template <typename T>
 __device__ __forceinline__ SweepConst<T> sweep_const(const KernelParams& p, const ProblemDesc& P, int l) {
   SweepConst<T> k;
-  const double H = P.h * (double)(1 << l);
   k.one_m_omega = (T)(1.0 - p.omega);
-  k.inv_c = (T)(2.0 * H * H / p.kappa);
+  k.inv_c = (T)P.inv_c[l];
   k.q_const = (T)P.q_const[l];
   k.w_e = (T)p.w_edge;
   k.w_c = (T)p.w_corner;
@@ -1120,7 +1146,7 @@ template <typename T, bool HET, bool LAST, bool DIAG = false>
 __device__ void sweep3(const KernelParams& p, const Phase& ph, int c, const TileTask& tk, SweepStage<T>* st,
                        const SweepCtl& sc) {
   constexpr int D = kSweepStages;
-  const ProblemDesc& P = p.probs[tk.b];
+  const ProblemDesc& P = prob_at(p, tk.b);
   const int N = sc.N;
   const int tid = threadIdx.x;
   const Columns cl = own_columns(P, N, tk.x0, tk.y0);
@@ -1134,7 +1160,7 @@ __device__ void sweep3(const KernelParams& p, const Phase& ph, int c, const Tile
   const HaloCells hc = halo_cells(P, N, tk.x0, tk.y0, false);
   const SweepConst<T> kc = sweep_const<T>(p, P, ph.level);
   const int b0 = (2 * (tid / kTX)) * kHX + (tid % kTX);
-  const double inv_scale = LAST ? 1.0 / p.state[tk.b].scale_used[c & 1] : 0.0;
+  const double inv_scale = LAST ? p.state[tk.b].inv_scale[c & 1] : 0.0;
   const bool keep = !LAST || p.mixed;
   const bool zero_in = sc.zero_in;
   const int nplanes = tk.nz + 2;
@@ -1164,7 +1190,9 @@ __device__ void sweep3(const KernelParams& p, const Phase& ph, int c, const Tile
     }
     cp_async_commit();
   };
-  for (int k = 0; k < D - 2; ++k) issue(k);
+  // A piece of one plane (the coarse levels' usual share) fetches its three planes in one round trip.
+  const int pre = nplanes <= D - 1 ? nplanes : D - 2;
+  for (int k = 0; k < pre; ++k) issue(k);
   double dmx = 0.0;  // diagnostic pseudo-residual of the thread's nodes (DIAG)
   // One plane step: wait for plane k, start plane k + D - 2, form its in-plane sums into `nw`,
   // update the nodes of plane k - 1 from (m, o, nw).  The z loop is unrolled by three so that the
@@ -1172,7 +1200,8 @@ __device__ void sweep3(const KernelParams& p, const Phase& ph, int c, const Tile
   auto step = [&](int k, const PlaneSums<T>* m, const PlaneSums<T>* o, PlaneSums<T>* nw) {
     cp_async_wait<D - 3>();
     __syncthreads();
-    issue(k + D - 2);
+    if (k + D - 2 >= pre) issue(k + D - 2);
+    else cp_async_commit();
     plane_sums2<T, HET>(st[k % D], b0, zero_in, nw);
     if (k >= 2) {
       const int z = tk.z0 + k - 2;
@@ -1224,7 +1253,7 @@ __device__ void sweep2(const KernelParams& p, const Phase& ph, int c, SweepStage
       const TileTask& tk = task(j);
       const SweepCtl sc = sweep_ctl(p, ph, tk.b);
       if (mine(sc)) {
-        const ProblemDesc& P = p.probs[tk.b];
+        const ProblemDesc& P = prob_at(p, tk.b);
         const int N = sc.N;
         const HaloCells hc = halo_cells(P, N, tk.x0, tk.y0, false);
         const Columns cl = own_columns(P, N, tk.x0, tk.y0);
@@ -1256,7 +1285,7 @@ __device__ void sweep2(const KernelParams& p, const Phase& ph, int c, SweepStage
     const SweepCtl sc = sweep_ctl(p, ph, tk.b);
     if (!mine(sc)) continue;
     double dmx = 0.0;
-    const ProblemDesc& P = p.probs[tk.b];
+    const ProblemDesc& P = prob_at(p, tk.b);
     const int N = sc.N;
     const Columns cl = own_columns(P, N, tk.x0, tk.y0);
     const SweepStage<T>& S = st[j % D];
@@ -1265,7 +1294,7 @@ __device__ void sweep2(const KernelParams& p, const Phase& ph, int c, SweepStage
     if (P.hetero) plane_sums2<T, true>(S, b0, sc.zero_in, ps);
     else plane_sums2<T, false>(S, b0, sc.zero_in, ps);
     T* dst = sweep_parity(p, l, ph.sweep) ? (T*)p.E + sc.off : (T*)p.E2 + sc.off;
-    const double inv_scale = LAST ? 1.0 / p.state[tk.b].scale_used[c & 1] : 0.0;
+    const double inv_scale = LAST ? p.state[tk.b].inv_scale[c & 1] : 0.0;
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
       if (!cl.in[r] || cl.fixed_xy[r]) continue;
@@ -1406,7 +1435,7 @@ template <typename T, bool HET, bool LAST>
 __device__ void sweep3_pair(const KernelParams& p, const Phase& ph, int c, const TileTask& tk, PairStage<T>* st,
                             T* ebuf, const SweepCtl& sc) {
   constexpr int D = kPairStages;
-  const ProblemDesc& P = p.probs[tk.b];
+  const ProblemDesc& P = prob_at(p, tk.b);
   const int N = sc.N;
   const int tid = threadIdx.x;
   const Columns cl = own_columns(P, N, tk.x0, tk.y0);
@@ -1420,7 +1449,7 @@ __device__ void sweep3_pair(const KernelParams& p, const Phase& ph, int c, const
   const PairCells pc = pair_cells(N, tk.x0, tk.y0);
   const PairUnits pu = pair_units(P, N, tk.x0, tk.y0);
   const SweepConst<T> kc = sweep_const<T>(p, P, ph.level);
-  const double inv_scale = LAST ? 1.0 / p.state[tk.b].scale_used[c & 1] : 0.0;
+  const double inv_scale = LAST ? p.state[tk.b].inv_scale[c & 1] : 0.0;
   const bool zero_in = sc.zero_in;
   const int nplanes = tk.nz + 4;
   const unsigned NN = (unsigned)N * (unsigned)N;
@@ -1623,7 +1652,7 @@ template <typename T, bool HET, bool LAST>
 __device__ void sweep3q(const KernelParams& p, const Phase& ph, int c, const TileTask& tk, QuadStage<T>* st,
                         const SweepCtl& sc) {
   constexpr int D = kSweepStages;
-  const ProblemDesc& P = p.probs[tk.b];
+  const ProblemDesc& P = prob_at(p, tk.b);
   const int N = sc.N;
   const int tid = threadIdx.x;
   const Columns4 cl = own_columns4(P, N, tk.x0, tk.y0);
@@ -1638,7 +1667,7 @@ __device__ void sweep3q(const KernelParams& p, const Phase& ph, int c, const Til
   halo_cells4(N, tk.x0, tk.y0, hoff);
   const SweepConst<T> kc = sweep_const<T>(p, P, ph.level);
   const int b0 = (4 * (tid / kTX)) * kHX + (tid % kTX);  // top-left of the thread's 6 x 3 block
-  const double inv_scale = LAST ? 1.0 / p.state[tk.b].scale_used[c & 1] : 0.0;
+  const double inv_scale = LAST ? p.state[tk.b].inv_scale[c & 1] : 0.0;
   const bool keep = !LAST || p.mixed;
   const bool zero_in = sc.zero_in;
   const int nplanes = tk.nz + 2;
@@ -1787,7 +1816,7 @@ __device__ void phase_sweep(const KernelParams& p, const Phase& ph, int c, unsig
       for_tasks4(p, ph.level, [&](const TileTask& tk) {
         const SweepCtl sc = sweep_ctl(p, ph, tk.b);
         if (!sc.active) return;
-        const bool het = p.probs[tk.b].hetero != 0;
+        const bool het = prob_at(p, tk.b).hetero != 0;
         if (sc.last) {
           if (het) sweep3q<T, true, true>(p, ph, c, tk, qst, sc);
           else sweep3q<T, false, true>(p, ph, c, tk, qst, sc);
@@ -1802,7 +1831,7 @@ __device__ void phase_sweep(const KernelParams& p, const Phase& ph, int c, unsig
   for_tasks(p, ph.level, [&](const TileTask& tk) {
     const SweepCtl sc = sweep_ctl(p, ph, tk.b);
     if (!sc.active) return;
-    const bool het = p.probs[tk.b].hetero != 0;
+    const bool het = prob_at(p, tk.b).hetero != 0;
     if constexpr (sizeof(T) == 4) {
       if (ph.flags & kPair) {
         PairStage<T>* pst = (PairStage<T>*)smem;
@@ -1847,7 +1876,7 @@ __device__ void phase_restrict(const KernelParams& p, int l) {
   T* R = (T*)p.R;
   const int lane = threadIdx.x & 31;
   for_rows<DIM>(p, l, [&](int b, const ProblemDesc& P, int N, int y, int z) {
-    if (l > P.n - 1 || p.accum[b].done) return;
+    if (l > P.n - 1 || done_at(p, b)) return;
     const int Ns = level_side(P.n, l - 1);
     const T* src = R + P.off_lvl[l - 1];
     T* dst = R + P.off_lvl[l] + ((long long)z * N + y) * N;
@@ -1908,7 +1937,7 @@ __device__ void prolong3(const KernelParams& p, const Phase& ph, const TileTask&
   constexpr int D = kProlongStages;
   const int l = ph.level;
   const bool init = (ph.flags & kInit) != 0;
-  const ProblemDesc& P = p.probs[tk.b];
+  const ProblemDesc& P = prob_at(p, tk.b);
   const int N = level_side(P.n, l), Nc = level_side(P.n, l + 1);
   const long long NN = (long long)N * N, NNc = (long long)Nc * Nc;
   const T* src = visit_result<T>(p, P, ph.tooth, l + 1);
@@ -1997,7 +2026,7 @@ __device__ void phase_prolong_rows(const KernelParams& p, const Phase& ph) {
   const bool init = (ph.flags & kInit) != 0;
   const int lane = threadIdx.x & 31;
   for_rows<DIM>(p, l, [&](int b, const ProblemDesc& P, int N, int y, int z) {
-    if (ph.tooth > P.n - 1 || p.accum[b].done) return;
+    if (ph.tooth > P.n - 1 || done_at(p, b)) return;
     const int Nc = level_side(P.n, l + 1);
     const T* src = visit_result<T>(p, P, ph.tooth, l + 1);
     const T* Bc = (const T*)p.B + P.off_lvl[l + 1];
@@ -2029,7 +2058,7 @@ template <typename T, int DIM>
 __device__ void phase_prolong(const KernelParams& p, const Phase& ph, unsigned char* smem) {
   if (DIM == 3) {
     for_tasks(p, ph.level, [&](const TileTask& tk) {
-      if (ph.tooth > p.probs[tk.b].n - 1 || p.accum[tk.b].done) return;
+      if (ph.tooth > prob_at(p, tk.b).n - 1 || done_at(p, tk.b)) return;
       prolong3<T>(p, ph, tk, (ProlongStage<T>*)smem);
     });
     return;
@@ -2043,7 +2072,7 @@ __device__ void phase_inject(const KernelParams& p, const Phase& ph) {
   const int l = ph.level;
   const int lane = threadIdx.x & 31;
   for_rows<DIM>(p, l, [&](int b, const ProblemDesc& P, int N, int y, int z) {
-    if (ph.tooth > P.n - 1 || l > P.n - 1 || p.accum[b].done) return;
+    if (ph.tooth > P.n - 1 || l > P.n - 1 || done_at(p, b)) return;
     const int Nf = level_side(P.n, l - 1);
     const T* src = visit_result<T>(p, P, ph.tooth, l - 1) + ((long long)(2 * z) * Nf + 2 * y) * Nf;
     const long long row = ((long long)z * N + y) * N;
@@ -2068,7 +2097,7 @@ template <int DIM>
 __device__ void phase_mean_rows(const KernelParams& p) {
   const int lane = threadIdx.x & 31;
   for_rows<DIM>(p, 0, [&](int b, const ProblemDesc& P, int N, int y, int z) {
-    if (!P.project_mean || p.accum[b].done) return;
+    if (!P.project_mean || done_at(p, b)) return;
     const double* u = p.U + P.off_full + ((long long)z * N + y) * N;
     double s = 0.0;
     for (int x = lane; x < N; x += 32) s += (x == 0 || x == N - 1) ? 0.5 * u[x] : u[x];
@@ -2087,8 +2116,8 @@ __device__ void phase_mean_rows(const KernelParams& p) {
 __device__ void phase_mean_reduce(const KernelParams& p, int dim, unsigned char* smem) {
   double* s_part = (double*)smem;
   for (int b = blockIdx.x; b < p.batch; b += gridDim.x) {
-    const ProblemDesc& P = p.probs[b];
-    if (!P.project_mean || p.accum[b].done) continue;
+    const ProblemDesc& P = prob_at(p, b);
+    if (!P.project_mean || done_at(p, b)) continue;
     const long long r0 = p.row_prefix[b], rows = p.row_prefix[b + 1] - r0;
     const long long chunk = (rows + kThreads - 1) / kThreads;
     double s = 0.0;
@@ -2111,7 +2140,7 @@ template <int DIM>
 __device__ void phase_mean_apply(const KernelParams& p) {
   const int lane = threadIdx.x & 31;
   for_rows<DIM>(p, 0, [&](int b, const ProblemDesc& P, int N, int y, int z) {
-    if (!P.project_mean || p.accum[b].done) return;
+    if (!P.project_mean || done_at(p, b)) return;
     double* u = p.U + P.off_full + ((long long)z * N + y) * N;
     const double m = p.umean[b];
     for (int x = lane; x < N; x += 32) u[x] -= m;
@@ -2138,6 +2167,7 @@ template <typename T, int DIM>
 __global__ void __launch_bounds__(kThreads, SGML_MIN_CTAS) cycle_kernel(const KernelParams p) {
   extern __shared__ __align__(16) unsigned char sm[];
   load_tables(p);
+  load_done(p);
   if (p.fresh) {
     phase_lift<T, DIM>(p);
     if (!grid_sync(p.sync, p.timeout_ns)) return;
@@ -2156,6 +2186,7 @@ __global__ void __launch_bounds__(kThreads, SGML_MIN_CTAS) cycle_kernel(const Ke
     if (!grid_sync(p.sync, p.timeout_ns)) return;
     stamp(c, 2);
     if (!ld_volatile(&p.sync->active[c & 1])) break;
+    load_done(p);
     for (int q = 0; q < p.nphases; ++q) {
       const Phase ph = phase_at(p, q);
       run_phase<T, DIM>(p, ph, c, sm);
@@ -2171,6 +2202,7 @@ template <typename T, int DIM>
 __global__ void __launch_bounds__(kThreads, SGML_MIN_CTAS) phase_kernel(const KernelParams p, int which, int c) {
   extern __shared__ __align__(16) unsigned char sm[];
   load_tables(p);
+  load_done(p);
   if (which == -3) {
     phase_lift<T, DIM>(p);
   } else if (which == -2) {

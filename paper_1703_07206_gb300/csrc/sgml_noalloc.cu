@@ -203,10 +203,12 @@ extern "C" int sgml_solve_noalloc(int dim, int n, int precision, const double* f
   const double theta = 0.7;
   const double kap = kappa(dim);
   const double tg = theta * (kappa(dim) * weight_sum(dim) / 2.0);
+  P.c0 = kap / (2.0 * P.h * P.h);
   for (int l = 0; l <= n - 1; ++l) {
     const double H = P.h * (double)(1LL << l);
     const double c = kap / (2.0 * H * H);
     P.q_const[l] = tg / (c * 2.0 * weight_sum(dim) - a_scalar) * c;
+    P.inv_c[l] = 2.0 * H * H / kap;
   }
 
   // ---- uploads and clears (stream-ordered, no allocation) ---------------------------------
