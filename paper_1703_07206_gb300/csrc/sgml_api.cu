@@ -305,6 +305,13 @@ static int ensure_hetero_pools(sgml_grid* g, bool need_a) {
   return SGML_OK;
 }
 
+// FP32 copies of the per-level constants (the kernels of the mixed form read them directly).
+static void fill_float_copies(ProblemDesc& P) {
+  for (int l = 0; l < kMaxLevels; ++l) P.inv_c_f[l] = (float)P.inv_c[l], P.q_const_f[l] = (float)P.q_const[l];
+  P.c0_f = (float)P.c0;
+  P.a_scalar_f = (float)P.a_scalar;
+}
+
 // Coefficient pyramid: restricted sigma / a and the local steps of every level (setup, excluded
 // from the solve).  Homogeneous problems get one constant per level computed here.
 static int build_coeffs(sgml_grid* g) {
@@ -322,6 +329,7 @@ static int build_coeffs(sgml_grid* g) {
       const double D = c * 2.0 * weight_sum(g->dim) - P.a_scalar;
       P.q_const[l] = tg / D * c;
     }
+    fill_float_copies(P);
     if (!P.hetero) continue;
     // level pyramid of sigma (and a) in FP64 temporaries
     std::vector<double*> sig(P.n, nullptr), av(P.n, nullptr);
@@ -455,6 +463,9 @@ static int launch(sgml_grid* g, int max_cycles, double tol) {
   p.w_edge = w_edge();
   p.w_corner = w_corner();
   p.omega = g->theta * jacobi_gain(g->dim);
+  p.w_edge_f = (float)p.w_edge;
+  p.w_corner_f = (float)p.w_corner;
+  p.one_m_omega_f = (float)(1.0 - p.omega);
   p.n_r = g->n_r;
   p.pair_levels = effective_pair_levels(g);
   p.sync = g->d_sync;

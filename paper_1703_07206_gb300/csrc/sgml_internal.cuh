@@ -59,6 +59,9 @@ struct ProblemDesc {
   double q_const[kMaxLevels];      // homogeneous problems: delta_tau * kappa / (2 H^2) per level
   double inv_c[kMaxLevels];        // 2 H^2 / kappa per level (the sweep's 1 / c)
   double c0;                       // kappa / (2 h^2) (the level-0 residual's factor)
+  float inv_c_f[kMaxLevels];       // FP32 copies of inv_c, q_const, c0 and a_scalar (made on the host:
+  float q_const_f[kMaxLevels];     //   a conversion per thread and tile would occupy the FP64 pipe)
+  float c0_f, a_scalar_f;
   int project_mean;                // every face Neumann, a >= 0 constant: Eq. 10, zero-mean u
 };
 
@@ -69,6 +72,9 @@ struct ProblemState {
   double rmax_prev;       // max-norm of the latest residual (sets the next cast scale)
   double scale_used[2];   // scale of the residual cast in cycle c (slot c & 1)
   double inv_scale[2];    // 1 / scale_used (no FP64 division per tile)
+  double next_scale;      // cast scale of the next cycle's residual (set by the check)
+  float next_scale_f;     // FP32 copies of next_scale and inv_scale
+  float inv_scale_f[2];
   double rel, rel_l2;     // latest relative residuals
   double rel_prev;
   int cycles;             // cycles completed since the last reset
@@ -128,6 +134,7 @@ struct KernelParams {
   double kappa;                  // stencil constant (consistent or literal)
   double w_edge, w_corner;       // 1/sqrt(2), 1/sqrt(3)
   double omega;                  // delta_tau * D_i of the Jacobi-scaled step
+  float w_edge_f, w_corner_f, one_m_omega_f;  // FP32 copies of w_edge, w_corner and 1 - omega
   int n_r;
   int pair_levels;               // levels 0 .. pair_levels - 1 run their sweeps in fused pairs (kPair)
   GridSync* sync;

@@ -208,10 +208,42 @@ __device__ __forceinline__ bool done_at(const KernelParams& p, int b) {
   return b < kDoneCache ? s_done[b] != 0 : p.accum[b].done != 0;
 }
 
+// Problem 0's cast scales for the current cycle (set by the check), cached with the stop flags.
+struct Scales {
+  double next, inv[2];
+  float next_f, inv_f[2];
+};
+__shared__ Scales s_scales0;
+
 __device__ void load_done(const KernelParams& p) {
   for (int b = threadIdx.x; b < p.batch && b < kDoneCache; b += blockDim.x)
     s_done[b] = (unsigned char)(ld_volatile(&p.accum[b].done) != 0);
+  if (threadIdx.x == 0) {
+    const volatile ProblemState& S = p.state[0];
+    s_scales0.next = S.next_scale;
+    s_scales0.inv[0] = S.inv_scale[0];
+    s_scales0.inv[1] = S.inv_scale[1];
+    s_scales0.next_f = S.next_scale_f;
+    s_scales0.inv_f[0] = S.inv_scale_f[0];
+    s_scales0.inv_f[1] = S.inv_scale_f[1];
+  }
   __syncthreads();
+}
+
+// A launch constant in the arithmetic type V: the double, or the FP32 copy the host or the check
+// made of it.  (A conversion per thread and tile occupies GB300's FP64 pipe for ~1 us a phase.)
+template <typename V>
+__device__ __forceinline__ V cv(double d, float f) {
+  if constexpr (sizeof(V) == 4) return f;
+  else return (V)d;
+}
+
+// 1 / s of cycle c's residual cast (slot c & 1), double and float.
+__device__ __forceinline__ double inv_scale_at(const KernelParams& p, int b, int slot) {
+  return b == 0 ? s_scales0.inv[slot] : p.state[b].inv_scale[slot];
+}
+__device__ __forceinline__ float inv_scale_f_at(const KernelParams& p, int b, int slot) {
+  return b == 0 ? s_scales0.inv_f[slot] : p.state[b].inv_scale_f[slot];
 }
 
 __device__ void load_tables(const KernelParams& p) {
@@ -300,6 +332,10 @@ __device__ __forceinline__ HaloCells halo_cells(const ProblemDesc& P, int N, int
     hc.ghost[s] = 0.0;
     if (k < kHalo) {
       int gx = x0 - 1 + k % kHX, gy = y0 - 1 + k / kHX;
+      // cells past the image of the far edge (a tile overhanging a small level) are never read by
+      // a node of the level: no copy is issued for them (their shared-memory slots keep stale
+      // values, used only by threads that own no node)
+      if (gx > N || gy > N) continue;
       double g = 0.0;
       if (flux) {
         if (gx < 0 && P.face_type[0] == 1) g += 2.0 * P.h * P.face_value[0];
@@ -307,7 +343,6 @@ __device__ __forceinline__ HaloCells halo_cells(const ProblemDesc& P, int N, int
         if (gy < 0 && P.face_type[2] == 1) g += 2.0 * P.h * P.face_value[2];
         if (gy > N - 1 && P.face_type[3] == 1) g += 2.0 * P.h * P.face_value[3];
       }
-      // cells beyond the image of the far edge (tile overhang past N) are clamped: never used
       gx = refl(gx, N);
       gy = refl(gy, N);
       gx = gx < 0 ? 0 : (gx > N - 1 ? N - 1 : gx);
@@ -502,6 +537,17 @@ __device__ __forceinline__ double cast_scale(const KernelParams& p, int b, int c
   return (ref > 0.0 && ref < 1e300) ? 1.0 / ref : 1.0;
 }
 
+// The cast scale of cycle c's residual: computed here for the first cycle of a fresh launch, else
+// the value the previous cycle's check stored (no FP64 division per tile).
+__device__ __forceinline__ double outer_scale(const KernelParams& p, int b, int c) {
+  if (c == 0 && p.fresh) return cast_scale(p, b, c);
+  return b == 0 ? s_scales0.next : p.state[b].next_scale;
+}
+__device__ __forceinline__ float outer_scale_f(const KernelParams& p, int b, int c) {
+  if (c == 0 && p.fresh) return (float)cast_scale(p, b, c);
+  return b == 0 ? s_scales0.next_f : p.state[b].next_scale_f;
+}
+
 // ---------------------------------------------------------------------------------------------
 // Residual phases.  Anchor (FP64, Sec. 2's recurrence restarted from the accumulated solution):
 // r = f - delta L_0 u.  Recurrence (mixed form, the paper's r_i = r_{i-1} - delta L(e_{i-1})):
@@ -620,15 +666,15 @@ __device__ void residual3(const KernelParams& p, const TileTask& tk, int c, ResS
   const int N = level_side(P.n, 0);
   const int tid = threadIdx.x;
   const Columns cl = own_columns(P, N, tk.x0, tk.y0);
-  const double scale = cast_scale(p, tk.b, c);
-  const float scale32 = (float)scale;
+  const double scale = outer_scale(p, tk.b, c);
+  const float scale32 = outer_scale_f(p, tk.b, c);
   T* R0 = (T*)p.R + P.off_lvl[0];
   float2* RES = p.RESP ? p.RESP + P.off_full : nullptr;
   const bool flux = src.images && tile_has_flux(P, N, tk.x0, tk.y0, 3);
   const HaloCells hc = halo_cells(P, N, tk.x0, tk.y0, flux);
-  const V c0v = (V)(P.c0 * (HET ? 1.0 : 2.0));
-  const V a_s = (V)src.a_scalar;
-  const V w_e = (V)p.w_edge, w_c = (V)p.w_corner;
+  const V c0v = cv<V>(P.c0 * (HET ? 1.0 : 2.0), P.c0_f * (HET ? 1.0f : 2.0f));
+  const V a_s = cv<V>(src.a_scalar, P.a_scalar_f);
+  const V w_e = cv<V>(p.w_edge, p.w_edge_f), w_c = cv<V>(p.w_corner, p.w_corner_f);
   const int b0 = (2 * (tid / kTX)) * kHX + (tid % kTX);  // top-left of the thread's 4 x 3 block
   const int nplanes = tk.nz + 2;
   const long long NN = (long long)N * N;
@@ -729,14 +775,14 @@ __device__ void residual3r(const KernelParams& p, const TileTask& tk, int c, Res
   const int N = level_side(P.n, 0);
   const int tid = threadIdx.x;
   const Columns cl = own_columns(P, N, tk.x0, tk.y0);
-  const double scale = cast_scale(p, tk.b, c);
-  const float scale32 = (float)scale;
+  const double scale = outer_scale(p, tk.b, c);
+  const float scale32 = outer_scale_f(p, tk.b, c);
   T* R0 = (T*)p.R + P.off_lvl[0];
   float2* RES = p.RESP + P.off_full;
   const HaloCells hc = halo_cells(P, N, tk.x0, tk.y0, false);
-  const V c0v = (V)(P.c0 * (HET ? 1.0 : 2.0));
-  const V a_s = (V)src.a_scalar;
-  const V w_e = (V)p.w_edge, w_c = (V)p.w_corner;
+  const V c0v = cv<V>(P.c0 * (HET ? 1.0 : 2.0), P.c0_f * (HET ? 1.0f : 2.0f));
+  const V a_s = cv<V>(src.a_scalar, P.a_scalar_f);
+  const V w_e = cv<V>(p.w_edge, p.w_edge_f), w_c = cv<V>(p.w_corner, p.w_corner_f);
   const int b0 = (2 * (tid / kTX)) * kHX + (tid % kTX);
   const int nplanes = tk.nz + 2;
   const long long NN = (long long)N * N;
@@ -863,8 +909,8 @@ __device__ __forceinline__ ResSrc<T> recur_src(const KernelParams& p, const Prob
   s.rhs = reinterpret_cast<const double*>(p.RESP + P.off_full);
   s.a = P.a_per_node ? (const T*)p.A0 + P.off_lvl[0] : nullptr;
   s.a_scalar = P.a_scalar;
-  s.opscale = p.state[b].inv_scale[(c - 1) & 1];
-  s.opscale32 = (float)s.opscale;
+  s.opscale = inv_scale_at(p, b, (c - 1) & 1);
+  s.opscale32 = inv_scale_f_at(p, b, (c - 1) & 1);
   s.images = false;
   return s;
 }
@@ -938,14 +984,15 @@ __device__ void residual2(const KernelParams& p, int c, ResStage<V>* st, bool an
     }
     if (src.s) res_plane<V, true>(S, b0, 0, uc, sc, cls);
     else res_plane<V, false>(S, b0, 0, uc, sc, cls);
-    const V c0v = (V)(P.c0 * (src.s ? 1.0 : 2.0));
-    const double scale = cast_scale(p, tk.b, c);
+    const V c0v = cv<V>(P.c0 * (src.s ? 1.0 : 2.0), P.c0_f * (src.s ? 1.0f : 2.0f));
+    const double scale = outer_scale(p, tk.b, c);
+    const float scale32 = outer_scale_f(p, tk.b, c);
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
       if (!cl.in[r] || cl.fixed_xy[r]) continue;
-      const V sum = rn_fma((V)p.w_edge, cls[r][1], cls[r][0]);
-      const V a = src.a ? S.a[tid + r * kThreads] : (V)src.a_scalar;
-      res_finish<T, V>(src, c0v, sum, uc[r], a, S.f[tid + r * kThreads], scale, (float)scale,
+      const V sum = rn_fma(cv<V>(p.w_edge, p.w_edge_f), cls[r][1], cls[r][0]);
+      const V a = src.a ? S.a[tid + r * kThreads] : cv<V>(src.a_scalar, P.a_scalar_f);
+      res_finish<T, V>(src, c0v, sum, uc[r], a, S.f[tid + r * kThreads], scale, scale32,
                        (T*)p.R + P.off_lvl[0], p.RESP ? p.RESP + P.off_full : nullptr, cl.off[r], mx, s2);
     }
     block_flush((double)mx, (double)s2, &p.accum[tk.b].rmax_bits[c & 1], &p.accum[tk.b].rsum2[c & 1]);
@@ -1001,6 +1048,7 @@ __device__ void phase_check(const KernelParams& p, int c) {
     }
     S.scale_used[c & 1] = cast_scale(p, b, c);
     S.inv_scale[c & 1] = 1.0 / S.scale_used[c & 1];
+    S.inv_scale_f[c & 1] = (float)S.inv_scale[c & 1];
     const double rel = S.fnorm > 0.0 ? rmax / S.fnorm : 0.0;
     const double rel2 = S.fnorm2 > 0.0 ? sqrt(rs2) / S.fnorm2 : 0.0;
     S.rel = rel;
@@ -1013,6 +1061,8 @@ __device__ void phase_check(const KernelParams& p, int c) {
     S.grow = (rel > S.rel_prev) ? S.grow + 1 : 0;
     S.rel_prev = rel;
     S.rmax_prev = rmax;
+    S.next_scale = cast_scale(p, b, c + 1);
+    S.next_scale_f = (float)S.next_scale;
     if (anchored) {
       S.anchor_rel = rel;
       S.last_anchor = c;
@@ -1126,11 +1176,11 @@ struct SweepConst {
 template <typename T>
 __device__ __forceinline__ SweepConst<T> sweep_const(const KernelParams& p, const ProblemDesc& P, int l) {
   SweepConst<T> k;
-  k.one_m_omega = (T)(1.0 - p.omega);
-  k.inv_c = (T)P.inv_c[l];
-  k.q_const = (T)P.q_const[l];
-  k.w_e = (T)p.w_edge;
-  k.w_c = (T)p.w_corner;
+  k.one_m_omega = cv<T>(1.0 - p.omega, p.one_m_omega_f);
+  k.inv_c = cv<T>(P.inv_c[l], P.inv_c_f[l]);
+  k.q_const = cv<T>(P.q_const[l], P.q_const_f[l]);
+  k.w_e = cv<T>(p.w_edge, p.w_edge_f);
+  k.w_c = cv<T>(p.w_corner, p.w_corner_f);
   return k;
 }
 
@@ -1160,7 +1210,7 @@ __device__ void sweep3(const KernelParams& p, const Phase& ph, int c, const Tile
   const HaloCells hc = halo_cells(P, N, tk.x0, tk.y0, false);
   const SweepConst<T> kc = sweep_const<T>(p, P, ph.level);
   const int b0 = (2 * (tid / kTX)) * kHX + (tid % kTX);
-  const double inv_scale = LAST ? p.state[tk.b].inv_scale[c & 1] : 0.0;
+  const double inv_scale = LAST ? inv_scale_at(p, tk.b, c & 1) : 0.0;
   const bool keep = !LAST || p.mixed;
   const bool zero_in = sc.zero_in;
   const int nplanes = tk.nz + 2;
@@ -1294,7 +1344,7 @@ __device__ void sweep2(const KernelParams& p, const Phase& ph, int c, SweepStage
     if (P.hetero) plane_sums2<T, true>(S, b0, sc.zero_in, ps);
     else plane_sums2<T, false>(S, b0, sc.zero_in, ps);
     T* dst = sweep_parity(p, l, ph.sweep) ? (T*)p.E + sc.off : (T*)p.E2 + sc.off;
-    const double inv_scale = LAST ? p.state[tk.b].inv_scale[c & 1] : 0.0;
+    const double inv_scale = LAST ? inv_scale_at(p, tk.b, c & 1) : 0.0;
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
       if (!cl.in[r] || cl.fixed_xy[r]) continue;
@@ -1449,7 +1499,7 @@ __device__ void sweep3_pair(const KernelParams& p, const Phase& ph, int c, const
   const PairCells pc = pair_cells(N, tk.x0, tk.y0);
   const PairUnits pu = pair_units(P, N, tk.x0, tk.y0);
   const SweepConst<T> kc = sweep_const<T>(p, P, ph.level);
-  const double inv_scale = LAST ? p.state[tk.b].inv_scale[c & 1] : 0.0;
+  const double inv_scale = LAST ? inv_scale_at(p, tk.b, c & 1) : 0.0;
   const bool zero_in = sc.zero_in;
   const int nplanes = tk.nz + 4;
   const unsigned NN = (unsigned)N * (unsigned)N;
@@ -1667,7 +1717,7 @@ __device__ void sweep3q(const KernelParams& p, const Phase& ph, int c, const Til
   halo_cells4(N, tk.x0, tk.y0, hoff);
   const SweepConst<T> kc = sweep_const<T>(p, P, ph.level);
   const int b0 = (4 * (tid / kTX)) * kHX + (tid % kTX);  // top-left of the thread's 6 x 3 block
-  const double inv_scale = LAST ? p.state[tk.b].inv_scale[c & 1] : 0.0;
+  const double inv_scale = LAST ? inv_scale_at(p, tk.b, c & 1) : 0.0;
   const bool keep = !LAST || p.mixed;
   const bool zero_in = sc.zero_in;
   const int nplanes = tk.nz + 2;
@@ -1947,9 +1997,10 @@ __device__ void prolong3(const KernelParams& p, const Phase& ph, const TileTask&
   const int tid = threadIdx.x, tx = tid % kTX, ty = tid / kTX;
   const Columns cl = own_columns(P, N, tk.x0, tk.y0);
   const int cx0 = tk.x0 >> 1, cy0 = tk.y0 >> 1;
-  // coarse footprint cells this thread loads (at most one: kCoarse <= kThreads), clamped inside
+  // coarse footprint cells this thread loads (at most one: kCoarse <= kThreads); cells past the
+  // level's far edge (a tile overhanging a small level) are read by no node and not loaded
   const int cell_x = tid % kCX, cell_y = tid / kCX;
-  const bool has_cell = tid < kCoarse;
+  const bool has_cell = tid < kCoarse && cx0 + cell_x <= Nc - 1 && cy0 + cell_y <= Nc - 1;
   const int coff = min(cy0 + cell_y, Nc - 1) * Nc + min(cx0 + cell_x, Nc - 1);
   // interpolation weights of the thread's column (x) and its two rows (y even, y odd)
   const int x = tk.x0 + tx;

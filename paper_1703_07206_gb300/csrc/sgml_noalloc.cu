@@ -210,6 +210,9 @@ extern "C" int sgml_solve_noalloc(int dim, int n, int precision, const double* f
     P.q_const[l] = tg / (c * 2.0 * weight_sum(dim) - a_scalar) * c;
     P.inv_c[l] = 2.0 * H * H / kap;
   }
+  for (int l = 0; l < kMaxLevels; ++l) P.inv_c_f[l] = (float)P.inv_c[l], P.q_const_f[l] = (float)P.q_const[l];
+  P.c0_f = (float)P.c0;
+  P.a_scalar_f = (float)P.a_scalar;
 
   // ---- uploads and clears (stream-ordered, no allocation) ---------------------------------
 #define NA_CUDA(call)                                                     \
@@ -264,6 +267,9 @@ extern "C" int sgml_solve_noalloc(int dim, int n, int precision, const double* f
   p.w_edge = w_edge();
   p.w_corner = w_corner();
   p.omega = tg;
+  p.w_edge_f = (float)p.w_edge;
+  p.w_corner_f = (float)p.w_corner;
+  p.one_m_omega_f = (float)(1.0 - p.omega);
   p.n_r = n_r;
   p.sync = (GridSync*)(base + o_sync);
   p.timeout_ns = 2000000000ull;

@@ -75,3 +75,22 @@ def test_autotuner_picks_a_candidate_and_caches(tmp_path):
     ref = gpu_grid([d], sgml.MIXED)
     ref.solve_to_tol(1e-10)
     assert np.array_equal(g.get_solution(0), ref.get_solution(0))
+
+
+def test_batch_beyond_the_cached_stop_flags_matches_single_solves():
+    """300 problems: the kernels keep the first 256 problems' stop flags in shared memory and read
+    the rest from global memory, and problem 0's descriptor from shared memory.  Problems stop at
+    different cycles; each one's solution must equal, bit for bit, its solve alone (the arithmetic
+    of a node does not depend on the batch or the work partition)."""
+    probs = [inputs.random_problem(2, 3 + (b % 3), seed=5000 + b, flux=(b % 7 == 0)) for b in range(300)]
+    g = gpu_grid(probs, sgml.MIXED, max_cycles=300)
+    st, cyc, rel = g.solve_to_tol(1e-10)
+    assert st == sgml.OK and np.all(rel <= 1e-10)
+    assert len(set(int(c) for c in np.asarray(cyc).ravel())) > 1  # the problems stop at different cycles
+    for b in (0, 1, 255, 256, 257, 298, 299):
+        d = probs[b]
+        g1 = gpu_grid([d], sgml.MIXED, max_cycles=300)
+        st1, cyc1, _ = g1.solve_to_tol(1e-10)
+        assert st1 == sgml.OK and int(np.asarray(cyc1).ravel()[0]) == int(np.asarray(cyc).ravel()[b]), b
+        assert np.array_equal(g.get_solution(b), g1.get_solution(0)), b
+        assert oracle_problem(d).rel_residual(g.get_solution(b), d["f"]) <= 1.2e-10, b
