@@ -150,16 +150,15 @@ __device__ bool grid_sync(GridSync* gs, unsigned long long timeout_ns) {
     // arrival: release (the CTA's writes, ordered before by the CTA barrier, become visible)
     asm volatile("atom.add.release.gpu.u64 %0, [%1], 1;" : "=l"(old) : "l"(&gs->arrive) : "memory");
     const unsigned long long target = (old / G + 1) * G;  // every CTA of this round has arrived
-    unsigned long long seen;
-    asm volatile("ld.relaxed.gpu.u64 %0, [%1];" : "=l"(seen) : "l"(&gs->arrive) : "memory");
-    if (seen < target) {
+    if (old + 1 < target) {  // the last CTA to arrive knows it from the returned value
       const unsigned long long t0 = globaltimer();
       unsigned spins = 0;
       for (;;) {
+        unsigned long long seen;
         asm volatile("ld.relaxed.gpu.u64 %0, [%1];" : "=l"(seen) : "l"(&gs->arrive) : "memory");
         if (seen >= target) break;
         if ((++spins & 31u) == 0u) {
-          if (ld_volatile(&gs->error)) {
+          if (ld_volatile(&gs->error)) {  // another CTA gave up: stop too
             ok = 0;
             break;
           }
@@ -171,8 +170,10 @@ __device__ bool grid_sync(GridSync* gs, unsigned long long timeout_ns) {
         }
       }
     }
-    asm volatile("fence.acq_rel.gpu;" ::: "memory");  // acquire: the other CTAs' writes are visible
-    if (ld_volatile(&gs->error)) ok = 0;
+    // acquire: the other CTAs' writes are visible.  No error load on success: only a timed-out
+    // CTA sets the flag, and it leaves the kernel, so every other CTA meets the flag while it
+    // spins at the next barrier (one load round trip less per barrier).
+    asm volatile("fence.acq_rel.gpu;" ::: "memory");
     s_ok = ok;
   }
   __syncthreads();
