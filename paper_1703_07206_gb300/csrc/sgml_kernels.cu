@@ -1921,6 +1921,10 @@ __device__ void phase_sweep(const KernelParams& p, const Phase& ph, int c, unsig
 // Row phases: restriction, interpolation to the next finer level, injection to the next coarser.
 // ---------------------------------------------------------------------------------------------
 
+// Row phases issue the loads of several x positions per lane before storing (a row of a large level
+// would otherwise take one load round trip per 32 nodes).
+constexpr int kRestrictBatch = 2, kInjectBatch = 4;
+
 // Restriction pass: level l-1 -> level l (Eqs. 3-4 at distance 2^(l-1) h), even images.
 template <typename T, int DIM>
 __device__ void phase_restrict(const KernelParams& p, int l) {
@@ -1937,21 +1941,31 @@ __device__ void phase_restrict(const KernelParams& p, int l) {
 #pragma unroll
       for (int dy = 0; dy < 3; ++dy)
         rows[dz][dy] = ((long long)(DIM == 3 ? refl(2 * z + dz - 1, Ns) : 0) * Ns + refl(2 * y + dy - 1, Ns)) * Ns;
-    for (int x = lane; x < N; x += 32) {
-      const int xm = refl(2 * x - 1, Ns), x0 = 2 * x, xp = refl(2 * x + 1, Ns);
-      T acc = (T)0;
+    // kRestrictBatch x positions per lane are formed before any is stored (source and destination
+    // share one array, so the compiler would not move the next position's loads above a store)
+    for (int xb = lane; xb < N; xb += 32 * kRestrictBatch) {
+      T acc[kRestrictBatch];
 #pragma unroll
-      for (int dz = 0; dz < (DIM == 3 ? 3 : 1); ++dz) {
-        T accz = (T)0;
+      for (int u = 0; u < kRestrictBatch; ++u) {
+        const int x = xb + 32 * u;
+        acc[u] = (T)0;
+        if (x >= N) continue;
+        const int xm = refl(2 * x - 1, Ns), x0 = 2 * x, xp = refl(2 * x + 1, Ns);
 #pragma unroll
-        for (int dy = 0; dy < 3; ++dy) {
-          const T* row = src + rows[DIM == 3 ? dz : 0][dy];
-          const T line = (T)0.25 * row[xm] + (T)0.5 * row[x0] + (T)0.25 * row[xp];
-          accz += (dy == 1 ? (T)0.5 : (T)0.25) * line;
+        for (int dz = 0; dz < (DIM == 3 ? 3 : 1); ++dz) {
+          T accz = (T)0;
+#pragma unroll
+          for (int dy = 0; dy < 3; ++dy) {
+            const T* row = src + rows[DIM == 3 ? dz : 0][dy];
+            const T line = (T)0.25 * row[xm] + (T)0.5 * row[x0] + (T)0.25 * row[xp];
+            accz += (dy == 1 ? (T)0.5 : (T)0.25) * line;
+          }
+          acc[u] += DIM == 3 ? (dz == 1 ? (T)0.5 : (T)0.25) * accz : accz;
         }
-        acc += DIM == 3 ? (dz == 1 ? (T)0.5 : (T)0.25) * accz : accz;
       }
-      dst[x] = acc;
+#pragma unroll
+      for (int u = 0; u < kRestrictBatch; ++u)
+        if (xb + 32 * u < N) dst[xb + 32 * u] = acc[u];
     }
   });
 }
@@ -2130,10 +2144,16 @@ __device__ void phase_inject(const KernelParams& p, const Phase& ph) {
     const long long row = ((long long)z * N + y) * N;
     T* E = (T*)p.E + P.off_lvl[l] + row;
     T* B = (T*)p.B + P.off_lvl[l] + row;
-    for (int x = lane; x < N; x += 32) {
-      const T v = src[2 * x];
-      E[x] = v;
-      B[x] = v;
+    for (int xb = lane; xb < N; xb += 32 * kInjectBatch) {
+      T v[kInjectBatch];
+#pragma unroll
+      for (int u = 0; u < kInjectBatch; ++u) v[u] = xb + 32 * u < N ? src[2 * (xb + 32 * u)] : (T)0;
+#pragma unroll
+      for (int u = 0; u < kInjectBatch; ++u)
+        if (xb + 32 * u < N) {
+          E[xb + 32 * u] = v[u];
+          B[xb + 32 * u] = v[u];
+        }
     }
   });
 }
