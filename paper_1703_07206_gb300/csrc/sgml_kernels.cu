@@ -1921,6 +1921,13 @@ __device__ void phase_sweep(const KernelParams& p, const Phase& ph, int c, unsig
 // Row phases: restriction, interpolation to the next finer level, injection to the next coarser.
 // ---------------------------------------------------------------------------------------------
 
+// One line of the restriction stencil, 1/4 f(x - 1) + 1/2 f(x) + 1/4 f(x + 1), explicitly rounded so
+// that its value never depends on how the compiler contracts the expression.
+template <typename T>
+__device__ __forceinline__ T restrict_line(T a, T b, T c) {
+  return rn_fma((T)0.25, c, rn_fma((T)0.5, b, rn_mul((T)0.25, a)));
+}
+
 // Row phases issue the loads of several x positions per lane before storing (a row of a large level
 // would otherwise take one load round trip per 32 nodes).
 constexpr int kRestrictBatch = 2, kInjectBatch = 4;
@@ -1957,10 +1964,9 @@ __device__ void phase_restrict(const KernelParams& p, int l) {
 #pragma unroll
           for (int dy = 0; dy < 3; ++dy) {
             const T* row = src + rows[DIM == 3 ? dz : 0][dy];
-            const T line = (T)0.25 * row[xm] + (T)0.5 * row[x0] + (T)0.25 * row[xp];
-            accz += (dy == 1 ? (T)0.5 : (T)0.25) * line;
+            accz = rn_fma(dy == 1 ? (T)0.5 : (T)0.25, restrict_line(row[xm], row[x0], row[xp]), accz);
           }
-          acc[u] += DIM == 3 ? (dz == 1 ? (T)0.5 : (T)0.25) * accz : accz;
+          acc[u] = DIM == 3 ? rn_fma(dz == 1 ? (T)0.5 : (T)0.25, accz, acc[u]) : rn_add(acc[u], accz);
         }
       }
 #pragma unroll
@@ -1996,6 +2002,12 @@ struct ProlongStage {
 
 static_assert(sizeof(ProlongStage<float>) * kProlongStages <= phase_smem_bytes<float>(), "shared memory");
 static_assert(sizeof(ProlongStage<double>) * kProlongStages <= phase_smem_bytes<double>(), "shared memory");
+
+// (a + b) / 2, explicitly rounded.
+template <typename T>
+__device__ __forceinline__ T half_sum(T a, T b) {
+  return rn_mul((T)0.5, rn_add(a, b));
+}
 
 template <typename T>
 __device__ void prolong3(const KernelParams& p, const Phase& ph, const TileTask& tk, ProlongStage<T>* st) {
@@ -2050,10 +2062,10 @@ __device__ void prolong3(const KernelParams& p, const Phase& ph, const TileTask&
   auto plane_val = [&](const ProlongStage<T>& S, T out[2]) {
     const T a0 = S.d[ty * kCX + lx0], a1 = S.d[ty * kCX + lx1];
     const T b0 = S.d[(ty + 1) * kCX + lx0], b1 = S.d[(ty + 1) * kCX + lx1];
-    const T ra = (x & 1) ? (T)0.5 * (a0 + a1) : a0;
-    const T rb = (x & 1) ? (T)0.5 * (b0 + b1) : b0;
-    out[0] = ra;                    // y even: the coarse row itself
-    out[1] = (T)0.5 * (ra + rb);    // y odd: halfway between two coarse rows
+    const T ra = (x & 1) ? half_sum(a0, a1) : a0;
+    const T rb = (x & 1) ? half_sum(b0, b1) : b0;
+    out[0] = ra;                // y even: the coarse row itself
+    out[1] = half_sum(ra, rb);  // y odd: halfway between two coarse rows
   };
   for (int k = 0; k < D - 2; ++k) issue(k);
   T prev[2] = {(T)0, (T)0};
@@ -2062,7 +2074,7 @@ __device__ void prolong3(const KernelParams& p, const Phase& ph, const TileTask&
     __syncthreads();
     issue(k + D - 2);
     ProlongStage<T>& S = st[k % D];
-    if (!init && has_cell) S.d[tid] -= S.b[tid];
+    if (!init && has_cell) S.d[tid] = rn_add(S.d[tid], -S.b[tid]);
     __syncthreads();
     T cur[2];
     plane_val(S, cur);
@@ -2074,9 +2086,9 @@ __device__ void prolong3(const KernelParams& p, const Phase& ph, const TileTask&
 #pragma unroll
       for (int r = 0; r < 2; ++r) {
         if (!cl.in[r]) continue;
-        const T v = j == 0 ? (T)0.5 * (prev[r] + cur[r]) : cur[r];
+        const T v = j == 0 ? half_sum(prev[r], cur[r]) : cur[r];
         const T b = init ? (T)0 : S.base[j][tid + r * kThreads];
-        El[z * NN + cl.off[r]] = b + v;
+        El[z * NN + cl.off[r]] = rn_add(b, v);
       }
     }
     prev[0] = cur[0];
