@@ -47,6 +47,8 @@ struct sgml_grid {
   GridSync* d_sync = nullptr;
   Phase* d_phases = nullptr;
   int nphases = 0;
+  std::vector<Phase> h_phases;  // host copy of the uploaded phase table
+  size_t phases_cap = 0;        // capacity of d_phases in entries
   long long* d_rows = nullptr;
   TileTask* d_tasks = nullptr;
   int* d_task_off = nullptr;
@@ -55,6 +57,8 @@ struct sgml_grid {
   double* d_hist = nullptr;
   int hist_cap = 0;
   double *U = nullptr, *F = nullptr, *SIG64 = nullptr, *A64 = nullptr;
+  double* pyr64 = nullptr;     // FP64 scratch of the coefficient pyramid (levels >= 1), kept between builds
+  long long pyr64_cap = 0;     // its size in doubles
   float2* RESP = nullptr;  // mixed form: accumulated residual as hi + lo float pairs
   void* A0 = nullptr;
   void *E = nullptr, *E2 = nullptr, *B = nullptr, *R = nullptr, *SIG = nullptr, *Q = nullptr;
@@ -200,12 +204,21 @@ static int effective_quad_levels(const sgml_grid* g) {
 
 static int upload_phases(sgml_grid* g) {
   std::vector<Phase> ph = build_phases(g->n_max, g->n_r, effective_pair_levels(g), any_projects_mean(g));
-  if (g->d_phases) SGML_CUDA(cudaFree(g->d_phases));
-  g->d_phases = nullptr;
+  const bool same = g->d_phases && ph.size() == g->h_phases.size() &&
+                    std::memcmp(ph.data(), g->h_phases.data(), sizeof(Phase) * ph.size()) == 0;
+  if (!same) {  // (re)upload only a changed table, reallocating only when it grew
+    if (ph.size() > g->phases_cap) {
+      if (g->d_phases) SGML_CUDA(cudaFree(g->d_phases));
+      g->d_phases = nullptr;
+      g->phases_cap = 0;
+      SGML_CUDA(cudaMalloc(&g->d_phases, sizeof(Phase) * std::max<size_t>(ph.size(), 1)));
+      g->phases_cap = ph.size();
+    }
+    SGML_CUDA(cudaMemcpyAsync(g->d_phases, ph.data(), sizeof(Phase) * ph.size(), cudaMemcpyHostToDevice, g->stream));
+    SGML_CUDA(cudaStreamSynchronize(g->stream));
+    g->h_phases = ph;
+  }
   g->nphases = (int)ph.size();
-  SGML_CUDA(cudaMalloc(&g->d_phases, sizeof(Phase) * std::max<size_t>(ph.size(), 1)));
-  SGML_CUDA(cudaMemcpyAsync(g->d_phases, ph.data(), sizeof(Phase) * ph.size(), cudaMemcpyHostToDevice, g->stream));
-  SGML_CUDA(cudaStreamSynchronize(g->stream));
   g->dirty_phases = false;
   return SGML_OK;
 }
@@ -317,7 +330,20 @@ static void fill_float_copies(ProblemDesc& P) {
 static int build_coeffs(sgml_grid* g) {
   const double kap = kappa_of(g->dim, g->stencil);
   const double tg = g->theta * jacobi_gain(g->dim);
-  std::vector<double*> tmp;
+  // FP64 scratch for the restricted sigma / a of every heterogeneous problem's levels >= 1, allocated
+  // once (re-setting coefficients, e.g. every step of an end-to-end loop, then costs no allocation)
+  long long need = 0;
+  for (const ProblemDesc& P : g->P)
+    if (P.hetero)
+      for (int l = 1; l <= P.n - 1; ++l) need += nodes(g->dim, P.n, l) * (P.a_per_node ? 2 : 1);
+  if (need > g->pyr64_cap) {
+    if (g->pyr64) SGML_CUDA(cudaFree(g->pyr64));
+    g->pyr64 = nullptr;
+    g->pyr64_cap = 0;
+    SGML_CUDA(cudaMalloc(&g->pyr64, sizeof(double) * need));
+    g->pyr64_cap = need;
+  }
+  double* next = g->pyr64;
   for (int b = 0; b < g->batch; ++b) {
     ProblemDesc& P = g->P[b];
     for (int l = 0; l < kMaxLevels; ++l) P.q_const[l] = 0.0, P.inv_c[l] = 0.0;
@@ -337,13 +363,13 @@ static int build_coeffs(sgml_grid* g) {
     av[0] = P.a_per_node ? g->A64 + P.off_full : nullptr;
     for (int l = 1; l <= P.n - 1; ++l) {
       const long long M = nodes(g->dim, P.n, l);
-      SGML_CUDA(cudaMalloc(&sig[l], sizeof(double) * M));
-      tmp.push_back(sig[l]);
+      sig[l] = next;
+      next += M;
       SGML_CUDA(launch_restrict64(g->dim, sig[l - 1], (int)side(P.n, l - 1), sig[l], (int)side(P.n, l), g->stream));
       g->launches++;
       if (P.a_per_node) {
-        SGML_CUDA(cudaMalloc(&av[l], sizeof(double) * M));
-        tmp.push_back(av[l]);
+        av[l] = next;
+        next += M;
         SGML_CUDA(launch_restrict64(g->dim, av[l - 1], (int)side(P.n, l - 1), av[l], (int)side(P.n, l), g->stream));
         g->launches++;
       }
@@ -354,8 +380,6 @@ static int build_coeffs(sgml_grid* g) {
       g->launches++;
     }
   }
-  SGML_CUDA(cudaStreamSynchronize(g->stream));
-  for (double* t : tmp) SGML_CUDA(cudaFree(t));
   g->dirty_coeffs = false;
   g->dirty_desc = true;
   return SGML_OK;
@@ -950,7 +974,7 @@ int sgml_launch_count(sgml_grid_t g, long long* count) {
 int sgml_destroy(sgml_grid_t g) {
   if (!g) return SGML_OK;
   cudaStreamSynchronize(g->stream);
-  void* ptrs[] = {g->U, g->F, g->SIG64, g->A64, g->RESP, g->A0, g->E, g->E2, g->B, g->R, g->SIG, g->Q,
+  void* ptrs[] = {g->U, g->F, g->SIG64, g->A64, g->pyr64, g->RESP, g->A0, g->E, g->E2, g->B, g->R, g->SIG, g->Q,
                   g->d_probs, g->d_state, g->d_accum, g->d_sync, g->d_phases, g->d_rows, g->d_tasks,
                   g->d_task_off, g->d_tasks4, g->d_task_off4, g->d_hist, g->d_trace, g->d_diag,
                   g->d_rowsum, g->d_umean, g->d_fmean};
