@@ -422,6 +422,88 @@ def run_ncu_case(args):
 args_global = None
 
 
+def run_next_rows(args):
+    """Timings of the widened rows (not the headline): the capacitor of Sec. 3.4, the all-Neumann
+    Helmholtz problem of Eq. 10, the per-level diagnostic residual, and the post-processing
+    kernels of Secs. 3.2-3.3 (curl, streamlines, grid motion).  Inputs are synthetic and resident on
+    the device; each figure is the mean of `--steps` calls after `--warmup` untimed ones, timed
+    with CUDA events on the current stream.  Prints one JSON line."""
+    import torch
+    from paper_1703_07206_gb300 import inputs, sgml
+    dev = torch.device("cuda:0")
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+    peak, peak_kind = load_peaks()
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(args.steps):
+            out = fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / args.steps, out
+
+    def solve_row(probs, tol, diag=0):
+        dim = probs[0]["dim"]
+        g = sgml.Grid(dim, [d["n"] for d in probs], precision=sgml.MIXED, stream=stream.cuda_stream)
+        g.set_params(max_cycles=args.max_cycles)
+        for b, d in enumerate(probs):
+            sgml.problem_into_grid(g, b, d)
+        if diag:
+            g.set_diagnostics(diag)
+
+        def one():
+            st, cyc, rel = g.solve_to_tol(tol)
+            if st != sgml.OK:
+                raise RuntimeError(f"solve failed: status {st}")
+            return int(np.max(cyc)), float(np.max(rel))
+
+        ms, (cyc, rel) = timed(one)
+        nodes = sum(int(np.prod(d["f"].shape)) for d in probs)
+        return {"nodes": nodes, "cycles": cyc, "rel_residual": rel, "ms_per_solve": round(ms, 3),
+                "solved_nodes_per_s": nodes / (ms * 1e-3)}
+
+    out = {"metric": "next-row timings", "data": "synthetic", "steps": args.steps, "warmup": args.warmup}
+    out["capacitor_129cubed"] = solve_row([inputs.capacitor_3d(n=7, sign=+1.0)], TOL)
+    out["eq10_neumann_helmholtz_1025sq"] = solve_row([inputs.neumann_helmholtz_2d(n=10, a=0.1)], TOL)
+    out["eq10_neumann_helmholtz_65sq"] = solve_row([inputs.neumann_helmholtz_2d(n=6, a=0.1)], TOL)
+    d129 = inputs.dielectric_spheres_3d(n=7)
+    base = solve_row([d129], TOL)
+    diag = solve_row([d129], TOL, diag=args.max_cycles + 1)
+    out["diagnostics_129cubed"] = {"ms_off": base["ms_per_solve"], "ms_on": diag["ms_per_solve"],
+                                   "overhead": diag["ms_per_solve"] / base["ms_per_solve"] - 1.0}
+    out["trefoil_3x129cubed"] = solve_row(inputs.trefoil_vorticity_3d(n=7), TOL)
+    # post-processing kernels on synthetic fields
+    rng = np.random.default_rng(7)
+    N = 257
+    psi = torch.from_numpy(rng.standard_normal((3, N, N, N))).to(dev)
+    ms, _ = timed(lambda: sgml.curl(psi, stream=stream))
+    bytes_per_call = 48.0 * N ** 3  # three potentials read, three velocity components written
+    out["curl_257cubed"] = {"ms": round(ms, 3), "achieved_gbs": bytes_per_call / (ms * 1e-3) / 1e9,
+                            "peak_gbs": peak, "peak_kind": peak_kind,
+                            "frac": bytes_per_call / (ms * 1e-3) / 1e9 / peak, "bytes_per_node": 48}
+    del psi
+    Nv = 129
+    v = torch.from_numpy(0.2 * rng.standard_normal((3, Nv, Nv, Nv))).to(dev)
+    seeds = torch.from_numpy(rng.uniform(0.2, 0.8, size=(4096, 3))).to(dev)
+    ms, _ = timed(lambda: sgml.streamlines(v, seeds, 1e-3, 1000, stream=stream))
+    out["streamlines_129cubed"] = {"ms": round(ms, 3), "seeds": 4096, "steps": 1000,
+                                   "rk4_steps_per_s": 4096 * 1000 / (ms * 1e-3)}
+    del v, seeds
+    for name, dim, n, steps in (("grid_motion_1025sq", 2, 10, 100), ("grid_motion_129cubed", 3, 7, 20)):
+        M = (2 ** n + 1) ** dim
+        shape = (2 ** n + 1,) * dim
+        u = torch.from_numpy(0.05 * rng.standard_normal(shape)).to(dev)
+        f = torch.from_numpy(0.5 + rng.uniform(size=shape)).to(dev)
+        ms, _ = timed(lambda: sgml.grid_motion(u, f, steps, stream=stream))
+        out[name] = {"ms": round(ms, 3), "nodes": M, "euler_steps": steps, "node_steps_per_s": M * steps / (ms * 1e-3)}
+    print(json.dumps(out))
+
+
 def main():
     global args_global
     ap = argparse.ArgumentParser()
@@ -448,6 +530,8 @@ def main():
     ap.add_argument("--quad-levels", type=int, default=0, help="levels whose sweeps run four rows per thread")
     ap.add_argument("--trace", action="store_true", help="with --ncu-case: per-phase times from the kernel's trace")
     ap.add_argument("--trace-cycles", type=int, default=64)
+    ap.add_argument("--next-rows", action="store_true",
+                    help="time the widened rows (capacitor, Eq. 10, diagnostics, curl, streamlines, grid motion)")
     args = ap.parse_args()
     args_global = args
     if args.warmup < 3 and args.impl == "gb300" and not args.ncu_case:
@@ -456,6 +540,8 @@ def main():
         run_reference(args)
     elif args.ncu_case:
         run_ncu_case(args)
+    elif args.next_rows:
+        run_next_rows(args)
     else:
         run_gpu(args)
 

@@ -99,6 +99,15 @@ __device__ __forceinline__ double nan_max(double a, double b) {
 // level, recorded per problem, cycle and level when the grid asks for it.  At a node it is
 // |e_new - e| / dtau; the CTA's maximum, in the units of the unscaled residual, is merged into
 // diag[(b * diag_cycles + c) * kMaxLevels + l] (non-negative doubles order like their bits).
+// Diagnostic pseudo-residual of one node, |e_new - e| / dtau = |e_new - e| c / q: kept per thread as
+// max |e_new - e| / q in the cycle precision and scaled by c = 1 / inv_c once (in the FP32 form a
+// reciprocal per node instead of an FP64 division, which would double the sweep's time).
+template <typename T>
+__device__ __forceinline__ T diag_term(T de, T q) {
+  if constexpr (sizeof(T) == 4) return fabsf(de) * __frcp_rn(q);
+  else return fabs(de) / q;
+}
+
 __device__ void diag_flush(const KernelParams& p, int b, int c, int l, double mx) {
   __shared__ double s_dmx[32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -1244,7 +1253,7 @@ __device__ void sweep3(const KernelParams& p, const Phase& ph, int c, const Tile
   // A piece of one plane (the coarse levels' usual share) fetches its three planes in one round trip.
   const int pre = nplanes <= D - 1 ? nplanes : D - 2;
   for (int k = 0; k < pre; ++k) issue(k);
-  double dmx = 0.0;  // diagnostic pseudo-residual of the thread's nodes (DIAG)
+  T dmx = (T)0;  // diagnostic pseudo-residual of the thread's nodes, times inv_c (DIAG)
   // One plane step: wait for plane k, start plane k + D - 2, form its in-plane sums into `nw`,
   // update the nodes of plane k - 1 from (m, o, nw).  The z loop is unrolled by three so that the
   // three-plane window rotates by renaming instead of moving registers.
@@ -1269,7 +1278,7 @@ __device__ void sweep3(const KernelParams& p, const Phase& ph, int c, const Tile
                            : (T)0;
         const int slot = tid + r * kThreads;
         const T e_new = sweep_update<T, HET>(kc, S, slot, b0 + (r + 1) * kHX + 1, CSe, CSse, o[r].v);
-        if (DIAG) dmx = fmax(dmx, (double)fabs(e_new - o[r].v) / ((double)(HET ? S.q[slot] : kc.q_const) * (double)kc.inv_c));
+        if (DIAG) dmx = fmax(dmx, diag_term(e_new - o[r].v, HET ? S.q[slot] : kc.q_const));
         const unsigned idx = zoff + (unsigned)cl.off[r];
         if (LAST) Ug[idx] = __fma_rn((double)e_new, inv_scale, S.u[slot]);
         if (keep) dst[idx] = e_new;
@@ -1286,7 +1295,7 @@ __device__ void sweep3(const KernelParams& p, const Phase& ph, int c, const Tile
   }
   cp_async_wait<0>();
   __syncthreads();
-  if (DIAG) diag_flush(p, tk.b, c, ph.level, dmx / p.state[tk.b].scale_used[c & 1]);
+  if (DIAG) diag_flush(p, tk.b, c, ph.level, (double)dmx / (double)kc.inv_c / p.state[tk.b].scale_used[c & 1]);
 }
 
 // 2-D: one halo tile per task, the CTA's tasks pipelined kSweepStages - 2 deep.
@@ -1335,7 +1344,7 @@ __device__ void sweep2(const KernelParams& p, const Phase& ph, int c, SweepStage
     const TileTask& tk = task(j);
     const SweepCtl sc = sweep_ctl(p, ph, tk.b);
     if (!mine(sc)) continue;
-    double dmx = 0.0;
+    T dmx = (T)0;  // pseudo-residual times inv_c (DIAG)
     const ProblemDesc& P = prob_at(p, tk.b);
     const int N = sc.N;
     const Columns cl = own_columns(P, N, tk.x0, tk.y0);
@@ -1353,15 +1362,11 @@ __device__ void sweep2(const KernelParams& p, const Phase& ph, int c, SweepStage
       const int slot = tid + r * kThreads, cc = b0 + (r + 1) * kHX + 1;
       const T e_new = P.hetero ? sweep_update<T, true>(kc, S, slot, cc, CSe, rn_fma(kc.w_e, ps[r].sC, ps[r].sF), ps[r].v)
                                : sweep_update<T, false>(kc, S, slot, cc, CSe, (T)0, ps[r].v);
-      if (DIAG) {
-        const double pr = (double)fabs(e_new - ps[r].v) /
-                          ((double)(P.hetero ? S.q[slot] : kc.q_const) * (double)kc.inv_c);
-        if (pr > dmx) dmx = pr;
-      }
+      if (DIAG) dmx = fmax(dmx, diag_term(e_new - ps[r].v, P.hetero ? S.q[slot] : kc.q_const));
       if (LAST) p.U[P.off_full + cl.off[r]] = __fma_rn((double)e_new, inv_scale, S.u[slot]);
       if (!LAST || p.mixed) dst[cl.off[r]] = e_new;
     }
-    if (DIAG) diag_flush(p, tk.b, c, l, dmx / p.state[tk.b].scale_used[c & 1]);
+    if (DIAG) diag_flush(p, tk.b, c, l, (double)dmx / (double)kc.inv_c / p.state[tk.b].scale_used[c & 1]);
   }
   cp_async_wait<0>();
   __syncthreads();

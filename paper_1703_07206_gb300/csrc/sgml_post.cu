@@ -37,17 +37,19 @@ __device__ __forceinline__ double deriv(const double* __restrict__ f, int N, dou
   return (f[c + s] - f[c - s]) * inv2h;
 }
 
-__global__ void curl_kernel(int N, double inv2h, const double* __restrict__ psi, double* __restrict__ v) {
+// One thread per node: x from the block's threads, y and z from the grid (no index divisions).
+__global__ void __launch_bounds__(128) curl_kernel(int N, double inv2h, const double* __restrict__ psi,
+                                                   double* __restrict__ v) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
+  if (i >= N) return;
   const long long M = (long long)N * N * N;
   const double* px = psi;
   const double* py = psi + M;
   const double* pz = psi + 2 * M;
-  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < M; c += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(c % N), j = (int)((c / N) % N), k = (int)(c / ((long long)N * N));
-    v[c] = deriv(pz, N, inv2h, i, j, k, 1) - deriv(py, N, inv2h, i, j, k, 2);
-    v[M + c] = deriv(px, N, inv2h, i, j, k, 2) - deriv(pz, N, inv2h, i, j, k, 0);
-    v[2 * M + c] = deriv(py, N, inv2h, i, j, k, 0) - deriv(px, N, inv2h, i, j, k, 1);
-  }
+  const long long c = ((long long)k * N + j) * N + i;
+  v[c] = deriv(pz, N, inv2h, i, j, k, 1) - deriv(py, N, inv2h, i, j, k, 2);
+  v[M + c] = deriv(px, N, inv2h, i, j, k, 2) - deriv(pz, N, inv2h, i, j, k, 0);
+  v[2 * M + c] = deriv(py, N, inv2h, i, j, k, 0) - deriv(px, N, inv2h, i, j, k, 1);
 }
 
 __device__ __forceinline__ bool inside(const double x[3]) {
@@ -261,14 +263,9 @@ int sgml_curl(int n, const double* psi, double* v, void* cuda_stream) {
   if (!psi || !v || psi == v) return post_fail(SGML_ERR_ARG, "psi and v must be distinct non-NULL arrays");
   if (!device_pointer(psi) || !device_pointer(v)) return post_fail(SGML_ERR_ARG, "psi and v must be device arrays");
   const int N = (1 << n) + 1;
-  const long long M = (long long)N * N * N;
   const double h = 1.0 / (double)(N - 1);
-  int dev = 0, sms = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const long long want = (M + 255) / 256;
-  const int blocks = (int)(want < 8LL * sms ? want : 8LL * sms);
-  curl_kernel<<<blocks, 256, 0, (cudaStream_t)cuda_stream>>>(N, 1.0 / (2.0 * h), psi, v);
+  const dim3 grid((unsigned)((N + 127) / 128), (unsigned)N, (unsigned)N);
+  curl_kernel<<<grid, 128, 0, (cudaStream_t)cuda_stream>>>(N, 1.0 / (2.0 * h), psi, v);
   const cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? SGML_OK : post_fail(SGML_ERR_CUDA, cudaGetErrorString(e));
 }
