@@ -108,18 +108,41 @@ __device__ __forceinline__ T diag_term(T de, T q) {
   else return fabs(de) / q;
 }
 
+// Problem 0's pseudo-residuals of the current cycle, per level, folded in shared memory and committed
+// to global memory once per cycle (diag_commit): a global atomic per tile on one address per level
+// serialised hundreds of CTAs, and the recording cost more than the solve.
+__shared__ unsigned long long s_diag0[kMaxLevels];
+
 __device__ void diag_flush(const KernelParams& p, int b, int c, int l, double mx) {
-  __shared__ double s_dmx[32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if (b == 0) {  // (positive doubles order like their bit patterns)
+    if (lane == 0 && mx > 0.0) atomicMax(&s_diag0[l], (unsigned long long)__double_as_longlong(mx));
+    return;
+  }
+  __shared__ double s_dmx[32];
   if (lane == 0) s_dmx[warp] = mx;
   __syncthreads();
   if (threadIdx.x == 0) {
     double m = 0.0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, s_dmx[w]);
-    if (c < p.diag_cycles && m > 0.0)
-      atomicMax(&p.diag[((long long)b * p.diag_cycles + c) * kMaxLevels + l], (unsigned long long)__double_as_longlong(m));
+    if (c < p.diag_cycles && m > 0.0) {
+      unsigned long long* slot = &p.diag[((long long)b * p.diag_cycles + c) * kMaxLevels + l];
+      const unsigned long long bits = (unsigned long long)__double_as_longlong(m);
+      if (bits > *(volatile unsigned long long*)slot) atomicMax(slot, bits);
+    }
+  }
+  __syncthreads();
+}
+
+// Commit problem 0's folded pseudo-residuals of cycle c (every CTA, after the cycle's last phase).
+__device__ void diag_commit(const KernelParams& p, int c) {
+  __syncthreads();
+  if (threadIdx.x < kMaxLevels) {
+    const unsigned long long v = s_diag0[threadIdx.x];
+    s_diag0[threadIdx.x] = 0ull;
+    if (v != 0ull && c < p.diag_cycles) atomicMax(&p.diag[(long long)c * kMaxLevels + threadIdx.x], v);
   }
   __syncthreads();
 }
@@ -258,6 +281,7 @@ __device__ __forceinline__ float inv_scale_f_at(const KernelParams& p, int b, in
 
 __device__ void load_tables(const KernelParams& p) {
   if (threadIdx.x == 0) s_prob0 = p.probs[0];
+  if (threadIdx.x < kMaxLevels) s_diag0[threadIdx.x] = 0ull;
   if (threadIdx.x < kMaxLevels) s_rows[threadIdx.x] = p.row_prefix[(long long)threadIdx.x * (p.batch + 1) + p.batch];
   for (int i = threadIdx.x; i < p.nphases && i < kPhaseCache; i += blockDim.x) s_phase[i] = p.phases[i];
   if (threadIdx.x < kMaxLevels) {
@@ -2282,6 +2306,7 @@ __global__ void __launch_bounds__(kThreads, SGML_MIN_CTAS) cycle_kernel(const Ke
       if (!grid_sync(p.sync, p.timeout_ns)) return;
       stamp(c, 3 + q);
     }
+    if (p.diag) diag_commit(p, c);
   }
 }
 
@@ -2301,6 +2326,7 @@ __global__ void __launch_bounds__(kThreads, SGML_MIN_CTAS) phase_kernel(const Ke
   } else {
     const Phase ph = phase_at(p, which);
     run_phase<T, DIM>(p, ph, c, sm);
+    if (p.diag) diag_commit(p, c);
   }
 }
 
