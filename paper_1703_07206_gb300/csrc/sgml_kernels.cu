@@ -113,23 +113,29 @@ __device__ __forceinline__ T diag_term(T de, T q) {
 // serialised hundreds of CTAs, and the recording cost more than the solve.
 __shared__ unsigned long long s_diag0[kMaxLevels];
 
-__device__ void diag_flush(const KernelParams& p, int b, int c, int l, double mx) {
+// A tile's pseudo-residual: each thread holds max |e_new - e| / q over its nodes in the cycle
+// precision; the warps reduce that (no FP64 work per thread) and one lane per warp scales it by
+// 1 / (inv_c s), which commutes with the maximum.
+template <typename T>
+__device__ void diag_flush(const KernelParams& p, int b, int c, int l, T mx, T inv_c) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  double m = 0.0;
+  if (lane == 0) m = (double)mx / (double)inv_c / p.state[b].scale_used[c & 1];
   if (b == 0) {  // (positive doubles order like their bit patterns)
-    if (lane == 0 && mx > 0.0) atomicMax(&s_diag0[l], (unsigned long long)__double_as_longlong(mx));
+    if (lane == 0 && m > 0.0) atomicMax(&s_diag0[l], (unsigned long long)__double_as_longlong(m));
     return;
   }
   __shared__ double s_dmx[32];
-  if (lane == 0) s_dmx[warp] = mx;
+  if (lane == 0) s_dmx[warp] = m;
   __syncthreads();
   if (threadIdx.x == 0) {
-    double m = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, s_dmx[w]);
-    if (c < p.diag_cycles && m > 0.0) {
+    double mm = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) mm = fmax(mm, s_dmx[w]);
+    if (c < p.diag_cycles && mm > 0.0) {
       unsigned long long* slot = &p.diag[((long long)b * p.diag_cycles + c) * kMaxLevels + l];
-      const unsigned long long bits = (unsigned long long)__double_as_longlong(m);
+      const unsigned long long bits = (unsigned long long)__double_as_longlong(mm);
       if (bits > *(volatile unsigned long long*)slot) atomicMax(slot, bits);
     }
   }
@@ -1319,7 +1325,7 @@ __device__ void sweep3(const KernelParams& p, const Phase& ph, int c, const Tile
   }
   cp_async_wait<0>();
   __syncthreads();
-  if (DIAG) diag_flush(p, tk.b, c, ph.level, (double)dmx / (double)kc.inv_c / p.state[tk.b].scale_used[c & 1]);
+  if (DIAG) diag_flush<T>(p, tk.b, c, ph.level, dmx, kc.inv_c);
 }
 
 // 2-D: one halo tile per task, the CTA's tasks pipelined kSweepStages - 2 deep.
@@ -1390,7 +1396,7 @@ __device__ void sweep2(const KernelParams& p, const Phase& ph, int c, SweepStage
       if (LAST) p.U[P.off_full + cl.off[r]] = __fma_rn((double)e_new, inv_scale, S.u[slot]);
       if (!LAST || p.mixed) dst[cl.off[r]] = e_new;
     }
-    if (DIAG) diag_flush(p, tk.b, c, l, (double)dmx / (double)kc.inv_c / p.state[tk.b].scale_used[c & 1]);
+    if (DIAG) diag_flush<T>(p, tk.b, c, l, dmx, kc.inv_c);
   }
   cp_async_wait<0>();
   __syncthreads();
