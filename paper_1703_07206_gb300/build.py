@@ -52,15 +52,22 @@ def build(force: bool = False, verbose: bool = False, defines=(), out: str | Non
     os.makedirs(BUILD, exist_ok=True)
     cc = nvcc()
     flags = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include"),
-                    "-I", CSRC]
-    if verbose:
-        flags += ["-Xptxas", "-v"]
+                    "-I", CSRC, "-Xptxas", "-v"]
     flags += [f"-D{d}" for d in defines]
 
     def compile_one(unit):
         src, tag, defs = unit
         obj = os.path.join(BUILD, f"{tag}.{os.getpid()}.{abs(hash(lib))}.o")
-        subprocess.run([cc, *flags, *[f"-D{d}" for d in defs], "-c", os.path.join(CSRC, src), "-o", obj], check=True)
+        r = subprocess.run([cc, *flags, *[f"-D{d}" for d in defs], "-c", os.path.join(CSRC, src), "-o", obj],
+                           capture_output=True, text=True)
+        if r.returncode != 0:
+            sys.stderr.write(r.stdout + r.stderr)
+            raise subprocess.CalledProcessError(r.returncode, r.args)
+        if verbose:
+            sys.stderr.write(r.stderr)
+        if out is None:  # ptxas's resource report (registers, spills, shared memory) of the build
+            with open(os.path.join(BUILD, f"ptxas_{tag}.log"), "w") as fh:
+                fh.write(r.stderr)
         return obj
 
     with ThreadPoolExecutor(len(UNITS)) as ex:
