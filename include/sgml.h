@@ -194,8 +194,9 @@ int sgml_get_trace(sgml_grid_t g, double* us, int cap, int* nphases, int* ncycle
  * launches record, for each problem, each of the first `cycles` cycles of the launch and each level
  * l, the largest |delta L_l e - r_l| met by that level's sweeps (|e_new - e| / delta tau at a node),
  * in the units of the residual f - delta L u.  At level 0 it is the residual of the correction
- * equation itself.  Costs a maximum and a division per node and sweep while on; fused pairs and
- * four-row tiles are not used meanwhile.  0 turns it off.  Synchronises. */
+ * equation itself.  Costs, while on, a reciprocal and a maximum per node and sweep and a warp
+ * reduction per tile (about +40 % solve time on a 129^3 problem); fused pairs and four-row tiles
+ * are not used meanwhile.  0 turns it off.  Synchronises. */
 int sgml_set_diagnostics(sgml_grid_t g, int cycles);
 
 /* The recorded pseudo-residuals of problem `problem` from the last launch: out[c * 13 + l] for
