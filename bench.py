@@ -4,8 +4,13 @@ Workload (one "step" = one full solve from the lifted boundary values, inputs re
 div(eps grad u) = f on the unit cube, 257^3 nodes, eps = 1 with 32 seeded spheres of eps = 80,
 f = 8 seeded unit Gaussian charges (std 2h), u = 0 on the boundary, solved by the SGML cycle until
 ||r||_inf / ||f||_inf <= 1e-10.  The mixed form (FP32 cycle, FP64 outer step) gives `value`; the FP64
-form is measured in the same run and reported beside it.  With --gpus N > 1 (torchrun, one rank per
-GPU) every rank solves its own seeded instance: independent replicas, weak scaling.
+form is measured in the same run and reported beside it, with its roofline against both HBM and the
+measured FP64 pipe.  Each form's error is reported against a tighter reference solution, the CPU
+oracle is timed on full solves (one thread and all cores), the coefficient-pyramid setup is timed
+on its own, and the other workloads of the benchmark set get secondary lines in `configs`:
+2-D Poisson 129^2 to 1e-12, the 3 x 513^3 trefoil vector Poisson, the batch of 256 uneven 2-D
+Helmholtz problems, and the 16 x 129^3 adjoint (forward + backward).  With --gpus N > 1 (torchrun,
+one rank per GPU) every rank solves its own seeded instance: independent replicas, weak scaling.
 
 Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle instead (host cores).
 """
@@ -32,6 +37,16 @@ TOL = 1e-10
 # pass per phase, n_r = 2, zig-zag, 8 level-0 sweeps (outer step 24 + 2b + 8, level-0 sweeps
 # 8 (3b + b), coarse levels (18b + 6b) / 7, b = bytes of the cycle precision).
 BYTES_PER_NODE_CYCLE = {"mixed": 182.0, "fp64": 331.0}
+# Algorithmic bytes per node per cycle of the other workloads (same count; 2-D / 3-D constant
+# coefficients: no sigma arrays).
+BYTES_2D_CONST = {"mixed": 152.0, "fp64": 280.0}
+BYTES_3D_CONST = {"mixed": 138.0, "fp64": 253.0}
+# FP64 instructions per node per cycle of the FP64 form on the 3-D heterogeneous workload, counted
+# from the kernels' arithmetic (n_r = 2, zig-zag): 8 level-0 sweeps x 36 (sigma * e products,
+# in-plane face / corner sums of e and sigma e, the z combination, the Jacobi update), the solution
+# update 1, the FP64 residual 88 (27 sigma-weighted differences: 78, the sums, the cast, the norms),
+# coarse-level sweeps 6 x 36 / 7, restrictions ~6, interpolations ~10.
+FP64_INSTR_PER_NODE_CYCLE = 424.0
 KERNEL_SOURCES = ["paper_1703_07206_gb300/csrc/sgml_kernels.cu", "paper_1703_07206_gb300/csrc/sgml_internal.cuh"]
 
 

@@ -126,7 +126,9 @@ int sgml_get_history(sgml_grid_t g, int problem, double* hist, int cap, int* cou
 
 /* r = f - delta L_0 u for one problem, with u given (N^dim values; the grid's own solution is not
  * touched), the grid's source, coefficients and boundary conditions (Neumann images carry the
- * prescribed derivative); r = 0 on fixed nodes.  FP64.  Synchronises. */
+ * prescribed derivative); r = 0 on fixed nodes.  FP64.  Device arrays of the grid's device are used in
+ * place; host arrays pass through a staging buffer the grid allocates once and keeps.  r must not
+ * alias u.  Synchronises. */
 int sgml_residual(sgml_grid_t g, int problem, const double* u, double* r);
 
 /* Adjoint gradient of J(u) with respect to sigma for one all-Dirichlet problem: given the forward
@@ -134,7 +136,9 @@ int sgml_residual(sgml_grid_t g, int problem, const double* u, double* r);
  * lambda = 0 on fixed nodes; delta L is symmetric there), writes
  * dJ/dsigma_m = kappa/(2h^2) sum_{o, m+o inside} w_o (lambda_{m+o} - lambda_m)(u_{m+o} - u_m)
  * (the derivative of Eq. 5's link coefficient (sigma_i + sigma_j)/2).  dJ/df = lambda.  FP64.
- * Returns SGML_ERR_ARG for a problem with a Neumann face.  Synchronises. */
+ * Device arrays of the grid's device are used in place, host arrays are staged as for sgml_residual.
+ * Returns SGML_ERR_ARG for a problem with a Neumann face, or if grad aliases lambda or u.
+ * Synchronises. */
 int sgml_sigma_gradient(sgml_grid_t g, int problem, const double* lambda, const double* u, double* grad);
 
 /* Launch shape and work partition of the cycle kernel (256 threads per CTA).
@@ -153,6 +157,16 @@ int sgml_sigma_gradient(sgml_grid_t g, int problem, const double* lambda, const 
  *     HBM once.  0: contiguous runs on every level.
  * Used by the autotuner.  Results do not depend on these settings (bit for bit). */
 int sgml_set_launch(sgml_grid_t g, int ctas_per_sm, int z_waves, int mode, int tile_x, int slab_z);
+
+/* Bounded grid barriers of the persistent cycle kernel (Sec. 2 runs every level inside one cycle;
+ * here one launch holds all of them, with grid-wide barriers between phases).  wait_limit_s (default
+ * 2.0, range 1e-4 .. 60) is the longest any CTA waits at one barrier before it records a timeout and
+ * the launch returns SGML_ERR_BARRIER_TIMEOUT (sync calls) -- a wait never spins forever.
+ * withhold_barrier >= 1 is a test aid: in every following launch CTA 0 withholds its arrival at
+ * that barrier (1-based count within the launch), so that all waits run out and the timeout path is
+ * exercised without any fault; 0 (the default) turns it off.  The grid stays usable: the next launch
+ * starts from cleared barrier words.  Host only; takes effect at the next launch. */
+int sgml_set_barrier_test(sgml_grid_t g, double wait_limit_s, int withhold_barrier);
 
 /* Fused sweep pairs (3-D, SGML_MIXED): on levels 0 .. pair_levels - 1 (default 0: off) the
  * k relaxation sweeps of a visit (Algorithm 2, Eq. 2) run two at a time in one pass over the level:
@@ -254,35 +268,46 @@ int sgml_streamlines(int n, const double* v, const double* seeds, int nseeds, do
 int sgml_grid_motion(int dim, int n, const double* u, const double* f, double t0, double t1, int nsteps, double* x,
                      void* cuda_stream);
 
+/* ---- Measurement aid ----------------------------------------------------------------------------
+ * Arithmetic throughput of the current GPU, the denominator of the FP64 form's roofline (the FP64
+ * form runs Sec. 2's pseudo-time iteration entirely in FP64; on a narrow FP64 pipe that pipe, not
+ * HBM, bounds it).  The paper has no counterpart.  Runs a kernel of independent FMA chains on every
+ * SM (a warm-up launch, then three timed with CUDA events on cuda_stream) in FP64 and in FP32 and
+ * writes thread-level FMA instructions per second to *fp64_fma_per_s and *fp32_fma_per_s.  Allocates
+ * and frees a small device buffer; synchronises.  SGML_ERR_ARG for NULL outputs. */
+int sgml_measure_fma_rates(void* cuda_stream, double* fp64_fma_per_s, double* fp32_fma_per_s);
+
 /* Message of the last failed sgml_curl / sgml_streamlines / sgml_grid_motion call on this thread. */
 const char* sgml_post_last_error(void);
 
 int sgml_destroy(sgml_grid_t g);
 const char* sgml_last_error(void);
 
-/* One complete solve that allocates no memory, for callers that cannot allocate device memory
- * where they want to solve: code running while a stream is captured into a CUDA graph, memory pools
- * that forbid foreign allocations, hosts with a device-memory budget fixed at start-up.  The paper
- * has no counterpart; this packages the same cycle kernel as sgml_solve_to_tol.
+/* One complete solve that allocates no memory, for callers that cannot allocate device memory where
+ * they want to solve: frameworks whose memory pool owns the device and forbids allocations made
+ * behind its back, hosts whose device-memory budget is fixed at start-up, and control loops that
+ * cannot take the synchronisation of cudaMalloc / cudaFree.  The paper has no counterpart; this
+ * packages the same cycle kernel as sgml_solve_to_tol.
  *
  * Solves L u = f (L = div(sigma grad) + a_scalar, paper's sign) for ONE problem of dimension dim with
  * N = 2^n + 1 nodes per side from the lifted boundary values until ||r||_inf / ||f||_inf <= rtol or
  * max_cycles cycles, with the default method parameters (n_r = 2, theta = 0.7, consistent stencil).
  * f (N^dim doubles), sigma (N^dim doubles or NULL for 1) and u (N^dim doubles, written) are DEVICE
- * pointers owned by the caller; face_type / face_value (2*dim entries, face_value may be NULL) are
- * host arrays as in sgml_set_bc; a_scalar <= 0 (all-Neumann problems need a_scalar < 0 here: the
- * Eq. 10 projection is a grid-API feature).  cycles_out / rel_out (host, may be NULL) receive the
- * cycles run and the final relative residual.  Work runs on cuda_stream; the call synchronises it.
+ * pointers of the current device owned by the caller (anything else -- host memory, another GPU's
+ * memory -- is refused with SGML_ERR_ARG); face_type / face_value (2*dim entries, face_value may be
+ * NULL) are host arrays as in sgml_set_bc; a_scalar <= 0 (all-Neumann problems need a_scalar < 0
+ * here: the mean projection of all-Neumann problems is a grid-API feature).  cycles_out / rel_out
+ * (host, may be NULL) receive the cycles run and the final relative residual.  Work runs on
+ * cuda_stream; the call synchronises it and copies its small status back to the host.
  *
  * All intermediate data lives in one file-scope device array of 24 MiB that every GPU loading the
  * library holds until the process exits; problems needing more (e.g. beyond 65^3 in 3-D or 513^2
  * in 2-D) are rejected with SGML_ERR_ARG before any GPU work.  No cudaMalloc, cudaFree or other
  * allocating routine is called.  The first call on each device looks up the array's device
- * address (cudaGetSymbolAddress) with that device current: make that first call before any stream
- * capture begins.  Every call shares the array and clears what must start at zero; calls whose
- * work overlaps on the GPU (other streams, other host threads) race on it and must be serialised by
- * the caller.  Returns SGML_OK on convergence, else an sgml_status; the message is in
- * sgml_noalloc_last_error(). */
+ * address (cudaGetSymbolAddress) with that device current.  Every call shares the array and clears
+ * what must start at zero; calls whose work overlaps on the GPU (other streams, other host threads)
+ * race on it and must be serialised by the caller.  Returns SGML_OK on convergence, else an
+ * sgml_status; the message is in sgml_noalloc_last_error(). */
 int sgml_solve_noalloc(int dim, int n, int precision, const double* f, const double* sigma, double a_scalar,
                        const int* face_type, const double* face_value, double rtol, int max_cycles, double* u,
                        int* cycles_out, double* rel_out, void* cuda_stream);

@@ -41,14 +41,36 @@ class _Problem(ctypes.Structure):
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle into ``oracle/_build/liboracle.so`` (plain -O2, no fast-math)."""
+    """Compile the oracle into ``oracle/_build/liboracle.so`` (plain -O2, no fast-math, no FMA
+    contraction), with OpenMP for its per-node loops when the compiler offers it (results do not
+    depend on the thread count), else serial."""
     os.makedirs(_BUILD, exist_ok=True)
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-fno-fast-math",
-                               "-ffp-contract=off", "-o", tmp, _SRC, "-lm"])
+        base = ["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-fno-fast-math", "-ffp-contract=off", "-o", tmp, _SRC]
+        r = subprocess.run(base[:1] + ["-fopenmp"] + base[1:] + ["-lm"], capture_output=True, text=True)
+        if r.returncode != 0:
+            subprocess.check_call(base + ["-lm"])
         os.replace(tmp, _LIB)
     return _LIB
+
+
+def default_threads() -> int:
+    """Host threads the oracle uses unless told otherwise: ORACLE_THREADS, else every core in this
+    process's affinity mask."""
+    env = os.environ.get("ORACLE_THREADS")
+    if env:
+        return max(1, int(env))
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def set_threads(n: int) -> int:
+    """Use n host threads in the oracle's per-node loops (1 if it was built without OpenMP);
+    returns the count now in effect."""
+    return int(_load().orc_set_threads(int(n)))
 
 
 _lib = None
@@ -88,6 +110,9 @@ def _load():
         lib.orc_trapezoid.restype = ctypes.c_double
         lib.orc_neumann_gradient.argtypes = [I, I, D, D]
         lib.orc_grid_motion.argtypes = [I, I, D, D, ctypes.c_double, ctypes.c_double, I, D]
+        lib.orc_set_threads.argtypes = [I]
+        lib.orc_set_threads.restype = I
+        lib.orc_set_threads(default_threads())
         _lib = lib
     return _lib
 

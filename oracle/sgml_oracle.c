@@ -35,6 +35,31 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* Loops over nodes run on several host threads when the oracle is built with OpenMP: each node's
+ * value is computed by the same arithmetic whichever thread computes it, and the only reduction
+ * shared between threads is a maximum, so results do not depend on the thread count.  The two
+ * order-dependent sums (the trapezoid mean and integral) stay serial. */
+#ifdef _OPENMP
+#define ORC_PRAGMA(x) _Pragma(#x)
+#define ORC_PARALLEL_FOR ORC_PRAGMA(omp parallel for schedule(static))
+#else
+#define ORC_PARALLEL_FOR
+#endif
+
+/* Host threads used by the parallel loops (1 without OpenMP); n < 1 keeps the current count. */
+int orc_set_threads(int n) {
+#ifdef _OPENMP
+  if (n >= 1) omp_set_num_threads(n);
+  return omp_get_max_threads();
+#else
+  (void)n;
+  return 1;
+#endif
+}
 
 #define ORC_DIRICHLET 0
 #define ORC_NEUMANN 1
@@ -203,6 +228,7 @@ static double op_at(const orc_problem* p, int nu, const double* sig, const doubl
 void orc_apply_op(const orc_problem* p, int nu, const double* sig, const double* a, const double* u,
                   int with_flux, double* out) {
   long M = nnodes(p);
+  ORC_PARALLEL_FOR
   for (long i = 0; i < M; ++i) {
     int c[3];
     coords(p, i, c);
@@ -228,6 +254,7 @@ static void restrict_pass(const orc_problem* p, int m, const double* in, double*
   int lam = 1 << m;
   long M = nnodes(p);
   double norm = p->dim == 3 ? 1.0 / 8.0 : 1.0 / 4.0;
+  ORC_PARALLEL_FOR
   for (long i = 0; i < M; ++i) {
     int c[3];
     coords(p, i, c);
@@ -303,6 +330,7 @@ static double step_at(const orc_problem* p, int nu, const double* sig, const dou
 /* Local pseudo-time step at every level-nu unknown (0 elsewhere). */
 void orc_local_step(const orc_problem* p, int nu, const double* sig, const double* a, double* out) {
   long M = nnodes(p);
+  ORC_PARALLEL_FOR
   for (long i = 0; i < M; ++i) {
     int c[3];
     coords(p, i, c);
@@ -320,6 +348,7 @@ void orc_interpolate_add(const orc_problem* p, int nu, const double* delta, doub
   int N = npts(p);
   int s = 1 << nu;
   long M = nnodes(p);
+  ORC_PARALLEL_FOR
   for (long i = 0; i < M; ++i) {
     int x[3];
     coords(p, i, x);
@@ -361,6 +390,10 @@ void orc_visit(const orc_problem* p, int nu, int k, const double* r_nu, const do
   memcpy(saved, e, sizeof(double) * M);
   for (int sweep = 0; sweep < k; ++sweep) {
     memcpy(next, e, sizeof(double) * M);
+    double dmax = diag ? diag[nu] : 0.0;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static) reduction(max : dmax)
+#endif
     for (long i = 0; i < M; ++i) {
       int c[3];
       coords(p, i, c);
@@ -368,11 +401,13 @@ void orc_visit(const orc_problem* p, int nu, int k, const double* r_nu, const do
       double dtau = step_at(p, nu, sig_nu, a_nu, c);
       double pseudo = op_at(p, nu, sig_nu, a_nu, e, c, 0) - r_nu[i];
       next[i] = e[i] + dtau * pseudo;
-      if (diag && fabs(pseudo) > diag[nu]) diag[nu] = fabs(pseudo);
+      if (fabs(pseudo) > dmax) dmax = fabs(pseudo);
     }
+    if (diag) diag[nu] = dmax;
     memcpy(e, next, sizeof(double) * M);
   }
   if (nu > 0) {
+    ORC_PARALLEL_FOR
     for (long i = 0; i < M; ++i) {
       int c[3];
       coords(p, i, c);
@@ -469,6 +504,7 @@ static double dirichlet_value(const orc_problem* p, const int c[3]) {
 /* u = Dirichlet values on fixed nodes, 0 on unknowns. */
 void orc_lift(const orc_problem* p, double* u) {
   long M = nnodes(p);
+  ORC_PARALLEL_FOR
   for (long i = 0; i < M; ++i) {
     int c[3];
     coords(p, i, c);
@@ -480,6 +516,7 @@ void orc_lift(const orc_problem* p, double* u) {
  * nodes. */
 void orc_residual(const orc_problem* p, const double* u, const double* f, double* r) {
   long M = nnodes(p);
+  ORC_PARALLEL_FOR
   for (long i = 0; i < M; ++i) {
     int c[3];
     coords(p, i, c);
@@ -490,6 +527,7 @@ void orc_residual(const orc_problem* p, const double* u, const double* f, double
 /* r = f - delta L_0 u at the listed nodes only (flat indices), 0 at fixed nodes: the residual of
  * Sec. 2 evaluated one node at a time, for checks on grids too large for a full pass. */
 void orc_residual_at(const orc_problem* p, const double* u, const double* f, const long* idx, long count, double* r) {
+  ORC_PARALLEL_FOR
   for (long q = 0; q < count; ++q) {
     int c[3];
     coords(p, idx[q], c);
@@ -501,6 +539,9 @@ void orc_residual_at(const orc_problem* p, const double* u, const double* f, con
 double orc_max_norm(const orc_problem* p, const double* v) {
   long M = nnodes(p);
   double m = 0.0;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static) reduction(max : m)
+#endif
   for (long i = 0; i < M; ++i) {
     int c[3];
     coords(p, i, c);
@@ -576,6 +617,7 @@ int orc_solve(const orc_problem* p, const double* f_in, double tol, int max_cycl
     }
     if (c == max_cycles) break;
     orc_cycle(p, r, e);
+    ORC_PARALLEL_FOR
     for (long i = 0; i < M; ++i) u[i] += e[i];
     if (project) orc_project_mean(p, u);
   }
@@ -601,6 +643,7 @@ void orc_sigma_gradient(const orc_problem* p, const double* lambda, const double
   int o[26][3];
   int m = offsets(p->dim, o);
   double c0 = kappa(p) / (2.0 * h * h);
+  ORC_PARALLEL_FOR
   for (long i = 0; i < M; ++i) {
     int c[3];
     coords(p, i, c);
@@ -657,6 +700,7 @@ void orc_curl(int n, const double* psi, double* v) {
   const double* px = psi;
   const double* py = psi + M;
   const double* pz = psi + 2 * M;
+  ORC_PARALLEL_FOR
   for (int k = 0; k < N; ++k)
     for (int j = 0; j < N; ++j)
       for (int i = 0; i < N; ++i) {
@@ -706,6 +750,7 @@ static int orc_inside(const double x[3]) {
 void orc_streamlines(int n, const double* v, const double* seeds, int nseeds, double dt, int nsteps, double* paths,
                      int* lengths) {
   const int N = (1 << n) + 1;
+  ORC_PARALLEL_FOR
   for (int sd = 0; sd < nseeds; ++sd) {
     double x[3] = {seeds[3 * sd], seeds[3 * sd + 1], seeds[3 * sd + 2]};
     double* out = paths + (long)sd * (nsteps + 1) * 3;
@@ -780,6 +825,7 @@ void orc_neumann_gradient(int dim, int n, const double* u, double* g) {
   const double h = 1.0 / (double)(N - 1);
   long M = 1;
   for (int a = 0; a < dim; ++a) M *= N;
+  ORC_PARALLEL_FOR
   for (long i = 0; i < M; ++i) {
     int c[3] = {0, 0, 0};
     long r = i;
@@ -827,6 +873,7 @@ void orc_grid_motion(int dim, int n, const double* u, const double* f, double t0
   orc_neumann_gradient(dim, n, u, g);
   const double F = orc_trapezoid(dim, n, f);
   const double dt = nsteps > 0 ? (t1 - t0) / (double)nsteps : 0.0;
+  ORC_PARALLEL_FOR
   for (long i = 0; i < M; ++i) {
     double p[3] = {0.0, 0.0, 0.0};
     for (int a = 0; a < dim; ++a) p[a] = x[a * M + i] < 0.0 ? 0.0 : (x[a * M + i] > 1.0 ? 1.0 : x[a * M + i]);

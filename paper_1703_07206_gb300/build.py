@@ -24,6 +24,7 @@ UNITS = [
     ("sgml_api.cu", "api", []),
     ("sgml_noalloc.cu", "noalloc", []),
     ("sgml_post.cu", "post", []),
+    ("sgml_peaks.cu", "peaks", []),
 ]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

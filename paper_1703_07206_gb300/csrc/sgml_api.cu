@@ -74,6 +74,8 @@ struct sgml_grid {
   int pair_levels = 0;  // levels whose sweeps run in fused pairs (3-D mixed form only; off by default)
   int quad_levels = 0;  // levels whose sweeps run four rows per thread (3-D mixed form only; off by default)
   int mode = 0;  // 0: one persistent cooperative launch per call, 1: one launch per phase
+  unsigned long long timeout_ns = 2000000000ull;  // limit of every grid-barrier wait (2 s)
+  int withhold_barrier = 0;  // test aid: CTA 0 withholds its arrival at this barrier (0: never)
   bool dirty_coeffs = true, dirty_desc = true, dirty_phases = true, dirty_tiles = true, fresh = true;
   long long launches = 0;
   ProblemState* h_state = nullptr;  // pinned
@@ -84,6 +86,8 @@ struct sgml_grid {
   std::vector<char> f_checked;            // F's projection matches the current boundary conditions
   unsigned long long* d_diag = nullptr;   // diagnostic pseudo-residuals (sgml_set_diagnostics)
   int diag_cycles = 0;
+  double* d_scratch = nullptr;            // staging of host arrays for sgml_residual / sgml_sigma_gradient
+  long long scratch_cap = 0;              // ... its size in doubles (grown once, then reused)
   unsigned long long* d_trace = nullptr;  // per-phase timestamps (sgml_set_trace)
   int trace_cycles = 0;
   int trace_last_cycles = 0;
@@ -493,7 +497,8 @@ static int launch(sgml_grid* g, int max_cycles, double tol) {
   p.n_r = g->n_r;
   p.pair_levels = effective_pair_levels(g);
   p.sync = g->d_sync;
-  p.timeout_ns = 2000000000ull;  // 2 s per barrier wait
+  p.timeout_ns = g->timeout_ns;
+  p.withhold_barrier = g->withhold_barrier;
   p.hist = g->d_hist;
   p.hist_cap = g->hist_cap;
   p.trace = g->d_trace;
@@ -795,26 +800,77 @@ int sgml_get_history(sgml_grid_t g, int problem, double* hist, int cap, int* cou
   return SGML_OK;
 }
 
+// Device memory the kernels can read directly: a device (or managed) pointer of the grid's device.
+static bool device_resident(const sgml_grid* g, const void* ptr) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeManaged || (a.type == cudaMemoryTypeDevice && a.device == g->device);
+}
+
+// Grid-owned staging area of at least `count` doubles (allocated once per size increase).
+static int ensure_scratch(sgml_grid* g, long long count) {
+  if (count <= g->scratch_cap) return SGML_OK;
+  SGML_CUDA(cudaStreamSynchronize(g->stream));
+  if (g->d_scratch) SGML_CUDA(cudaFree(g->d_scratch));
+  g->d_scratch = nullptr;
+  g->scratch_cap = 0;
+  SGML_CUDA(cudaMalloc(&g->d_scratch, sizeof(double) * count));
+  g->scratch_cap = count;
+  return SGML_OK;
+}
+
+// Node arrays of the per-problem FP64 kernels: device arrays are used in place, host arrays are
+// staged through the grid's scratch (slot k of M doubles).
+struct Staged {
+  const double* in[2] = {nullptr, nullptr};
+  double* out = nullptr;
+  bool copy_out = false;
+};
+
+static int stage(sgml_grid* g, long long M, const double* a, const double* b, double* out, Staged& st) {
+  const double* src[2] = {a, b};
+  int need = 0;
+  bool dev[3];
+  for (int k = 0; k < 2; ++k) dev[k] = src[k] ? device_resident(g, src[k]) : true;
+  dev[2] = device_resident(g, out);
+  for (int k = 0; k < 3; ++k) need += dev[k] ? 0 : 1;
+  int st_ = ensure_scratch(g, need * M);
+  if (st_ != SGML_OK) return st_;
+  int slot = 0;
+  for (int k = 0; k < 2; ++k) {
+    if (!src[k] || dev[k]) {
+      st.in[k] = src[k];
+      continue;
+    }
+    double* d = g->d_scratch + (long long)(slot++) * M;
+    SGML_CUDA(cudaMemcpyAsync(d, src[k], sizeof(double) * M, cudaMemcpyDefault, g->stream));
+    st.in[k] = d;
+  }
+  st.out = dev[2] ? out : g->d_scratch + (long long)(slot++) * M;
+  st.copy_out = !dev[2];
+  return SGML_OK;
+}
+
 int sgml_residual(sgml_grid_t g, int problem, const double* u, double* r) {
   if (!valid(g)) return fail(SGML_ERR_ARG, "invalid grid");
   if (problem < 0 || problem >= g->batch || !u || !r) return fail(SGML_ERR_ARG, "bad arguments");
   int st;
   if ((st = project_sources(g)) != SGML_OK) return st;
   if (g->dirty_desc && (st = upload_desc(g)) != SGML_OK) return st;
+  if (r == u) return fail(SGML_ERR_ARG, "r must not alias u");
   const ProblemDesc& P = g->P[problem];
   const long long M = nodes(g->dim, P.n, 0);
-  double *du = nullptr, *dr = nullptr;
-  SGML_CUDA(cudaMalloc(&du, sizeof(double) * M));
-  SGML_CUDA(cudaMalloc(&dr, sizeof(double) * M));
-  SGML_CUDA(cudaMemcpyAsync(du, u, sizeof(double) * M, cudaMemcpyDefault, g->stream));
-  SGML_CUDA(launch_residual64(g->dim, P, du, g->F + P.off_full, g->SIG64 ? g->SIG64 + P.off_full : nullptr,
+  Staged sg;
+  if ((st = stage(g, M, u, nullptr, r, sg)) != SGML_OK) return st;
+  SGML_CUDA(launch_residual64(g->dim, P, sg.in[0], g->F + P.off_full, g->SIG64 ? g->SIG64 + P.off_full : nullptr,
                               g->A64 ? g->A64 + P.off_full : nullptr, kappa_of(g->dim, g->stencil), w_edge(),
-                              w_corner(), dr, g->stream));
+                              w_corner(), sg.out, g->stream));
   g->launches++;
-  SGML_CUDA(cudaMemcpyAsync(r, dr, sizeof(double) * M, cudaMemcpyDefault, g->stream));
+  if (sg.copy_out) SGML_CUDA(cudaMemcpyAsync(r, sg.out, sizeof(double) * M, cudaMemcpyDefault, g->stream));
   SGML_CUDA(cudaStreamSynchronize(g->stream));
-  SGML_CUDA(cudaFree(du));
-  SGML_CUDA(cudaFree(dr));
   return SGML_OK;
 }
 
@@ -825,19 +881,15 @@ int sgml_sigma_gradient(sgml_grid_t g, int problem, const double* lambda, const 
   for (int k = 0; k < 2 * g->dim; ++k)
     if (P.face_type[k] != SGML_DIRICHLET) return fail(SGML_ERR_ARG, "the sigma gradient needs all faces Dirichlet");
   const long long M = nodes(g->dim, P.n, 0);
-  double *dl = nullptr, *du = nullptr, *dg = nullptr;
-  SGML_CUDA(cudaMalloc(&dl, sizeof(double) * M));
-  SGML_CUDA(cudaMalloc(&du, sizeof(double) * M));
-  SGML_CUDA(cudaMalloc(&dg, sizeof(double) * M));
-  SGML_CUDA(cudaMemcpyAsync(dl, lambda, sizeof(double) * M, cudaMemcpyDefault, g->stream));
-  SGML_CUDA(cudaMemcpyAsync(du, u, sizeof(double) * M, cudaMemcpyDefault, g->stream));
-  SGML_CUDA(launch_sigma_gradient(g->dim, P, dl, du, kappa_of(g->dim, g->stencil), w_edge(), w_corner(), dg, g->stream));
+  if (grad == lambda || grad == u) return fail(SGML_ERR_ARG, "grad must not alias lambda or u");
+  Staged sg;
+  int st;
+  if ((st = stage(g, M, lambda, u, grad, sg)) != SGML_OK) return st;
+  SGML_CUDA(launch_sigma_gradient(g->dim, P, sg.in[0], sg.in[1], kappa_of(g->dim, g->stencil), w_edge(), w_corner(),
+                                  sg.out, g->stream));
   g->launches++;
-  SGML_CUDA(cudaMemcpyAsync(grad, dg, sizeof(double) * M, cudaMemcpyDefault, g->stream));
+  if (sg.copy_out) SGML_CUDA(cudaMemcpyAsync(grad, sg.out, sizeof(double) * M, cudaMemcpyDefault, g->stream));
   SGML_CUDA(cudaStreamSynchronize(g->stream));
-  SGML_CUDA(cudaFree(dl));
-  SGML_CUDA(cudaFree(du));
-  SGML_CUDA(cudaFree(dg));
   return SGML_OK;
 }
 
@@ -852,6 +904,15 @@ int sgml_set_launch(sgml_grid_t g, int ctas_per_sm, int z_waves, int mode, int t
   g->tile_x = tile_x;
   g->slab_z = slab_z;
   g->dirty_tiles = true;
+  return SGML_OK;
+}
+
+int sgml_set_barrier_test(sgml_grid_t g, double wait_limit_s, int withhold_barrier) {
+  if (!valid(g)) return fail(SGML_ERR_ARG, "invalid grid");
+  if (!(wait_limit_s >= 1e-4 && wait_limit_s <= 60.0) || withhold_barrier < 0)
+    return fail(SGML_ERR_ARG, "wait_limit_s must be in [1e-4, 60] and withhold_barrier >= 0");
+  g->timeout_ns = (unsigned long long)(wait_limit_s * 1e9);
+  g->withhold_barrier = withhold_barrier;
   return SGML_OK;
 }
 
@@ -977,7 +1038,7 @@ int sgml_destroy(sgml_grid_t g) {
   void* ptrs[] = {g->U, g->F, g->SIG64, g->A64, g->pyr64, g->RESP, g->A0, g->E, g->E2, g->B, g->R, g->SIG, g->Q,
                   g->d_probs, g->d_state, g->d_accum, g->d_sync, g->d_phases, g->d_rows, g->d_tasks,
                   g->d_task_off, g->d_tasks4, g->d_task_off4, g->d_hist, g->d_trace, g->d_diag,
-                  g->d_rowsum, g->d_umean, g->d_fmean};
+                  g->d_rowsum, g->d_umean, g->d_fmean, g->d_scratch};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (g->h_state) cudaFreeHost(g->h_state);

@@ -138,7 +138,8 @@ struct KernelParams {
   int n_r;
   int pair_levels;               // levels 0 .. pair_levels - 1 run their sweeps in fused pairs (kPair)
   GridSync* sync;
-  unsigned long long timeout_ns;
+  unsigned long long timeout_ns;  // limit of every grid-barrier wait
+  int withhold_barrier;          // test aid: CTA 0 withholds its arrival at this barrier (1-based; 0: never)
   double* hist;
   int hist_cap;
   double* rowsum;             // Eq. 10 projection: weighted level-0 row sums of u (row_prefix order)

@@ -178,17 +178,29 @@ __device__ __forceinline__ int ld_volatile(const int* p) { return *(const volati
 // every CTA returns from the kernel at its next barrier, so a fault in the schedule can never hang
 // the GPU.  Requires all CTAs to be co-resident (cooperative launch).
 // ---------------------------------------------------------------------------------------------
-__device__ bool grid_sync(GridSync* gs, unsigned long long timeout_ns) {
+// Test aid (KernelParams::withhold_barrier = k >= 1): CTA 0 withholds its arrival at the k-th
+// barrier of the launch, so that every CTA's bounded wait runs out and the launch ends with the
+// timeout status -- the error path is exercised without any fault.
+__shared__ int s_barriers;  // barriers this CTA has passed in the launch (counted only for the test aid)
+
+__device__ bool grid_sync(GridSync* gs, unsigned long long timeout_ns, int withhold_barrier) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
     int ok = 1;
     const unsigned long long G = gridDim.x;
     unsigned long long old;
-    // arrival: release (the CTA's writes, ordered before by the CTA barrier, become visible)
-    asm volatile("atom.add.release.gpu.u64 %0, [%1], 1;" : "=l"(old) : "l"(&gs->arrive) : "memory");
+    bool arrive = true;
+    if (withhold_barrier > 0 && blockIdx.x == 0) arrive = ++s_barriers != withhold_barrier;
+    if (arrive) {
+      // arrival: release (the CTA's writes, ordered before by the CTA barrier, become visible)
+      asm volatile("atom.add.release.gpu.u64 %0, [%1], 1;" : "=l"(old) : "l"(&gs->arrive) : "memory");
+    } else {
+      asm volatile("ld.relaxed.gpu.u64 %0, [%1];" : "=l"(old) : "l"(&gs->arrive) : "memory");
+      old = old / G * G;  // this round's target is never reached: the wait below runs out
+    }
     const unsigned long long target = (old / G + 1) * G;  // every CTA of this round has arrived
-    if (old + 1 < target) {  // the last CTA to arrive knows it from the returned value
+    if (old + 1 < target || !arrive) {  // the last CTA to arrive knows it from the returned value
       const unsigned long long t0 = globaltimer();
       unsigned spins = 0;
       for (;;) {
@@ -287,6 +299,7 @@ __device__ __forceinline__ float inv_scale_f_at(const KernelParams& p, int b, in
 
 __device__ void load_tables(const KernelParams& p) {
   if (threadIdx.x == 0) s_prob0 = p.probs[0];
+  if (threadIdx.x == 0) s_barriers = 0;
   if (threadIdx.x < kMaxLevels) s_diag0[threadIdx.x] = 0ull;
   if (threadIdx.x < kMaxLevels) s_rows[threadIdx.x] = p.row_prefix[(long long)threadIdx.x * (p.batch + 1) + p.batch];
   for (int i = threadIdx.x; i < p.nphases && i < kPhaseCache; i += blockDim.x) s_phase[i] = p.phases[i];
@@ -1089,8 +1102,9 @@ __device__ void phase_check(const KernelParams& p, int c) {
     S.scale_used[c & 1] = cast_scale(p, b, c);
     S.inv_scale[c & 1] = 1.0 / S.scale_used[c & 1];
     S.inv_scale_f[c & 1] = (float)S.inv_scale[c & 1];
-    const double rel = S.fnorm > 0.0 ? rmax / S.fnorm : 0.0;
-    const double rel2 = S.fnorm2 > 0.0 ? sqrt(rs2) / S.fnorm2 : 0.0;
+    // (a NaN norm must stay NaN: it ends the solve with SGML_ERR_NONFINITE below, not as converged)
+    const double rel = S.fnorm > 0.0 ? rmax / S.fnorm : (S.fnorm == 0.0 ? 0.0 : S.fnorm + rmax);
+    const double rel2 = S.fnorm2 > 0.0 ? sqrt(rs2) / S.fnorm2 : (S.fnorm2 == 0.0 ? 0.0 : S.fnorm2 + rs2);
     S.rel = rel;
     S.rel_l2 = rel2;
     if (c < p.hist_cap) p.hist[(long long)b * p.hist_cap + c] = rel;
@@ -2289,7 +2303,7 @@ __global__ void __launch_bounds__(kThreads, SGML_MIN_CTAS) cycle_kernel(const Ke
   load_done(p);
   if (p.fresh) {
     phase_lift<T, DIM>(p);
-    if (!grid_sync(p.sync, p.timeout_ns)) return;
+    if (!grid_sync(p.sync, p.timeout_ns, p.withhold_barrier)) return;
   }
   // Optional trace: CTA 0 stamps the global timer after every barrier of the first cycles.
   auto stamp = [&](int c, int slot) {
@@ -2299,17 +2313,17 @@ __global__ void __launch_bounds__(kThreads, SGML_MIN_CTAS) cycle_kernel(const Ke
   for (int c = 0;; ++c) {
     stamp(c, 0);
     phase_outer<T, DIM>(p, c, sm);
-    if (!grid_sync(p.sync, p.timeout_ns)) return;
+    if (!grid_sync(p.sync, p.timeout_ns, p.withhold_barrier)) return;
     stamp(c, 1);
     if (blockIdx.x == 0) phase_check<T, DIM>(p, c);
-    if (!grid_sync(p.sync, p.timeout_ns)) return;
+    if (!grid_sync(p.sync, p.timeout_ns, p.withhold_barrier)) return;
     stamp(c, 2);
     if (!ld_volatile(&p.sync->active[c & 1])) break;
     load_done(p);
     for (int q = 0; q < p.nphases; ++q) {
       const Phase ph = phase_at(p, q);
       run_phase<T, DIM>(p, ph, c, sm);
-      if (!grid_sync(p.sync, p.timeout_ns)) return;
+      if (!grid_sync(p.sync, p.timeout_ns, p.withhold_barrier)) return;
       stamp(c, 3 + q);
     }
     if (p.diag) diag_commit(p, c);

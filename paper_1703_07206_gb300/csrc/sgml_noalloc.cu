@@ -1,13 +1,14 @@
 // sgml_noalloc.cu -- sgml_solve_noalloc: a solve that allocates no memory.
 //
-// Some callers cannot allocate device memory at the point where they want a solve: code running
-// while a CUDA stream is being captured into a graph (where cudaMalloc is not allowed), allocators
-// or memory pools that forbid foreign allocations, and embedded hosts whose device memory budget is
-// fixed at start-up.  This entry point serves them: the caller passes device pointers for the inputs
-// and the output, and every intermediate array (the level pyramid, the residual accumulator, the
-// schedule tables, the per-problem state and the barrier words) lives in one file-scope
-// `__device__` array of kNoAllocBytes bytes.  Every GPU that loads the library holds that array
-// until the process exits.
+// Some callers cannot allocate device memory at the point where they want a solve: frameworks whose
+// memory pool owns the whole device and forbids allocations made behind its back, embedded or
+// real-time hosts whose device-memory budget is fixed at start-up (and which cannot afford the
+// implicit synchronisation of cudaMalloc / cudaFree inside a control loop), and services that must
+// not fail for lack of memory once they are running.  This entry point serves them: the caller
+// passes device pointers for the inputs and the output, and every intermediate array (the level
+// pyramid, the residual accumulator, the schedule tables, the per-problem state and the barrier
+// words) lives in one file-scope `__device__` array of kNoAllocBytes bytes.  Every GPU that loads
+// the library holds that array until the process exits.
 //
 // The paper has no counterpart: this is a packaging of the same cycle kernel (Algorithms 1-3) for
 // callers without an allocator.
@@ -43,10 +44,11 @@ int fail(int code, const char* msg) {
   return code;
 }
 
-// Device address of g_scratch on each device, looked up once with that device current.
+// Device address of g_scratch on each device, looked up once with that device current.  Read and
+// written only with g_table_mutex held.
 unsigned char* g_scratch_addr[kMaxDevices] = {nullptr};
 
-int scratch_address(unsigned char** out) {
+int scratch_address(unsigned char** out) {  // caller holds g_table_mutex
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return fail(SGML_ERR_CUDA, "no current device");
   if (!g_scratch_addr[dev]) {
@@ -70,6 +72,19 @@ long long nodes(int dim, int n, int l) {
   return dim == 3 ? N * N * N : N * N;
 }
 size_t align256(size_t x) { return (x + 255) / 256 * 256; }
+
+// The kernel dereferences f, sigma and u directly: each must be device (or managed) memory that the
+// current device can address.  A host pointer, or memory of another GPU, is refused instead of
+// becoming a stray device access.
+bool on_current_device(const void* ptr, int dev) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+    cudaGetLastError();  // clear the sticky-free error of an unregistered host pointer
+    return false;
+  }
+  if (a.type == cudaMemoryTypeManaged) return true;
+  return a.type == cudaMemoryTypeDevice && a.device == dev;
+}
 
 // Bump layout inside the scratch array.
 struct Bump {
@@ -141,6 +156,13 @@ extern "C" int sgml_solve_noalloc(int dim, int n, int precision, const double* f
   if (bump.used > kNoAllocBytes)
     return fail(SGML_ERR_ARG, "problem too large for the no-alloc scratch (24 MiB: e.g. 65^3 or 513^2 in either precision)");
 
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return fail(SGML_ERR_CUDA, "no current device");
+  if (!on_current_device(f, dev) || !on_current_device(u, dev) || (sigma && !on_current_device(sigma, dev)))
+    return fail(SGML_ERR_ARG, "f, sigma and u must be device memory of the current device");
+
+  // the scratch address table and the static partition tables below are shared by all host threads
+  std::lock_guard<std::mutex> lock(g_table_mutex);
   unsigned char* base = nullptr;
   int st = scratch_address(&base);
   if (st != SGML_OK) return st;
@@ -149,9 +171,8 @@ extern "C" int sgml_solve_noalloc(int dim, int n, int precision, const double* f
   int bps = 0;
   if (sgml_t64::cycle_kernel_occupancy(mixed ? 1 : 0, dim, kThreads, &bps) != 0 || bps < 1)
     return fail(SGML_ERR_CUDA, "occupancy query failed");
-  int dev = 0, sms = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return fail(SGML_ERR_CUDA, "multiprocessor count query failed");
   const int blocks = sms * bps;
 
   long long rows[kMaxLevels * 2];
@@ -160,10 +181,10 @@ extern "C" int sgml_solve_noalloc(int dim, int n, int precision, const double* f
     const long long N = side(n, std::min(l, n - 1));
     rows[2 * l + 1] = l <= n - 1 ? (dim == 3 ? N * N : N) : 0;
   }
-  // partition tables in static host storage (no allocation); the mutex serialises their use
+  // partition tables in static host storage (no allocation); the mutex taken above serialises
+  // their use
   static TileTask tasks[kMaxTasks];
   static int toff[kMaxToff];
-  std::lock_guard<std::mutex> lock(g_table_mutex);
   constexpr int kTX = 64, kTY = 2 * kThreads / 64;  // the 64 x 8 tile kernels
   if (blocks > 1024 || partition_bound(dim, &n, 1, blocks, kTX, kTY) > kMaxTasks)
     return fail(SGML_ERR_ARG, "problem too large for the no-alloc task table");

@@ -136,13 +136,14 @@ def helmholtz_batch_2d(count=256, seed=4000, exponents=(6, 7, 8, 9, 10)):
         rng = np.random.default_rng(seed + b)
         n = int(rng.choice(np.asarray(exponents)))
         k2 = float(rng.uniform(0.0, 10.0))
-        X, Y = _axes(n, 2)
-        f = np.zeros_like(X)
+        x = np.linspace(0.0, 1.0, 2 ** n + 1)
+        f = np.zeros((x.size, x.size))
         for _ in range(16):
             amp = rng.normal()
             p_, q_ = rng.integers(1, 9, size=2)
             phi, psi = rng.uniform(0, 2 * np.pi, size=2)
-            f += amp * np.sin(np.pi * p_ * X + phi) * np.sin(np.pi * q_ * Y + psi)
+            # separable mode, same products in the same order as amp * sin(.. X ..) * sin(.. Y ..)
+            f += (amp * np.sin(np.pi * p_ * x + phi))[None, :] * np.sin(np.pi * q_ * x + psi)[:, None]
         faces = [DIRICHLET if rng.uniform() < 0.5 else NEUMANN for _ in range(4)]
         if all(t == NEUMANN for t in faces) and k2 < 0.1:
             faces[0] = DIRICHLET

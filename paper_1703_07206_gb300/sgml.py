@@ -54,6 +54,7 @@ _SIGNATURES = {
     "sgml_residual": [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p],
     "sgml_sigma_gradient": [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
     "sgml_set_fusion": [ctypes.c_void_p, ctypes.c_int],
+    "sgml_set_barrier_test": [ctypes.c_void_p, ctypes.c_double, ctypes.c_int],
     "sgml_set_diagnostics": [ctypes.c_void_p, ctypes.c_int],
     "sgml_get_diagnostics": [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.c_int,
                              ctypes.POINTER(ctypes.c_int)],
@@ -79,6 +80,7 @@ _SIGNATURES = {
     "sgml_grid_motion": [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double,
                          ctypes.c_double, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p],
     "sgml_post_last_error": [],
+    "sgml_measure_fma_rates": [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)],
 }
 
 
@@ -240,6 +242,11 @@ class Grid:
         _check(load().sgml_sigma_gradient(self._h, problem, _addr(lam, m), _addr(u, m), _addr(out, m)))
         return out
 
+    def set_barrier_test(self, wait_limit_s=2.0, withhold_barrier=0):
+        """Limit of every grid-barrier wait in seconds; withhold_barrier >= 1 makes CTA 0 withhold its
+        arrival at that barrier of every launch (a test aid for the timeout status; 0: off)."""
+        _check(load().sgml_set_barrier_test(self._h, float(wait_limit_s), int(withhold_barrier)))
+
     def set_fusion(self, pair_levels=0):
         """Levels 0 .. pair_levels - 1 run their sweeps in fused pairs (3-D mixed form; 0: off)."""
         _check(load().sgml_set_fusion(self._h, pair_levels))
@@ -303,8 +310,16 @@ class Grid:
 
 def solve_noalloc(dim, n, f, u, sigma=None, a_scalar=0.0, faces=None, values=None, rtol=1e-10, max_cycles=200,
                   precision=MIXED, stream=None):
-    """sgml_solve_noalloc: one solve with no allocation; f, sigma, u are CUDA tensors (float64).
-    Returns (status, cycles, relative residual); raises on argument / CUDA errors."""
+    """sgml_solve_noalloc: one solve that allocates no device memory, for callers that cannot
+    allocate where they solve.  f, sigma (or None) and u are float64 CUDA tensors on the current
+    device.  Returns (status, cycles, relative residual); raises on argument / CUDA errors."""
+    import torch
+    dev = torch.cuda.current_device()
+    for name, t in (("f", f), ("u", u), ("sigma", sigma)):
+        if t is None and name == "sigma":
+            continue
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.device.index == dev):
+            raise TypeError(f"{name} must be a CUDA tensor on the current device (cuda:{dev})")
     lib = load()
     faces = list(faces) if faces is not None else [DIRICHLET] * (2 * dim)
     ft = (ctypes.c_int * 6)(*(faces + [0] * (6 - len(faces))))
@@ -402,6 +417,15 @@ def grid_motion(u, f, nsteps, t0=0.0, t1=1.0, x=None, stream=None):
     if st != OK:
         raise SGMLError(st, lib.sgml_post_last_error().decode())
     return x
+
+
+def measure_fma_rates(stream=None):
+    """Measured (FP64, FP32) FMA instructions per second of the current GPU (thread level)."""
+    a, b = ctypes.c_double(), ctypes.c_double()
+    st = load().sgml_measure_fma_rates(_stream_ptr(stream), ctypes.byref(a), ctypes.byref(b))
+    if st != OK:
+        raise SGMLError(st, "sgml_measure_fma_rates failed")
+    return a.value, b.value
 
 
 def problem_into_grid(grid, b, prob):

@@ -1,7 +1,7 @@
 // Host-side check of the tiled phases' work partition (sgml_tasks.h): for every level, the tasks of
 // all CTAs cover every (problem, tile, plane) that holds an unknown exactly once, stay within the
 // bound the allocation uses, and give the CTAs equal shares.  Prints one line per case:
-//   dim n_list G tile_x slab ok max_share_over_mean_level0
+//   dim n_list G tile_x slab ok max_share_over_mean_level0 longest_level0_piece
 #include <cstdio>
 #include <cstdlib>
 #include <map>
@@ -23,6 +23,8 @@ static void run(int dim, std::vector<int> nb, int G, int tx, int slab) {
   const int nt = build_partition(dim, nb.data(), dir_hi.data(), batch, G, tx, ty, t.data(), off.data(), slab);
   bool ok = nt <= bound;
   double share0 = 0.0;
+  int maxnz0 = 0;
+  for (int k = off[0]; k < off[G]; ++k) maxnz0 = std::max<int>(maxnz0, t[k].nz);
   for (int l = 0; l < kMaxLevels; ++l) {
     const int* o = off.data() + (size_t)l * (G + 1);
     std::map<std::tuple<int, int, int, int>, int> cover;
@@ -56,7 +58,7 @@ static void run(int dim, std::vector<int> nb, int G, int tx, int slab) {
   }
   std::printf("%d ", dim);
   for (int b = 0; b < batch; ++b) std::printf("%s%d", b ? "," : "", nb[b]);
-  std::printf(" %d %d %d %d %.4f\n", G, tx, slab, ok ? 1 : 0, share0);
+  std::printf(" %d %d %d %d %.4f %d\n", G, tx, slab, ok ? 1 : 0, share0, maxnz0);
 }
 
 int main() {

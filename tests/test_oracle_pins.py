@@ -255,6 +255,103 @@ def test_local_step_equals_theta_times_bound(dim):
     assert np.allclose(dt[m], theta * p.h ** 2 / (2 * sig[m]), rtol=1e-14)
 
 
+def level_operator_diagonal(p, nu, sig_nu, a_nu):
+    """Diagonal of the level-nu operator delta L_nu on the level-nu unknowns, read off the operator
+    itself (apply_op, pinned above by exactness and eigenvalue tests): the column of node i is
+    delta L_nu applied to the unit vector at i.  Columns of nodes that are three or more level-nu
+    cells apart in every coordinate have disjoint supports (the stencil and its even images reach
+    one level-nu cell), so one probe vector per colour class (index mod 3 per axis) gives every
+    diagonal entry exactly."""
+    s = 2 ** nu
+    idx = [np.arange(p.N) for _ in range(p.dim)]
+    coarse = [np.where(i % s == 0, i // s, -1) for i in idx]
+    diag = np.zeros(p.shape)
+    m = p.unknown_mask() & level_mask(p.shape, nu)
+    for colour in np.ndindex(*([3] * p.dim)):
+        e = np.ones(p.shape, dtype=bool)
+        for ax in range(p.dim):  # array axis ax holds coordinate dim - 1 - ax
+            c = coarse[ax]
+            sel = (c >= 0) & (c % 3 == colour[ax])
+            sh = [1] * p.dim
+            sh[ax] = p.N
+            e &= sel.reshape(sh)
+        probe = e.astype(float)
+        col = p.apply_op(probe, nu=nu, sig=sig_nu, a=a_nu)
+        diag[e & m] = col[e & m]
+    return diag, m
+
+
+def brute_force_diagonal(p, nu, sig_nu, a_nu):
+    """The same diagonal, one unit column at a time (small grids only)."""
+    diag = np.zeros(p.shape)
+    m = p.unknown_mask() & level_mask(p.shape, nu)
+    for flat in np.flatnonzero(m):
+        e = np.zeros(p.shape)
+        e.ravel()[flat] = 1.0
+        diag.ravel()[flat] = p.apply_op(e, nu=nu, sig=sig_nu, a=a_nu).ravel()[flat]
+    return diag
+
+
+@pytest.mark.parametrize("dim,n,seed", [(2, 5, 41), (2, 4, 42), (3, 3, 43), (3, 4, 44)])
+def test_local_step_is_jacobi_scaled_by_assembled_diagonal(dim, n, seed):
+    """Sec. 2 stability bound and Sec. 3.4 local step, Jacobi-scaled reading: at every level nu the
+    oracle's pseudo-time step is theta (kappa_d S_d / 2) / D_i with D_i = -(delta L_nu)_ii, the
+    operator built with the level-nu (tent-restricted) sigma and a.  Heterogeneous sigma, per-node
+    a <= 0 and mixed Dirichlet / Neumann faces: a dropped or flipped -a, a wrong sigma average or a
+    sigma taken from the wrong level changes D_i and fails here."""
+    facts = golden_facts()
+    d = inputs.random_problem(dim, n, seed, hetero=True, helmholtz=True, mixed_bc=True)
+    faces = list(d["faces"])
+    if NEUMANN not in faces:
+        faces[1] = NEUMANN
+    if DIRICHLET not in faces:
+        faces[0] = DIRICHLET
+    theta = 0.7
+    p = Problem(dim, n, faces=faces, sigma=d["sigma"], a=d["a"], theta=theta)
+    w = [1.0 / facts["eq5_l_face"], 1.0 / facts["eq5_l_edge"], 1.0 / facts["eq5_l_corner"]]
+    counts = [4, 4, 0] if dim == 2 else [6, 12, 8]  # face, edge, corner neighbours
+    S = sum(c * wk for c, wk in zip(counts, w))
+    gain = consistent_kappa(dim) * S / 2.0  # sqrt(2) in 2-D
+    if dim == 2:
+        assert abs(gain - math.sqrt(2)) < 1e-15  # (sqrt 2 - 1)(4 + 2 sqrt 2) / 2 = sqrt 2
+    for nu in range(0, n):
+        sig_nu = tent_restriction(d["sigma"], nu)
+        a_nu = tent_restriction(d["a"], nu)
+        diag, m = level_operator_diagonal(p, nu, sig_nu, a_nu)
+        if m.sum() <= 64:
+            assert np.array_equal(diag[m], brute_force_diagonal(p, nu, sig_nu, a_nu)[m])
+        D = -diag[m]
+        assert np.all(D > 0)
+        dt = p.local_step(nu)
+        np.testing.assert_allclose(dt[m], theta * gain / D, rtol=1e-12, atol=0)
+        assert np.all(dt[~m] == 0.0)
+
+
+def test_local_step_pin_fails_on_planted_mistakes():
+    """The pin above is sharp: a step built from a flipped -a, from sigma_i alone instead of the
+    link average, or from level-0 coefficients at a coarse level departs from the oracle's step by
+    far more than its tolerance."""
+    d = inputs.random_problem(3, 3, 45, hetero=True, helmholtz=True, mixed_bc=True)
+    p = Problem(3, 3, faces=d["faces"], sigma=d["sigma"], a=d["a"])
+    gain = consistent_kappa(3) * (6 + 12 / math.sqrt(2) + 8 / math.sqrt(3)) / 2.0
+    for nu in (0, 1):
+        sig_nu, a_nu = tent_restriction(d["sigma"], nu), tent_restriction(d["a"], nu)
+        diag, m = level_operator_diagonal(p, nu, sig_nu, a_nu)
+        dt = p.local_step(nu)[m]
+        good = 0.7 * gain / -diag[m]
+        assert np.abs(dt / good - 1).max() < 1e-12
+        plus_a = 0.7 * gain / (-diag[m] + 2 * a_nu[m])   # -a flipped to +a
+        assert np.abs(dt / plus_a - 1).max() > 1e-3
+        H = 2 ** nu * p.h
+        k = consistent_kappa(3)
+        sigma_i = 0.7 * gain / (k / H ** 2 * sig_nu[m] * (6 + 12 / math.sqrt(2) + 8 / math.sqrt(3)) - a_nu[m])
+        assert np.abs(dt / sigma_i - 1).max() > 1e-3
+        if nu == 1:
+            diag0, _ = level_operator_diagonal(p, nu, d["sigma"], d["a"])  # level-0 coefficients
+            wrong_level = 0.7 * gain / -diag0[m]
+            assert np.abs(dt / wrong_level - 1).max() > 1e-3
+
+
 # --------------------------------------------------------------------------------------------
 # Interpolation (Sec. 2, Algorithm 2): multilinear reproduction and nesting
 # --------------------------------------------------------------------------------------------

@@ -39,8 +39,9 @@ def results(tmp_path_factory):
     out = subprocess.check_output([exe], text=True)
     rows = []
     for line in out.strip().splitlines():
-        dim, ns, G, tx, slab, ok, share = line.split()
-        rows.append(dict(dim=int(dim), ns=ns, G=int(G), tx=int(tx), slab=int(slab), ok=int(ok), share=float(share)))
+        dim, ns, G, tx, slab, ok, share, maxnz0 = line.split()
+        rows.append(dict(dim=int(dim), ns=ns, G=int(G), tx=int(tx), slab=int(slab), ok=int(ok), share=float(share),
+                         maxnz0=int(maxnz0)))
     return rows
 
 
@@ -55,3 +56,13 @@ def test_level0_shares_are_balanced(results):
         if r["ns"] in ("8", "7,7,7,7,7,7,7,7,7,7,7,7,7,7,7,7") or (r["dim"] == 2 and r["ns"] == "10"):
             # large levels: within one slab (or one tile-plane) of the mean
             assert r["share"] <= 1.12, r
+
+
+def test_slab_cut_reaches_level0_where_the_parity_tests_need_it(results):
+    """129^3 on 304 CTAs: a slab height of 4 puts level 0 on the slab cut (pieces of at most
+    3/2 x 4 planes, dealt in turn), the contiguous cut gives runs of ~13.6 planes.  The GPU parity
+    tests of the headline recipe rely on this to compare the slab path with the oracle."""
+    for tx in (32, 64):
+        slab = [r for r in results if r["dim"] == 3 and r["ns"] == "7" and r["tx"] == tx and r["slab"] == 4][0]
+        runs = [r for r in results if r["dim"] == 3 and r["ns"] == "7" and r["tx"] == tx and r["slab"] == 0][0]
+        assert slab["maxnz0"] <= 6 < runs["maxnz0"], (slab, runs)

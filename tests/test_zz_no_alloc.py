@@ -1,7 +1,8 @@
-"""sgml_solve_noalloc, the entry point for callers that cannot allocate device memory (e.g. code
-running during CUDA-graph stream capture, or under an allocator that forbids foreign allocations):
-its scratch is a fixed device array inside the library.  It must give the same solution as the
-ordinary grid API, call after call (the shared scratch keeps the previous call's contents).
+"""sgml_solve_noalloc, the entry point for callers that cannot allocate device memory where they
+solve (a memory pool that owns the device and forbids foreign allocations, a device-memory budget
+fixed at start-up, a control loop that cannot take cudaMalloc's synchronisation): its scratch is a
+fixed device array inside the library.  It must give the same solution as the ordinary grid API,
+call after call (the shared scratch keeps the previous call's contents).
 
 Collected last on purpose, so that a run stopping at the first failure has run everything else."""
 import numpy as np
@@ -54,3 +55,21 @@ def test_noalloc_rejects_sizes_beyond_its_scratch():
                                 None, None, None)
     assert st == sgml.ERR_ARG
     assert b"too large" in lib.sgml_noalloc_last_error()
+
+
+def test_noalloc_refuses_host_memory():
+    """f and u in host memory are refused by the library's own pointer check, before any GPU work
+    (the binding refuses them too; the C entry point is called directly here)."""
+    import ctypes
+    import torch
+    lib = sgml.load()
+    N = 2 ** 3 + 1
+    f_host = np.zeros(N * N)
+    u_dev = torch.zeros(N * N, dtype=torch.float64, device="cuda")
+    faces = (ctypes.c_int * 6)(*([sgml.DIRICHLET] * 6))
+    st = lib.sgml_solve_noalloc(2, 3, sgml.MIXED, f_host.ctypes.data, None, 0.0, faces, None, 1e-10, 50,
+                                u_dev.data_ptr(), None, None, None)
+    assert st == sgml.ERR_ARG
+    assert b"device memory" in lib.sgml_noalloc_last_error()
+    with pytest.raises(TypeError):
+        sgml.solve_noalloc(2, 3, torch.from_numpy(f_host), u_dev)
