@@ -33,6 +33,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "solved nodes/s to rel. residual 1e-10 (mixed vs FP64 form), % of HBM roofline"
 TOL = 1e-10
+ACC_TOL = 5e-12  # residual tolerance at which the 257^3 solutions are within 1e-10 (relative L2) of the reference
 # Algorithmic HBM bytes per fine node per cycle of the schedule (3-D, heterogeneous eps): one DRAM
 # pass per phase, n_r = 2, zig-zag, 8 level-0 sweeps (outer step 24 + 2b + 8, level-0 sweeps
 # 8 (3b + b), coarse levels (18b + 6b) / 7, b = bytes of the cycle precision).
@@ -174,51 +175,78 @@ def whole_job_rate(world, nodes_per_replica, ms_per_step):
 
 
 # ------------------------------------------------------------------------------------------------
-# CPU oracle sample (the cpu_baseline leg and the reference arm)
+# CPU oracle (the cpu_baseline leg and the reference arm): measured full solves, never tuned
 # ------------------------------------------------------------------------------------------------
-def oracle_seconds_per_node_cycle(n_sample, cycles):
-    """Time `cycles` outer steps + cycles of the FP64 CPU oracle on the n_sample instance of the
-    workload recipe (single thread).  Returns seconds per node per cycle."""
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def oracle_solve(n_sample, threads, tol=TOL, max_cycles=1000):
+    """One full FP64 oracle solve of the n_sample instance of the workload recipe to `tol` on
+    `threads` host threads.  Returns (seconds, cycles, solution, threads used)."""
+    from oracle import oracle
     from oracle.oracle import Problem
     from paper_1703_07206_gb300 import inputs
+    used = oracle.set_threads(threads)
     d = inputs.dielectric_spheres_3d(n=n_sample, seed=2000)
     p = Problem(3, n_sample, sigma=d["sigma"])
-    u = p.lift()
     t0 = time.perf_counter()
-    for _ in range(cycles):
-        r = p.residual(u, d["f"])
-        u = u + p.cycle(r)
+    u, cycles, _ = p.solve(d["f"], tol=tol, max_cycles=max_cycles)
     dt = time.perf_counter() - t0
-    return dt / (cycles * (2 ** n_sample + 1) ** 3), dt
+    return dt, cycles, u, used
 
 
 def run_reference(args):
+    """The oracle as it stands, on the machine's host cores: every step one full solve of the 33^3
+    instance of the workload recipe to the tolerance (a bounded sample of the 257^3 workload: same
+    recipe, 1/512 of its nodes, ~3/5 of its cycles)."""
     world, rank, _ = dist_env()
     if rank != 0:
         return
-    K_cycles = args.ref_cycles
-    n_s = 6
+    n_s = args.ref_n
     M_s = (2 ** n_s + 1) ** 3
+    cores = host_cores()
     for _ in range(args.warmup):
-        oracle_seconds_per_node_cycle(n_s, 1)
-    per, total = [], 0.0
+        oracle_solve(n_s, cores)
+    per, cycles, used = [], 0, cores
     for _ in range(args.steps):
-        s, dt = oracle_seconds_per_node_cycle(n_s, 1)
-        per.append(s)
-        total += dt
-    s = float(np.median(per))
-    value = 1.0 / (s * K_cycles)
+        dt, cycles, _, used = oracle_solve(n_s, cores)
+        per.append(dt)
+    ms = float(np.mean(per)) * 1e3
+    value = M_s / (ms / 1e3)
     line = {"metric": METRIC, "value": value, "unit": "nodes/s", "n_gpus": args.gpus, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": total / args.steps * 1e3, "higher_is_better": True,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
             "config": {"workload": workload_name(args.n), "form": "fp64 CPU oracle"},
-            "cpu_baseline": {"value": value, "unit": "nodes/s", "cores": 1, "kind": "oracle",
-                             "sample": f"each step: one outer step + one cycle of the oracle on the "
-                                       f"{2 ** n_s + 1}^3 instance of the recipe ({M_s} nodes), scaled by "
-                                       f"{K_cycles} cycles to tolerance (the cycle count of the {2 ** args.n + 1}^3 "
-                                       f"FP64 solve)"},
+            "cpu_baseline": {"value": value, "unit": "nodes/s", "cores": used, "kind": "oracle",
+                             "sample": f"each step one full solve of the {2 ** n_s + 1}^3 instance of the recipe "
+                                       f"({M_s} nodes) to rel. residual {TOL:g}: {cycles} cycles, "
+                                       f"{ms / 1e3:.1f} s on {used} threads"},
             "e2e": {"value": value, "unit": "nodes/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def cpu_baseline_leg(args):
+    """The oracle timed on full solves to the tolerance: the 65^3 instance on every core of the
+    affinity mask (the value) and the 33^3 instance on one thread.  Returns (cpu_baseline dict,
+    the 65^3 oracle solution for the accuracy comparison)."""
+    cores = host_cores()
+    dt_all, cyc_all, u_all, used = oracle_solve(args.cpu_n, cores)
+    M_all = (2 ** args.cpu_n + 1) ** 3
+    dt_one, cyc_one, _, _ = oracle_solve(args.cpu_n - 1, 1)
+    M_one = (2 ** (args.cpu_n - 1) + 1) ** 3
+    from oracle import oracle
+    oracle.set_threads(cores)
+    cpu = {"value": M_all / dt_all, "unit": "nodes/s", "cores": used, "kind": "oracle",
+           "sample": f"one full solve of the {2 ** args.cpu_n + 1}^3 instance of the recipe to rel. residual "
+                     f"{TOL:g}: {cyc_all} cycles, {dt_all:.1f} s on {used} threads",
+           "single_thread": {"value": M_one / dt_one, "unit": "nodes/s", "cores": 1,
+                             "sample": f"one full solve of the {2 ** (args.cpu_n - 1) + 1}^3 instance to "
+                                       f"{TOL:g}: {cyc_one} cycles, {dt_one:.1f} s"}}
+    return cpu, u_all
 
 
 # ------------------------------------------------------------------------------------------------
@@ -234,11 +262,12 @@ def make_grid(d, precision, stream):
     return g
 
 
-def time_solves(torch, g, stream, steps, warmup):
-    """Warm-up, then time `steps` solves with CUDA events on the grid's stream."""
+def time_solves(torch, g, stream, steps, warmup, tol=TOL):
+    """Warm-up, then time `steps` solves with CUDA events on the grid's stream.  Returns (total ms,
+    mean ms per solve, cycles (largest of the batch), relative residual (largest), launches)."""
     from paper_1703_07206_gb300 import sgml
     for _ in range(warmup):
-        st, cyc, rel = g.solve_to_tol(TOL)
+        st, cyc, rel = g.solve_to_tol(tol)
         if st != sgml.OK:
             raise RuntimeError(f"solve failed: status {st}, cycles {cyc}, rel {rel}")
     launches0 = g.launch_count()
@@ -249,7 +278,7 @@ def time_solves(torch, g, stream, steps, warmup):
     for _ in range(steps):
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        st, cyc, rel = g.solve_to_tol(TOL)
+        st, cyc, rel = g.solve_to_tol(tol)
         b.record(stream)
         per.append((a, b))
         if st != sgml.OK:
@@ -258,7 +287,18 @@ def time_solves(torch, g, stream, steps, warmup):
     torch.cuda.synchronize()
     total_ms = e0.elapsed_time(e1)
     kernel_ms = float(np.mean([a.elapsed_time(b) for a, b in per]))
-    return total_ms, kernel_ms, int(cyc[0]), float(rel[0]), g.launch_count() - launches0
+    return total_ms, kernel_ms, int(np.max(cyc)), float(np.max(rel)), g.launch_count() - launches0
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def hbm_roofline(bytes_per_node_cycle, nodes, cycles, ms, peak, peak_kind, traffic=None):
+    achieved = bytes_per_node_cycle * nodes * cycles / (ms / 1e3) / 1e9
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": traffic, "peak_kind": f"{peak_kind} HBM copy bandwidth",
+            "algorithmic_bytes_per_node_cycle": bytes_per_node_cycle}
 
 
 def run_gpu(args):
@@ -271,26 +311,37 @@ def run_gpu(args):
         dist.init_process_group("nccl")
     build.build()
     stream = torch.cuda.Stream()
+    dev = f"cuda:{local}"
     n = args.n
     N = 2 ** n + 1
     M = N ** 3
     d = inputs.dielectric_spheres_3d(n=n, seed=replica_seed(rank))
     f = np.ascontiguousarray(d["f"])
     sig = np.ascontiguousarray(d["sigma"])
-    f_dev = torch.from_numpy(f).to(f"cuda:{local}")
-    s_dev = torch.from_numpy(sig).to(f"cuda:{local}")
+    f_dev = torch.from_numpy(f).to(dev)
+    s_dev = torch.from_numpy(sig).to(dev)
     results = {}
     forms = ["mixed", "fp64"] if args.form == "both" else [args.form]
     grids = {}
+    setup_ms = {}
     for form in forms:
         prec = sgml.MIXED if form == "mixed" else sgml.FP64
         g = make_grid(d, prec, stream)
-        g.set_coeffs(0, s_dev)
-        g.set_source(0, f_dev)
         g.set_bc(0, [sgml.DIRICHLET] * 6)
+        g.set_source(0, f_dev)
+        g.set_coeffs(0, s_dev)
+        g.launch_info()  # work tables and the first pyramid (allocates the coefficient pools)
+        # A0, the coefficient pyramid (restricted sigma, local steps per level), timed on its own
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        g.set_coeffs(0, s_dev)
+        g.launch_info()  # rebuilds the pyramid and synchronises
+        torch.cuda.synchronize()
+        setup_ms[form] = (time.perf_counter() - t0) * 1e3
         grids[form] = g
     peak, peak_kind = load_peaks()
     traffic = load_traffic()
+    fp64_rate, fp32_rate = sgml.measure_fma_rates(stream)
     for form in forms:
         g = grids[form]
         steps = args.steps if form == forms[0] else max(1, min(args.steps, args.fp64_steps))
@@ -299,26 +350,45 @@ def run_gpu(args):
         torch.cuda.synchronize()
         with ClockSampler(local) as clk:
             total_ms, kernel_ms, cycles, rel, launches = time_solves(torch, g, stream, steps, args.warmup)
-        total_ms = max_over_ranks(total_ms, f"cuda:{local}")
+        total_ms = max_over_ranks(total_ms, dev)
         ms = total_ms / steps
         value = whole_job_rate(world, M, ms)
-        achieved = BYTES_PER_NODE_CYCLE[form] * M * cycles / (kernel_ms / 1e3) / 1e9
         tr = traffic.get(form)
         ctas, threads, smem = g.launch_info()
         results[form] = {"value": value, "ms_per_step": ms, "kernel_ms": kernel_ms, "cycles": cycles, "rel": rel,
                          "launches_per_step": launches / steps, "steps": steps, "clocks": clk.summary(),
                          "launch": {"ctas": ctas, "threads_per_cta": threads, "smem_bytes_per_cta": smem},
-                         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                                      "frac": achieved / peak,
-                                      "traffic": (tr * M * cycles if tr is not None else None),
-                                      "peak_kind": f"{peak_kind} HBM copy bandwidth",
-                                      "algorithmic_bytes_per_node_cycle": BYTES_PER_NODE_CYCLE[form]}}
-    # accuracy: mixed vs FP64 GPU solutions (the FP64 form matches the CPU oracle in the parity tests)
-    acc = None
-    if len(forms) == 2:
-        um = grids["mixed"].get_solution(0)
-        uf = grids["fp64"].get_solution(0)
-        acc = float(np.linalg.norm(um - uf) / np.linalg.norm(uf))
+                         "roofline": hbm_roofline(BYTES_PER_NODE_CYCLE[form], M, cycles, kernel_ms, peak, peak_kind,
+                                                  tr * M * cycles if tr is not None else None)}
+        if form == "fp64":
+            achieved = FP64_INSTR_PER_NODE_CYCLE * M * cycles / (kernel_ms / 1e3)
+            results[form]["roofline_fp64_pipe"] = {
+                "bound": "fp64", "achieved": achieved, "peak": fp64_rate, "unit": "FP64 instructions/s",
+                "frac": achieved / fp64_rate, "instructions_per_node_cycle": FP64_INSTR_PER_NODE_CYCLE,
+                "peak_kind": "measured FP64 FMA rate (sgml_measure_fma_rates, this run)"}
+    # accuracy: each form at the benchmark tolerance against the FP64 form driven to 1e-13 (the
+    # FP64 form equals the oracle cycle by cycle to 1e-12 in the parity tests)
+    acc = {}
+    u_form = {form: grids[form].get_solution(0) for form in forms}
+    if "fp64" in grids:
+        gf = grids["fp64"]
+        gf.set_params(max_cycles=args.max_cycles + 200)
+        st, cyc, rel = gf.solve_to_tol(1e-13)
+        u_tight = gf.get_solution(0)
+        acc = {"reference": f"FP64 form solved to rel. residual 1e-13 ({int(cyc[0])} cycles, status {st})",
+               **{form: rel_l2(u_form[form], u_tight) for form in forms}}
+        # the residual tolerance at which each form's solution is within 1e-10 of the reference
+        # (the operator amplifies the relative residual ~14x in the relative L2 error here)
+        matched = {}
+        for form in forms:
+            g = grids[form]
+            g.set_params(max_cycles=args.max_cycles + 200)
+            torch.cuda.synchronize()
+            _, ms_m, cyc_m, rel_m, _ = time_solves(torch, g, stream, 1, 0, ACC_TOL)
+            matched[form] = {"tol": ACC_TOL, "cycles": cyc_m, "rel_residual": rel_m, "ms_per_solve": ms_m,
+                             "solved_nodes_per_s": M / (ms_m / 1e3), "rel_l2": rel_l2(g.get_solution(0), u_tight)}
+            g.set_params(max_cycles=args.max_cycles)
+        acc["at_matched_tolerance"] = matched
     # end to end through the C ABI with host buffers (pinned), copies and setup inside
     e2e = None
     if not args.no_e2e:
@@ -341,17 +411,20 @@ def run_gpu(args):
             g.get_solution(0, u_h)
         torch.cuda.synchronize()
         el = time.perf_counter() - t0
-        el = max_over_ranks(el, f"cuda:{local}")
+        el = max_over_ranks(el, dev)
         e2e = {"value": world * M * args.steps / el, "unit": "nodes/s", "h2d_bytes_per_step": 2 * M * 8,
                "d2h_bytes_per_step": M * 8}
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        s, dt = oracle_seconds_per_node_cycle(args.cpu_n, 1)
-        K = results.get("fp64", results[forms[0]])["cycles"]
-        cpu = {"value": 1.0 / (s * K), "unit": "nodes/s", "cores": 1, "kind": "oracle",
-               "sample": f"one outer step + one cycle of the FP64 oracle on the {2 ** args.cpu_n + 1}^3 instance "
-                         f"of the recipe ({dt:.1f} s, single thread), scaled by the {K} cycles the FP64 form "
-                         f"needs at {N}^3"}
+    for g in grids.values():
+        g.close()
+    del grids
+    cpu, configs = None, None
+    if rank == 0 and world == 1:
+        if not args.no_cpu_baseline:
+            cpu, u_orc = cpu_baseline_leg(args)
+            acc["at_65cubed_vs_oracle"] = small_accuracy(args, stream, u_orc)
+        if not args.no_configs:
+            torch.cuda.empty_cache()
+            configs = run_configs(args, stream, local, peak, peak_kind)
     if rank != 0:
         return
     main = results[forms[0]]
@@ -365,17 +438,160 @@ def run_gpu(args):
                        "launch": main["launch"],
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
             "roofline": main["roofline"], "cpu_baseline": cpu, "e2e": e2e,
-            "gpu_launches": int(round(main["launches_per_step"] * main["steps"])), "clocks": main["clocks"]}
+            "gpu_launches": int(round(main["launches_per_step"] * main["steps"])), "clocks": main["clocks"],
+            "setup_ms": setup_ms, "rel_l2_vs_reference": acc,
+            "fma_rates": {"fp64_per_s": fp64_rate, "fp32_per_s": fp32_rate}}
     if "fp64" in results and forms[0] != "fp64":
         fp = results["fp64"]
         line["fp64_form"] = {"value": fp["value"], "ms_per_step": fp["ms_per_step"], "cycles": fp["cycles"],
                              "rel_residual": fp["rel"], "steps": fp["steps"], "roofline": fp["roofline"],
-                             "clocks": fp["clocks"]}
+                             "roofline_fp64_pipe": fp["roofline_fp64_pipe"], "clocks": fp["clocks"]}
         line["mixed_over_fp64"] = main["value"] / fp["value"]
-        line["mixed_vs_fp64_rel_l2"] = acc
+        line["mixed_vs_fp64_rel_l2"] = rel_l2(u_form["mixed"], u_form["fp64"])
+    if configs is not None:
+        line["configs"] = configs
     print(json.dumps(line), flush=True)
-    for g in grids.values():
+
+
+def small_accuracy(args, stream, u_orc):
+    """Both forms on the 65^3 instance of the recipe at the benchmark tolerance against the oracle's
+    own solve at that tolerance, and against the FP64 form driven to 1e-13."""
+    from paper_1703_07206_gb300 import inputs, sgml
+    n = args.cpu_n
+    d = inputs.dielectric_spheres_3d(n=n, seed=2000)
+    out = {}
+    u = {}
+    for form, prec in (("mixed", sgml.MIXED), ("fp64", sgml.FP64)):
+        g = sgml.Grid(3, [n], precision=prec, stream=stream)
+        g.set_params(max_cycles=args.max_cycles + 200)
+        sgml.problem_into_grid(g, 0, d)
+        st, cyc, rel = g.solve_to_tol(TOL)
+        u[form] = g.get_solution(0)
+        if form == "fp64":
+            st2, cyc2, _ = g.solve_to_tol(1e-13)
+            u["tight"] = g.get_solution(0)
         g.close()
+    for form in ("mixed", "fp64"):
+        out[form] = rel_l2(u[form], u_orc)
+        out[form + "_vs_fp64_1e-13"] = rel_l2(u[form], u["tight"])
+    out["oracle_vs_fp64_1e-13"] = rel_l2(u_orc, u["tight"])
+    out["reference"] = (f"the oracle's solution of the {2 ** n + 1}^3 instance at rel. residual {TOL:g} (and the "
+                        f"GPU FP64 form at 1e-13)")
+    return out
+
+
+def run_configs(args, stream, local, peak, peak_kind):
+    """Secondary lines: the other workloads of the benchmark set, each timed on its own (CUDA events
+    on the grid's stream, inputs resident on the device, warm-up solves first)."""
+    import torch
+    from paper_1703_07206_gb300 import inputs, sgml
+    dev = f"cuda:{local}"
+    out = {}
+    steps = max(1, min(args.steps, args.config_steps))
+
+    def solve_line(probs, prec, tol, bytes_node_cycle, label, n_steps=steps, warmup=1):
+        dim = probs[0]["dim"]
+        g = sgml.Grid(dim, [q["n"] for q in probs], precision=prec, stream=stream)
+        g.set_params(max_cycles=args.max_cycles)
+        for b, q in enumerate(probs):
+            g.set_bc(b, q["faces"], q["values"])
+            g.set_coeffs(b, torch.from_numpy(np.ascontiguousarray(q["sigma"])).to(dev) if q["sigma"] is not None
+                         else None, None, q.get("a_scalar", 0.0))
+            g.set_source(b, torch.from_numpy(np.ascontiguousarray(q["f"])).to(dev))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        g.launch_info()
+        torch.cuda.synchronize()
+        setup = (time.perf_counter() - t0) * 1e3
+        nodes = sum(int(np.prod(q["f"].shape)) for q in probs)
+        with ClockSampler(local) as clk:
+            total_ms, kernel_ms, cycles, rel, launches = time_solves(torch, g, stream, n_steps, warmup, tol)
+        g.close()
+        return {"workload": label, "form": "mixed" if prec == sgml.MIXED else "fp64", "nodes": nodes,
+                "tol": tol, "cycles": cycles, "rel_residual": rel, "ms_per_solve": kernel_ms,
+                "solved_nodes_per_s": nodes / (kernel_ms / 1e3), "setup_ms": setup, "steps": n_steps,
+                "launches_per_solve": launches / n_steps,
+                "roofline": hbm_roofline(bytes_node_cycle[ "mixed" if prec == sgml.MIXED else "fp64"], nodes, cycles,
+                                         kernel_ms, peak, peak_kind),
+                "clocks": clk.summary()}
+
+    # 2-D Poisson 129^2, sin(pi x) sin(pi y), Dirichlet 0, tolerance 1e-12 (the plain method)
+    p1 = [inputs.poisson_sine_2d(7)]
+    out["poisson_129sq"] = {f: solve_line(p1, prec, 1e-12, BYTES_2D_CONST,
+                                          "2-D Poisson 129^2, -Lap u = 2 pi^2 sin(pi x) sin(pi y), Dirichlet 0",
+                                          n_steps=max(steps, 10), warmup=3)
+                            for f, prec in (("fp64", sgml.FP64), ("mixed", sgml.MIXED))}
+    # 3 x 513^3 trefoil vector Poisson (Sec. 3.3), both forms, one batch of three components
+    p3 = inputs.trefoil_vorticity_3d(n=9)
+    out["trefoil_3x513cubed"] = {f: solve_line(p3, prec, TOL, BYTES_3D_CONST,
+                                               "3-D vector Poisson -Lap psi_i = omega_i, 3 x 513^3, trefoil tube")
+                                 for f, prec in (("mixed", sgml.MIXED), ("fp64", sgml.FP64))}
+    del p3
+    torch.cuda.empty_cache()
+    # 256 uneven 2-D Helmholtz problems in one persistent launch per solve (mixed form)
+    p4 = inputs.helmholtz_batch_2d()
+    out["helmholtz_batch_256"] = solve_line(p4, sgml.MIXED, TOL, BYTES_2D_CONST,
+                                            "256 x 2-D -Lap u + k^2 u = f, sides 65..1025, D/N sides, one launch")
+    del p4
+    # 16 x 129^3 adjoint: forward solve + adjoint solve + gradient (autograd), mixed form (FP64 outer step)
+    out["adjoint_16x129cubed"] = adjoint_line(args, stream, local, peak, peak_kind, steps)
+    return out
+
+
+def adjoint_line(args, stream, local, peak, peak_kind, steps):
+    import torch
+    from paper_1703_07206_gb300 import inputs, sgml
+    from paper_1703_07206_gb300.autograd import SGMLSolve
+    dev = f"cuda:{local}"
+    probs = inputs.lognormal_dielectric_batch_3d(count=16, n=7, seed=5000)
+    n = probs[0]["n"]
+    M = (2 ** n + 1) ** 3
+    # targets: solutions with the perturbed eps (one batched solve, outside the timed region)
+    gt = sgml.Grid(3, [n] * 16, precision=sgml.MIXED, stream=stream)
+    gt.set_params(max_cycles=args.max_cycles)
+    gt.set_coeffs(-1, torch.from_numpy(np.stack([q["eps_target"] for q in probs])).to(dev))
+    f_all = torch.from_numpy(np.stack([q["f"] for q in probs])).to(dev)
+    gt.set_source(-1, f_all)
+    st, cyc_t, _ = gt.solve_to_tol(TOL)
+    ut = torch.empty_like(f_all)
+    for b in range(16):
+        gt.get_solution(b, ut[b])
+    gt.close()
+    grid = sgml.Grid(3, [n] * 16, precision=sgml.MIXED, stream=stream)
+    grid.set_params(max_cycles=args.max_cycles)
+    sig0 = torch.from_numpy(np.stack([q["sigma"] for q in probs])).to(dev)
+
+    def step():
+        f = f_all.clone().requires_grad_(True)
+        s = sig0.clone().requires_grad_(True)
+        u = SGMLSolve.apply(f, s, grid, TOL, True)
+        J = 0.5 * ((u - ut) ** 2).sum()
+        J.backward()
+        return f.grad, s.grad
+
+    with torch.cuda.stream(stream):
+        step()
+        torch.cuda.synchronize()
+        launches0 = grid.launch_count()
+        with ClockSampler(local) as clk:
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(steps):
+                step()
+            b.record(stream)
+            torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / steps
+    launches = (grid.launch_count() - launches0) / steps
+    cyc_adj = max(grid.get_stats(b)[0] for b in range(16))
+    grid.close()
+    nodes = 16 * M
+    return {"workload": "16 x 3-D dielectric 129^3, log-normal eps, J = 1/2 ||u - u_t||^2: forward solve, "
+                        "adjoint solve, dJ/deps and dJ/df (autograd)",
+            "form": "mixed (FP32 cycle, FP64 outer step)", "nodes": nodes, "tol": TOL,
+            "ms_per_forward_backward": ms, "nodes_per_s_forward_backward": nodes / (ms / 1e3),
+            "launches_per_step": launches, "adjoint_solve_cycles": int(cyc_adj),
+            "target_solve_cycles": int(np.max(cyc_t)), "steps": steps,
+            "clocks": clk.summary()}
 
 
 def schedule_labels(g):
@@ -530,8 +746,10 @@ def main():
     ap.add_argument("--n", type=int, default=8, help="N = 2^n + 1 nodes per side (8: 257^3)")
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--max-cycles", type=int, default=400)
-    ap.add_argument("--cpu-n", type=int, default=7)
-    ap.add_argument("--ref-cycles", type=int, default=185, help="cycles to tolerance used to scale the oracle sample")
+    ap.add_argument("--cpu-n", type=int, default=6, help="cpu_baseline: oracle solve at 2^n + 1 (all cores) and at 2^(n-1) + 1 (one thread)")
+    ap.add_argument("--ref-n", type=int, default=5, help="reference arm: oracle solve of the 2^n + 1 instance per step")
+    ap.add_argument("--no-configs", action="store_true", help="skip the secondary workloads")
+    ap.add_argument("--config-steps", type=int, default=2, help="timed solves per secondary workload")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--ncu-case", action="store_true")

@@ -1246,7 +1246,32 @@ __device__ __forceinline__ T sweep_update(const SweepConst<T>& k, const SweepSta
   return rn_fma(k.q_const, rn_fma(-r_i, k.inv_c, rn_mul((T)2, CSe)), rn_mul(k.one_m_omega, e_c));
 }
 
-template <typename T, bool HET, bool LAST, bool DIAG = false>
+#ifndef SGML_QREG
+#define SGML_QREG 0
+#endif
+// Local step formed from sigma in registers (mixed form, heterogeneous sigma, constant a): with
+// D'_i = S sigma_i + CS(sigma) - a inv_c (D_i / c, c = kappa / (2 H^2)) the step factor is
+// q_i = dtau_i c = omega / D'_i.  The in-plane parts of CS(sigma) of a plane, t = v + w_e F + w_c C
+// and m = F + w_e C, are rolled over z like the four-row sweep's sums.
+template <typename T>
+__device__ __forceinline__ void sigma_tm(const SweepStage<T>& S, int b0, T we, T wc, T t[2], T m[2]) {
+  T s[4][3], A[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) s[i][j] = S.s[b0 + i * kHX + j];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) A[i] = rn_add(s[i][0], s[i][2]);
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    const T F = rn_add(A[r + 1], rn_add(s[r][1], s[r + 2][1]));
+    const T C = rn_add(A[r], A[r + 2]);
+    t[r] = rn_fma(wc, C, rn_fma(we, F, s[r + 1][1]));
+    m[r] = rn_fma(we, C, F);
+  }
+}
+
+template <typename T, bool HET, bool LAST, bool DIAG = false, bool QREG = false>
 __device__ void sweep3(const KernelParams& p, const Phase& ph, int c, const TileTask& tk, SweepStage<T>* st,
                        const SweepCtl& sc) {
   constexpr int D = kSweepStages;
@@ -1287,13 +1312,17 @@ __device__ void sweep3(const KernelParams& p, const Phase& ph, int c, const Tile
           if (cl.in[r]) {
             const unsigned o = base + (unsigned)cl.off[r];
             cp_async_t(&S.r[tid + r * kThreads], R + o);
-            if (HET) cp_async_t(&S.q[tid + r * kThreads], Q + o);
+            if (HET && !QREG) cp_async_t(&S.q[tid + r * kThreads], Q + o);
             if (LAST) cp_async_t(&S.u[tid + r * kThreads], Ug + o);
           }
       }
     }
     cp_async_commit();
   };
+  // local step from sigma (QREG): rolled sigma sums of the thread's two nodes
+  T Ssg[2] = {(T)0, (T)0}, Tsg[2] = {(T)0, (T)0};
+  const T wsum = cv<T>(0.0, p.wsum_f), omega = cv<T>(p.omega, p.omega_f);
+  const T a_inv_c = QREG ? rn_mul(cv<T>(P.a_scalar, P.a_scalar_f), kc.inv_c) : (T)0;
   // A piece of one plane (the coarse levels' usual share) fetches its three planes in one round trip.
   const int pre = nplanes <= D - 1 ? nplanes : D - 2;
   for (int k = 0; k < pre; ++k) issue(k);
@@ -1307,6 +1336,8 @@ __device__ void sweep3(const KernelParams& p, const Phase& ph, int c, const Tile
     if (k + D - 2 >= pre) issue(k + D - 2);
     else cp_async_commit();
     plane_sums2<T, HET>(st[k % D], b0, zero_in, nw);
+    T tsg[2], msg[2];
+    if (QREG) sigma_tm<T>(st[k % D], b0, kc.w_e, kc.w_c, tsg, msg);
     if (k >= 2) {
       const int z = tk.z0 + k - 2;
       const bool zf = z_fixed(cl, z, N);
@@ -1321,11 +1352,27 @@ __device__ void sweep3(const KernelParams& p, const Phase& ph, int c, const Tile
                                     rn_fma(kc.w_e, (o[r].sC + m[r].sF) + nw[r].sF, (o[r].sF + m[r].sv) + nw[r].sv))
                            : (T)0;
         const int slot = tid + r * kThreads;
-        const T e_new = sweep_update<T, HET>(kc, S, slot, b0 + (r + 1) * kHX + 1, CSe, CSse, o[r].v);
+        T e_new;
+        if constexpr (QREG) {
+          const int cc = b0 + (r + 1) * kHX + 1;
+          const T sg_c = S.s[cc];
+          const T Dp = rn_add(rn_fma(wsum, sg_c, rn_add(Ssg[r], tsg[r])), -a_inv_c);
+          const T q = __fdividef(omega, Dp);
+          e_new = rn_fma(q, rn_fma(-S.r[slot], kc.inv_c, rn_fma(sg_c, CSe, CSse)), rn_mul(kc.one_m_omega, o[r].v));
+        } else {
+          e_new = sweep_update<T, HET>(kc, S, slot, b0 + (r + 1) * kHX + 1, CSe, CSse, o[r].v);
+        }
         if (DIAG) dmx = fmax(dmx, diag_term(e_new - o[r].v, HET ? S.q[slot] : kc.q_const));
         const unsigned idx = zoff + (unsigned)cl.off[r];
         if (LAST) Ug[idx] = __fma_rn((double)e_new, inv_scale, S.u[slot]);
         if (keep) dst[idx] = e_new;
+      }
+    }
+    if (QREG) {
+#pragma unroll
+      for (int r = 0; r < 2; ++r) {
+        Ssg[r] = rn_add(msg[r], Tsg[r]);
+        Tsg[r] = tsg[r];
       }
     }
   };
@@ -1340,6 +1387,167 @@ __device__ void sweep3(const KernelParams& p, const Phase& ph, int c, const Tile
   cp_async_wait<0>();
   __syncthreads();
   if (DIAG) diag_flush<T>(p, tk.b, c, ph.level, dmx, kc.inv_c);
+}
+
+// ---------------------------------------------------------------------------------------------
+// Level sweep of the FP64 form (3-D).  On a GPU with a narrow FP64 pipe the FP64 sweep is bound by
+// its FP64 instruction count, not by HBM, so its arithmetic is arranged to need fewer of them (25
+// per node for a heterogeneous problem instead of 36) -- the same Jacobi update (Eq. 2 with the
+// radial stencil of Eq. 5), summed in another order:
+//   - sigma * e is formed once per halo cell (in place of sigma in shared memory, after each
+//     thread has kept sigma at its own two nodes), not once per use by the 2 x 3 threads around it;
+//   - a thread's two nodes share the horizontal pair sums of its 4 x 3 block (face sums
+//     F = A(r + 1) + (v(r) + v(r + 2)), corner sums C = A(r) + A(r + 2), A(r) = v(r, x-1) + v(r, x+1));
+//   - the z sums are rolled as in the four-row sweep: with t = v + w_e F + w_c C and m = F + w_e C
+//     of a plane, CS at plane z is (m_z + t_{z-1}) + t_{z+1} (two registers per node and array
+//     instead of three planes of sums).
+// Explicitly rounded throughout, so every node's value is independent of the tile and launch shape.
+// ---------------------------------------------------------------------------------------------
+template <bool HET, bool LAST>
+__device__ void sweep3_f64(const KernelParams& p, const Phase& ph, int c, const TileTask& tk, SweepStage<double>* st,
+                           const SweepCtl& sc) {
+  using T = double;
+  constexpr int D = kSweepStages;
+  const ProblemDesc& P = prob_at(p, tk.b);
+  const int N = sc.N;
+  const int tid = threadIdx.x;
+  const Columns cl = own_columns(P, N, tk.x0, tk.y0);
+  const bool odd = sweep_parity(p, ph.level, ph.sweep) != 0;
+  const T* src = odd ? (const T*)p.E2 + sc.off : (const T*)p.E + sc.off;
+  T* dst = odd ? (T*)p.E + sc.off : (T*)p.E2 + sc.off;
+  const T* R = (const T*)p.R + sc.off;
+  const T* SG = HET ? (const T*)p.SIG + sc.off : nullptr;
+  const T* Q = HET ? (const T*)p.Q + sc.off : nullptr;
+  double* Ug = p.U + P.off_full;
+  const HaloCells hc = halo_cells(P, N, tk.x0, tk.y0, false);
+  const SweepConst<T> kc = sweep_const<T>(p, P, ph.level);
+  const int b0 = (2 * (tid / kTX)) * kHX + (tid % kTX);
+  const double inv_scale = LAST ? inv_scale_at(p, tk.b, c & 1) : 0.0;
+  const bool zero_in = sc.zero_in;
+  const int nplanes = tk.nz + 2;
+  const unsigned NN = (unsigned)N * (unsigned)N;
+  auto issue = [&](int k) {
+    if (k < nplanes) {
+      SweepStage<T>& S = st[k % D];
+      const unsigned base = (unsigned)refl(tk.z0 - 1 + k, N) * NN;
+#pragma unroll
+      for (int q = 0; q < kCells; ++q)
+        if (hc.off[q] >= 0) {
+          const unsigned o = base + (unsigned)hc.off[q];
+          if (!zero_in) cp_async_t(&S.e[tid + q * kThreads], src + o);
+          if (HET) cp_async_t(&S.s[tid + q * kThreads], SG + o);
+        }
+      if (k >= 1 && k <= tk.nz) {
+#pragma unroll
+        for (int r = 0; r < 2; ++r)
+          if (cl.in[r]) {
+            const unsigned o = base + (unsigned)cl.off[r];
+            cp_async_t(&S.r[tid + r * kThreads], R + o);
+            if (HET) cp_async_t(&S.q[tid + r * kThreads], Q + o);
+            if (LAST) cp_async_t(&S.u[tid + r * kThreads], Ug + o);
+          }
+      }
+    }
+    cp_async_commit();
+  };
+  const int pre = nplanes <= D - 1 ? nplanes : D - 2;
+  for (int k = 0; k < pre; ++k) issue(k);
+  // rolled z sums (Se = m_{z} + t_{z-1} awaiting t_{z+1}, Te = t_z) of e and sigma e, and e and sigma
+  // at the thread's two nodes one plane behind
+  T Se[2], Te[2], Ss[2], Ts[2], vp[2], sp[2];
+#pragma unroll
+  for (int r = 0; r < 2; ++r) Se[r] = Te[r] = Ss[r] = Ts[r] = vp[r] = sp[r] = (T)0;
+  for (int k = 0; k < nplanes; ++k) {
+    cp_async_wait<D - 3>();
+    __syncthreads();
+    if (k + D - 2 >= pre) issue(k + D - 2);
+    else cp_async_commit();
+    SweepStage<T>& S = st[k % D];
+    T t[2], m[2], ts[2], ms[2], v[2], sv[2];
+    if (zero_in) {
+#pragma unroll
+      for (int r = 0; r < 2; ++r) {
+        t[r] = m[r] = ts[r] = ms[r] = v[r] = (T)0;
+        sv[r] = HET ? S.s[b0 + (r + 1) * kHX + 1] : (T)0;
+      }
+    } else {
+      if (HET) {  // sigma at the own nodes, then sigma * e in place of sigma on the plane's halo tile
+#pragma unroll
+        for (int r = 0; r < 2; ++r) sv[r] = S.s[b0 + (r + 1) * kHX + 1];
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < kCells; ++q)
+          if (hc.off[q] >= 0) S.s[tid + q * kThreads] = rn_mul(S.s[tid + q * kThreads], S.e[tid + q * kThreads]);
+        __syncthreads();
+      }
+      T a[4][3], se[4][3];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+          a[i][j] = S.e[b0 + i * kHX + j];
+          if (HET) se[i][j] = S.s[b0 + i * kHX + j];
+        }
+      T A[4], As[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        A[i] = rn_add(a[i][0], a[i][2]);
+        if (HET) As[i] = rn_add(se[i][0], se[i][2]);
+      }
+#pragma unroll
+      for (int r = 0; r < 2; ++r) {
+        const T F = rn_add(A[r + 1], rn_add(a[r][1], a[r + 2][1]));
+        const T C = rn_add(A[r], A[r + 2]);
+        v[r] = a[r + 1][1];
+        t[r] = rn_fma(kc.w_c, C, rn_fma(kc.w_e, F, v[r]));
+        m[r] = rn_fma(kc.w_e, C, F);
+        if (HET) {
+          const T sF = rn_add(As[r + 1], rn_add(se[r][1], se[r + 2][1]));
+          const T sC = rn_add(As[r], As[r + 2]);
+          ts[r] = rn_fma(kc.w_c, sC, rn_fma(kc.w_e, sF, se[r + 1][1]));
+          ms[r] = rn_fma(kc.w_e, sC, sF);
+        } else {
+          ts[r] = ms[r] = sv[r] = (T)0;
+        }
+      }
+    }
+    if (k >= 2) {  // the nodes of plane k - 1 receive this plane (dz = +1) and are updated
+      const int z = tk.z0 + k - 2;
+      const bool zf = z_fixed(cl, z, N);
+      const SweepStage<T>& S1 = st[(k - 1) % D];
+      const unsigned zoff = (unsigned)z * NN;
+#pragma unroll
+      for (int r = 0; r < 2; ++r) {
+        if (!cl.in[r] || cl.fixed_xy[r] || zf) continue;
+        const int slot = tid + r * kThreads;
+        const T CSe = rn_add(Se[r], t[r]);
+        const T r_i = S1.r[slot];
+        T e_new;
+        if (HET) {
+          const T CSse = rn_add(Ss[r], ts[r]);
+          e_new = rn_fma(S1.q[slot], rn_fma(-r_i, kc.inv_c, rn_fma(sp[r], CSe, CSse)), rn_mul(kc.one_m_omega, vp[r]));
+        } else {
+          e_new = rn_fma(kc.q_const, rn_fma(-r_i, kc.inv_c, rn_mul((T)2, CSe)), rn_mul(kc.one_m_omega, vp[r]));
+        }
+        const unsigned idx = zoff + (unsigned)cl.off[r];
+        if (LAST) Ug[idx] = __fma_rn(e_new, inv_scale, S1.u[slot]);
+        else dst[idx] = e_new;
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      Se[r] = rn_add(m[r], Te[r]);
+      Te[r] = t[r];
+      if (HET) {
+        Ss[r] = rn_add(ms[r], Ts[r]);
+        Ts[r] = ts[r];
+      }
+      vp[r] = v[r];
+      sp[r] = sv[r];
+    }
+  }
+  cp_async_wait<0>();
+  __syncthreads();
 }
 
 // 2-D: one halo tile per task, the CTA's tasks pipelined kSweepStages - 2 deep.
@@ -1946,6 +2154,18 @@ __device__ void phase_sweep(const KernelParams& p, const Phase& ph, int c, unsig
         return;
       }
     }
+    if constexpr (sizeof(T) == 8) {
+      if (!p.diag) {  // the FP64 form's sweep with fewer FP64 instructions per node
+        if (sc.last) {
+          if (het) sweep3_f64<true, true>(p, ph, c, tk, st, sc);
+          else sweep3_f64<false, true>(p, ph, c, tk, st, sc);
+        } else {
+          if (het) sweep3_f64<true, false>(p, ph, c, tk, st, sc);
+          else sweep3_f64<false, false>(p, ph, c, tk, st, sc);
+        }
+        return;
+      }
+    }
     if (p.diag) {
       if (sc.last) {
         if (het) sweep3<T, true, true, true>(p, ph, c, tk, st, sc);
@@ -1955,6 +2175,13 @@ __device__ void phase_sweep(const KernelParams& p, const Phase& ph, int c, unsig
         else sweep3<T, false, false, true>(p, ph, c, tk, st, sc);
       }
       return;
+    }
+    if constexpr (sizeof(T) == 4 && SGML_QREG) {
+      if (het && !prob_at(p, tk.b).a_per_node) {  // local step formed from sigma in registers
+        if (sc.last) sweep3<T, true, true, false, true>(p, ph, c, tk, st, sc);
+        else sweep3<T, true, false, false, true>(p, ph, c, tk, st, sc);
+        return;
+      }
     }
     if (sc.last) {
       if (het) sweep3<T, true, true>(p, ph, c, tk, st, sc);
