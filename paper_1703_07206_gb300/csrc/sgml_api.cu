@@ -494,8 +494,6 @@ static int launch(sgml_grid* g, int max_cycles, double tol) {
   p.w_edge_f = (float)p.w_edge;
   p.w_corner_f = (float)p.w_corner;
   p.one_m_omega_f = (float)(1.0 - p.omega);
-  p.omega_f = (float)p.omega;
-  p.wsum_f = (float)weight_sum(g->dim);
   p.n_r = g->n_r;
   p.pair_levels = effective_pair_levels(g);
   p.sync = g->d_sync;

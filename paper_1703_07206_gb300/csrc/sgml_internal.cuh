@@ -135,7 +135,6 @@ struct KernelParams {
   double w_edge, w_corner;       // 1/sqrt(2), 1/sqrt(3)
   double omega;                  // delta_tau * D_i of the Jacobi-scaled step
   float w_edge_f, w_corner_f, one_m_omega_f;  // FP32 copies of w_edge, w_corner and 1 - omega
-  float omega_f, wsum_f;         // FP32 omega and S_d = sum_o w_o (the local step formed from sigma)
   int n_r;
   int pair_levels;               // levels 0 .. pair_levels - 1 run their sweeps in fused pairs (kPair)
   GridSync* sync;

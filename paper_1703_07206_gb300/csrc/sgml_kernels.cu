@@ -1246,32 +1246,7 @@ __device__ __forceinline__ T sweep_update(const SweepConst<T>& k, const SweepSta
   return rn_fma(k.q_const, rn_fma(-r_i, k.inv_c, rn_mul((T)2, CSe)), rn_mul(k.one_m_omega, e_c));
 }
 
-#ifndef SGML_QREG
-#define SGML_QREG 0
-#endif
-// Local step formed from sigma in registers (mixed form, heterogeneous sigma, constant a): with
-// D'_i = S sigma_i + CS(sigma) - a inv_c (D_i / c, c = kappa / (2 H^2)) the step factor is
-// q_i = dtau_i c = omega / D'_i.  The in-plane parts of CS(sigma) of a plane, t = v + w_e F + w_c C
-// and m = F + w_e C, are rolled over z like the four-row sweep's sums.
-template <typename T>
-__device__ __forceinline__ void sigma_tm(const SweepStage<T>& S, int b0, T we, T wc, T t[2], T m[2]) {
-  T s[4][3], A[4];
-#pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int j = 0; j < 3; ++j) s[i][j] = S.s[b0 + i * kHX + j];
-#pragma unroll
-  for (int i = 0; i < 4; ++i) A[i] = rn_add(s[i][0], s[i][2]);
-#pragma unroll
-  for (int r = 0; r < 2; ++r) {
-    const T F = rn_add(A[r + 1], rn_add(s[r][1], s[r + 2][1]));
-    const T C = rn_add(A[r], A[r + 2]);
-    t[r] = rn_fma(wc, C, rn_fma(we, F, s[r + 1][1]));
-    m[r] = rn_fma(we, C, F);
-  }
-}
-
-template <typename T, bool HET, bool LAST, bool DIAG = false, bool QREG = false>
+template <typename T, bool HET, bool LAST, bool DIAG = false>
 __device__ void sweep3(const KernelParams& p, const Phase& ph, int c, const TileTask& tk, SweepStage<T>* st,
                        const SweepCtl& sc) {
   constexpr int D = kSweepStages;
@@ -1312,17 +1287,13 @@ __device__ void sweep3(const KernelParams& p, const Phase& ph, int c, const Tile
           if (cl.in[r]) {
             const unsigned o = base + (unsigned)cl.off[r];
             cp_async_t(&S.r[tid + r * kThreads], R + o);
-            if (HET && !QREG) cp_async_t(&S.q[tid + r * kThreads], Q + o);
+            if (HET) cp_async_t(&S.q[tid + r * kThreads], Q + o);
             if (LAST) cp_async_t(&S.u[tid + r * kThreads], Ug + o);
           }
       }
     }
     cp_async_commit();
   };
-  // local step from sigma (QREG): rolled sigma sums of the thread's two nodes
-  T Ssg[2] = {(T)0, (T)0}, Tsg[2] = {(T)0, (T)0};
-  const T wsum = cv<T>(0.0, p.wsum_f), omega = cv<T>(p.omega, p.omega_f);
-  const T a_inv_c = QREG ? rn_mul(cv<T>(P.a_scalar, P.a_scalar_f), kc.inv_c) : (T)0;
   // A piece of one plane (the coarse levels' usual share) fetches its three planes in one round trip.
   const int pre = nplanes <= D - 1 ? nplanes : D - 2;
   for (int k = 0; k < pre; ++k) issue(k);
@@ -1336,8 +1307,6 @@ __device__ void sweep3(const KernelParams& p, const Phase& ph, int c, const Tile
     if (k + D - 2 >= pre) issue(k + D - 2);
     else cp_async_commit();
     plane_sums2<T, HET>(st[k % D], b0, zero_in, nw);
-    T tsg[2], msg[2];
-    if (QREG) sigma_tm<T>(st[k % D], b0, kc.w_e, kc.w_c, tsg, msg);
     if (k >= 2) {
       const int z = tk.z0 + k - 2;
       const bool zf = z_fixed(cl, z, N);
@@ -1352,27 +1321,11 @@ __device__ void sweep3(const KernelParams& p, const Phase& ph, int c, const Tile
                                     rn_fma(kc.w_e, (o[r].sC + m[r].sF) + nw[r].sF, (o[r].sF + m[r].sv) + nw[r].sv))
                            : (T)0;
         const int slot = tid + r * kThreads;
-        T e_new;
-        if constexpr (QREG) {
-          const int cc = b0 + (r + 1) * kHX + 1;
-          const T sg_c = S.s[cc];
-          const T Dp = rn_add(rn_fma(wsum, sg_c, rn_add(Ssg[r], tsg[r])), -a_inv_c);
-          const T q = __fdividef(omega, Dp);
-          e_new = rn_fma(q, rn_fma(-S.r[slot], kc.inv_c, rn_fma(sg_c, CSe, CSse)), rn_mul(kc.one_m_omega, o[r].v));
-        } else {
-          e_new = sweep_update<T, HET>(kc, S, slot, b0 + (r + 1) * kHX + 1, CSe, CSse, o[r].v);
-        }
+        const T e_new = sweep_update<T, HET>(kc, S, slot, b0 + (r + 1) * kHX + 1, CSe, CSse, o[r].v);
         if (DIAG) dmx = fmax(dmx, diag_term(e_new - o[r].v, HET ? S.q[slot] : kc.q_const));
         const unsigned idx = zoff + (unsigned)cl.off[r];
         if (LAST) Ug[idx] = __fma_rn((double)e_new, inv_scale, S.u[slot]);
         if (keep) dst[idx] = e_new;
-      }
-    }
-    if (QREG) {
-#pragma unroll
-      for (int r = 0; r < 2; ++r) {
-        Ssg[r] = rn_add(msg[r], Tsg[r]);
-        Tsg[r] = tsg[r];
       }
     }
   };
@@ -2175,13 +2128,6 @@ __device__ void phase_sweep(const KernelParams& p, const Phase& ph, int c, unsig
         else sweep3<T, false, false, true>(p, ph, c, tk, st, sc);
       }
       return;
-    }
-    if constexpr (sizeof(T) == 4 && SGML_QREG) {
-      if (het && !prob_at(p, tk.b).a_per_node) {  // local step formed from sigma in registers
-        if (sc.last) sweep3<T, true, true, false, true>(p, ph, c, tk, st, sc);
-        else sweep3<T, true, false, false, true>(p, ph, c, tk, st, sc);
-        return;
-      }
     }
     if (sc.last) {
       if (het) sweep3<T, true, true>(p, ph, c, tk, st, sc);

@@ -291,8 +291,6 @@ extern "C" int sgml_solve_noalloc(int dim, int n, int precision, const double* f
   p.w_edge_f = (float)p.w_edge;
   p.w_corner_f = (float)p.w_corner;
   p.one_m_omega_f = (float)(1.0 - p.omega);
-  p.omega_f = (float)p.omega;
-  p.wsum_f = (float)weight_sum(dim);
   p.n_r = n_r;
   p.sync = (GridSync*)(base + o_sync);
   p.timeout_ns = 2000000000ull;
