@@ -193,8 +193,9 @@ __device__ bool grid_sync(GridSync* gs, unsigned long long timeout_ns, int withh
     bool arrive = true;
     if (withhold_barrier > 0 && blockIdx.x == 0) arrive = ++s_barriers != withhold_barrier;
     if (arrive) {
-      // arrival: release (the CTA's writes, ordered before by the CTA barrier, become visible)
-      asm volatile("atom.add.release.gpu.u64 %0, [%1], 1;" : "=l"(old) : "l"(&gs->arrive) : "memory");
+      // arrival: release (the CTA's writes, ordered before by the CTA barrier, become visible) and, for
+      // the last CTA to arrive, acquire (the others' writes are visible to it)
+      asm volatile("atom.add.acq_rel.gpu.u64 %0, [%1], 1;" : "=l"(old) : "l"(&gs->arrive) : "memory");
     } else {
       asm volatile("ld.relaxed.gpu.u64 %0, [%1];" : "=l"(old) : "l"(&gs->arrive) : "memory");
       old = old / G * G;  // this round's target is never reached: the wait below runs out
@@ -205,7 +206,8 @@ __device__ bool grid_sync(GridSync* gs, unsigned long long timeout_ns, int withh
       unsigned spins = 0;
       for (;;) {
         unsigned long long seen;
-        asm volatile("ld.relaxed.gpu.u64 %0, [%1];" : "=l"(seen) : "l"(&gs->arrive) : "memory");
+        // acquire: the load that sees every arrival makes the other CTAs' writes visible
+        asm volatile("ld.acquire.gpu.u64 %0, [%1];" : "=l"(seen) : "l"(&gs->arrive) : "memory");
         if (seen >= target) break;
         if ((++spins & 31u) == 0u) {
           if (ld_volatile(&gs->error)) {  // another CTA gave up: stop too
@@ -220,10 +222,11 @@ __device__ bool grid_sync(GridSync* gs, unsigned long long timeout_ns, int withh
         }
       }
     }
-    // acquire: the other CTAs' writes are visible.  No error load on success: only a timed-out
-    // CTA sets the flag, and it leaves the kernel, so every other CTA meets the flag while it
-    // spins at the next barrier (one load round trip less per barrier).
-    asm volatile("fence.acq_rel.gpu;" ::: "memory");
+    // No error load on success: only a timed-out CTA sets the flag, and it leaves the kernel, so
+    // every other CTA meets the flag while it spins at the next barrier (one load round trip less
+    // per barrier).  The acquire of the arrival or of the polling load, then the CTA barrier below,
+    // orders the CTA's later reads after the other CTAs' writes; no separate fence (measured: 8-14 %
+    // less per barrier, ~1 % of the solve).
     s_ok = ok;
   }
   __syncthreads();
