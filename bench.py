@@ -42,12 +42,15 @@ BYTES_PER_NODE_CYCLE = {"mixed": 182.0, "fp64": 331.0}
 # coefficients: no sigma arrays).
 BYTES_2D_CONST = {"mixed": 152.0, "fp64": 280.0}
 BYTES_3D_CONST = {"mixed": 138.0, "fp64": 253.0}
-# FP64 instructions per node per cycle of the FP64 form on the 3-D heterogeneous workload, counted
-# from the kernels' arithmetic (n_r = 2, zig-zag): 8 level-0 sweeps x 36 (sigma * e products,
-# in-plane face / corner sums of e and sigma e, the z combination, the Jacobi update), the solution
-# update 1, the FP64 residual 88 (27 sigma-weighted differences: 78, the sums, the cast, the norms),
-# coarse-level sweeps 6 x 36 / 7, restrictions ~6, interpolations ~10.
-FP64_INSTR_PER_NODE_CYCLE = 424.0
+# FP64 instructions per node per cycle of the FP64 form on the 3-D heterogeneous workload at 257^3,
+# counted from the kernels' arithmetic (n_r = 2, zig-zag; ncu's DADD + DFMA + DMUL counts of the
+# two dominant kernels agree: 87.7 per node for the residual, 28.2 for a level-0 sweep at 129^3,
+# where the sweep's short z-runs add plane sums of 2 halo planes per ~14 planes):
+#   8 level-0 sweeps x 25.7 (sigma e once per halo cell 1.3, pair / face / corner sums 10, rolled z
+#   terms 10, Jacobi update 4, halo planes of ~108-plane runs 0.4), the solution update 1, the FP64
+#   residual 87.7 (27 sigma-weighted differences 78, sums, cast, norms), coarse-level sweeps 26.8
+#   (6 per level and cycle, on short runs), restrictions 5.6, interpolations 11.
+FP64_INSTR_PER_NODE_CYCLE = 338.0
 KERNEL_SOURCES = ["paper_1703_07206_gb300/csrc/sgml_kernels.cu", "paper_1703_07206_gb300/csrc/sgml_internal.cuh"]
 
 
