@@ -1119,7 +1119,6 @@ __device__ void phase_check(const KernelParams& p, int c) {
     S.hist_len = c + 1;
     if (c > 0) S.cycles += 1;
     const bool anchored = !p.mixed || c == 0 || S.anchor_next;
-    const double rho = S.rel_prev < 1e300 && S.rel_prev > 0.0 ? rel / S.rel_prev : 1.0;
     S.grow = (rel > S.rel_prev) ? S.grow + 1 : 0;
     S.rel_prev = rel;
     S.rmax_prev = rmax;
@@ -1142,13 +1141,14 @@ __device__ void phase_check(const KernelParams& p, int c) {
       st = p.tol >= 0.0 ? -3 : 0;  // SGML_ERR_NOT_CONVERGED for a solve; fine for run_cycle
       stop = 1;
     }
-    // Mixed form: the next residual is the FP64 anchor when the recurrence may have drifted by a few
-    // per cent of the current residual (it fell a hundred-fold since the last anchor, 64 cycles
-    // passed, or the cycle contracts fast), when the tolerance may have been reached, and before
-    // the last cycle of the launch.  The FP32 stencil's error is ~1e-7 of the stencil's terms, which
-    // exceed |delta L e| by up to ~1/h for smooth e, so the drift grows like 3e-5 * sum |r_i|.
-    S.anchor_next = !p.mixed || rho < 0.2 || rel <= 0.01 * S.anchor_rel || rel <= p.tol ||
-                    c + 1 >= p.max_cycles || c + 1 - S.last_anchor >= 64;
+    // Mixed form: the next residual is the FP64 anchor once the residual fell 1e4-fold since the last
+    // anchor or 64 cycles passed, when the tolerance may have been reached, and after the launch's
+    // last cycle.  The recurrence's error is that of the FP32 stencil applied to each correction,
+    // ~1e-7 of the residual it removes (measured at 257^3: the recurrence residual within 1.3e-7 of
+    // the exact FP64 residual of the same iterate), so after a 1e4-fold fall it is still ~1e-3 of
+    // the current residual; convergence is accepted on anchored residuals only.
+    S.anchor_next = !p.mixed || rel <= 1e-4 * S.anchor_rel || rel <= p.tol || c + 1 >= p.max_cycles ||
+                    c + 1 - S.last_anchor >= 64;
     S.status = st;
     A.done = stop;
     A.rmax_bits[(c + 1) & 1] = 0ull;
