@@ -630,13 +630,18 @@ def run_ncu_case(args):
     from paper_1703_07206_gb300 import build, inputs, sgml
     build.build()
     torch.cuda.set_device(0)
-    d = inputs.dielectric_spheres_3d(n=args.n, seed=2000)
+    if args.ncu_workload == "batch":  # the 256 uneven 2-D Helmholtz problems
+        probs = inputs.helmholtz_batch_2d()
+    else:
+        probs = [inputs.dielectric_spheres_3d(n=args.n, seed=2000)]
     prec = sgml.MIXED if args.form in ("mixed", "both") else sgml.FP64
-    g = sgml.Grid(3, [args.n], precision=prec)
+    g = sgml.Grid(probs[0]["dim"], [q["n"] for q in probs], precision=prec)
+    g.set_params(max_cycles=args.max_cycles)
     g.set_launch(0, 1, 1 if args.phased else 0, args.tile_x, args.slab_z)
     g.set_fusion(args.pair_levels)
     g.set_quad(args.quad_levels)
-    sgml.problem_into_grid(g, 0, d)
+    for b, q in enumerate(probs):
+        sgml.problem_into_grid(g, b, q)
     g.run_cycle(1)  # warm-up launch (and setup)
     if args.trace:
         run_trace(args, g, args.n)
@@ -649,7 +654,8 @@ def run_ncu_case(args):
         g.run_cycle(args.ncu_cycles)
     torch.cuda.synchronize()
     c, rel, st = g.get_stats(0)
-    print(json.dumps({"ncu_case": True, "n": args.n, "form": args.form, "cycles": c, "rel": rel, "status": st}))
+    print(json.dumps({"ncu_case": True, "workload": args.ncu_workload, "n": args.n, "form": args.form, "cycles": c,
+                      "rel": rel, "status": st, "phases": len(g.get_phases())}))
     g.close()
 
 
@@ -758,6 +764,8 @@ def main():
     ap.add_argument("--ncu-case", action="store_true")
     ap.add_argument("--ncu-cycles", type=int, default=2)
     ap.add_argument("--ncu-solve", action="store_true", help="ncu case: one full solve instead of --ncu-cycles")
+    ap.add_argument("--ncu-workload", default="dielectric", choices=["dielectric", "batch"],
+                    help="ncu case: the 3-D dielectric workload (--n) or the 256-problem 2-D Helmholtz batch")
     ap.add_argument("--phased", action="store_true")
     ap.add_argument("--tile-x", type=int, default=64, choices=[32, 64], help="column tiles 32 x 16 or 64 x 8")
     ap.add_argument("--slab-z", type=int, default=None,

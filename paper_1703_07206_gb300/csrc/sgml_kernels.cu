@@ -976,42 +976,87 @@ __device__ __forceinline__ ResSrc<T> recur_src(const KernelParams& p, const Prob
   return s;
 }
 
-// 2-D: one halo tile per task, the CTA's tasks pipelined kOuterStages - 2 deep; `anchor` selects
-// which problems this pass serves.
+// 2-D: one halo tile per task, the CTA's tasks pipelined kOuterStages - 2 deep, in one pass: each
+// task's problem takes the FP64 anchor or (mixed form) the FP32 recurrence.  The stage slots are
+// sized for the anchor's FP64 layout, so both kinds of tile share the pipeline (two passes over all
+// tiles, one per kind, cost a pipeline wait and a CTA barrier per skipped tile).
 template <typename T, typename V>
-__device__ void residual2(const KernelParams& p, int c, ResStage<V>* st, bool anchor) {
-  constexpr int D = kOuterStages;
-  const int t0 = s_toff[0][0], J = s_toff[0][1] - s_toff[0][0];  // level 0
+__device__ __forceinline__ void res2_issue(const KernelParams& p, const ProblemDesc& P, const TileTask& tk,
+                                           ResStage<V>& S, const ResSrc<V>& src) {
+  const int tid = threadIdx.x;
+  const int N = level_side(P.n, 0);
+  const HaloCells hc = halo_cells(P, N, tk.x0, tk.y0, false);
+  const Columns cl = own_columns(P, N, tk.x0, tk.y0);
+#pragma unroll
+  for (int s = 0; s < kCells; ++s)
+    if (hc.off[s] >= 0) {
+      cp_async_t(&S.u[tid + s * kThreads], src.u + hc.off[s]);
+      if (src.s) cp_async_t(&S.s[tid + s * kThreads], src.s + hc.off[s]);
+    }
+#pragma unroll
+  for (int r = 0; r < 2; ++r)
+    if (cl.in[r]) {
+      cp_async_t(&S.f[tid + r * kThreads], src.rhs + cl.off[r]);
+      if (src.a) cp_async_t(&S.a[tid + r * kThreads], src.a + cl.off[r]);
+    }
+}
+
+template <typename T, typename V>
+__device__ __forceinline__ void res2_compute(const KernelParams& p, const ProblemDesc& P, const TileTask& tk, int c,
+                                             ResStage<V>& S, const ResSrc<V>& src) {
   const int tid = threadIdx.x;
   const int b0 = (2 * (tid / kTX)) * kHX + (tid % kTX);
+  const int N = level_side(P.n, 0);
+  if (src.images && tile_has_flux(P, N, tk.x0, tk.y0, 2)) {
+    const HaloCells hc = halo_cells(P, N, tk.x0, tk.y0, true);
+#pragma unroll
+    for (int s = 0; s < kCells; ++s)
+      if (hc.off[s] >= 0) S.u[tid + s * kThreads] += (V)hc.ghost[s];
+    __syncthreads();
+  }
+  const Columns cl = own_columns(P, N, tk.x0, tk.y0);
+  V mx = (V)0, s2 = (V)0;
+  V uc[2], sc[2], cls[2][3];
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    uc[r] = S.u[b0 + (r + 1) * kHX + 1];
+    sc[r] = src.s ? S.s[b0 + (r + 1) * kHX + 1] : (V)1;
+    cls[r][0] = cls[r][1] = cls[r][2] = (V)0;
+  }
+  if (src.s) res_plane<V, true>(S, b0, 0, uc, sc, cls);
+  else res_plane<V, false>(S, b0, 0, uc, sc, cls);
+  const V c0v = cv<V>(P.c0 * (src.s ? 1.0 : 2.0), P.c0_f * (src.s ? 1.0f : 2.0f));
+  const double scale = outer_scale(p, tk.b, c);
+  const float scale32 = outer_scale_f(p, tk.b, c);
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    if (!cl.in[r] || cl.fixed_xy[r]) continue;
+    const V sum = rn_fma(cv<V>(p.w_edge, p.w_edge_f), cls[r][1], cls[r][0]);
+    const V a = src.a ? S.a[tid + r * kThreads] : cv<V>(src.a_scalar, P.a_scalar_f);
+    res_finish<T, V>(src, c0v, sum, uc[r], a, S.f[tid + r * kThreads], scale, scale32, (T*)p.R + P.off_lvl[0],
+                     p.RESP ? p.RESP + P.off_full : nullptr, cl.off[r], mx, s2);
+  }
+  block_flush((double)mx, (double)s2, &p.accum[tk.b].rmax_bits[c & 1], &p.accum[tk.b].rsum2[c & 1]);
+}
+
+template <typename T>
+__device__ void residual2(const KernelParams& p, int c, unsigned char* smem) {
+  constexpr int D = kOuterStages;
+  constexpr size_t kSlot = sizeof(ResStage<double>);
+  static_assert(sizeof(ResStage<T>) <= kSlot && kSlot % 16 == 0, "residual stage slots");
+  const int t0 = s_toff[0][0], J = s_toff[0][1] - s_toff[0][0];  // level 0
   auto task = [&](int j) -> const TileTask& { return p.tasks[t0 + j]; };
-  auto mine = [&](int b) { return !done_at(p, b) && use_anchor<T>(p, b, c) == anchor; };
-  auto source = [&](int b) -> ResSrc<V> {
-    if constexpr (sizeof(V) == 8) return anchor_src(p, prob_at(p, b));
-    else return recur_src<T>(p, prob_at(p, b), b, c);
-  };
+  auto slot = [&](int j) { return smem + (size_t)(j % D) * kSlot; };
   auto issue = [&](int j) {
     if (j < J) {
       const TileTask& tk = task(j);
-      if (mine(tk.b)) {
+      if (!done_at(p, tk.b)) {
         const ProblemDesc& P = prob_at(p, tk.b);
-        const int N = level_side(P.n, 0);
-        const HaloCells hc = halo_cells(P, N, tk.x0, tk.y0, false);
-        const Columns cl = own_columns(P, N, tk.x0, tk.y0);
-        const ResSrc<V> src = source(tk.b);
-        ResStage<V>& S = st[j % D];
-#pragma unroll
-        for (int s = 0; s < kCells; ++s)
-          if (hc.off[s] >= 0) {
-            cp_async_t(&S.u[tid + s * kThreads], src.u + hc.off[s]);
-            if (src.s) cp_async_t(&S.s[tid + s * kThreads], src.s + hc.off[s]);
-          }
-#pragma unroll
-        for (int r = 0; r < 2; ++r)
-          if (cl.in[r]) {
-            cp_async_t(&S.f[tid + r * kThreads], src.rhs + cl.off[r]);
-            if (src.a) cp_async_t(&S.a[tid + r * kThreads], src.a + cl.off[r]);
-          }
+        if (use_anchor<T>(p, tk.b, c)) {
+          res2_issue<T, double>(p, P, tk, *(ResStage<double>*)slot(j), anchor_src(p, P));
+        } else if constexpr (sizeof(T) == 4) {
+          res2_issue<T, T>(p, P, tk, *(ResStage<T>*)slot(j), recur_src<T>(p, P, tk.b, c));
+        }
       }
     }
     cp_async_commit();
@@ -1022,41 +1067,13 @@ __device__ void residual2(const KernelParams& p, int c, ResStage<V>* st, bool an
     __syncthreads();
     issue(j + D - 2);
     const TileTask& tk = task(j);
-    if (!mine(tk.b)) continue;  // uniform over the CTA
+    if (done_at(p, tk.b)) continue;  // uniform over the CTA
     const ProblemDesc& P = prob_at(p, tk.b);
-    const ResSrc<V> src = source(tk.b);
-    ResStage<V>& S = st[j % D];
-    const int N = level_side(P.n, 0);
-    if (src.images && tile_has_flux(P, N, tk.x0, tk.y0, 2)) {
-      const HaloCells hc = halo_cells(P, N, tk.x0, tk.y0, true);
-#pragma unroll
-      for (int s = 0; s < kCells; ++s)
-        if (hc.off[s] >= 0) S.u[tid + s * kThreads] += (V)hc.ghost[s];
-      __syncthreads();
+    if (use_anchor<T>(p, tk.b, c)) {
+      res2_compute<T, double>(p, P, tk, c, *(ResStage<double>*)slot(j), anchor_src(p, P));
+    } else if constexpr (sizeof(T) == 4) {
+      res2_compute<T, T>(p, P, tk, c, *(ResStage<T>*)slot(j), recur_src<T>(p, P, tk.b, c));
     }
-    const Columns cl = own_columns(P, N, tk.x0, tk.y0);
-    V mx = (V)0, s2 = (V)0;
-    V uc[2], sc[2], cls[2][3];
-#pragma unroll
-    for (int r = 0; r < 2; ++r) {
-      uc[r] = S.u[b0 + (r + 1) * kHX + 1];
-      sc[r] = src.s ? S.s[b0 + (r + 1) * kHX + 1] : (V)1;
-      cls[r][0] = cls[r][1] = cls[r][2] = (V)0;
-    }
-    if (src.s) res_plane<V, true>(S, b0, 0, uc, sc, cls);
-    else res_plane<V, false>(S, b0, 0, uc, sc, cls);
-    const V c0v = cv<V>(P.c0 * (src.s ? 1.0 : 2.0), P.c0_f * (src.s ? 1.0f : 2.0f));
-    const double scale = outer_scale(p, tk.b, c);
-    const float scale32 = outer_scale_f(p, tk.b, c);
-#pragma unroll
-    for (int r = 0; r < 2; ++r) {
-      if (!cl.in[r] || cl.fixed_xy[r]) continue;
-      const V sum = rn_fma(cv<V>(p.w_edge, p.w_edge_f), cls[r][1], cls[r][0]);
-      const V a = src.a ? S.a[tid + r * kThreads] : cv<V>(src.a_scalar, P.a_scalar_f);
-      res_finish<T, V>(src, c0v, sum, uc[r], a, S.f[tid + r * kThreads], scale, scale32,
-                       (T*)p.R + P.off_lvl[0], p.RESP ? p.RESP + P.off_full : nullptr, cl.off[r], mx, s2);
-    }
-    block_flush((double)mx, (double)s2, &p.accum[tk.b].rmax_bits[c & 1], &p.accum[tk.b].rsum2[c & 1]);
   }
   cp_async_wait<0>();
   __syncthreads();
@@ -1065,8 +1082,7 @@ __device__ void residual2(const KernelParams& p, int c, ResStage<V>* st, bool an
 template <typename T, int DIM>
 __device__ void phase_outer(const KernelParams& p, int c, unsigned char* smem) {
   if (DIM == 2) {
-    residual2<T, double>(p, c, (ResStage<double>*)smem, true);
-    if (p.mixed) residual2<T, T>(p, c, (ResStage<T>*)smem, false);
+    residual2<T>(p, c, smem);
     return;
   }
   for_tasks(p, 0, [&](const TileTask& tk) {
@@ -1511,8 +1527,10 @@ __device__ void sweep3_f64(const KernelParams& p, const Phase& ph, int c, const 
   __syncthreads();
 }
 
-// 2-D: one halo tile per task, the CTA's tasks pipelined kSweepStages - 2 deep.
-template <typename T, bool LAST, bool DIAG = false>
+// 2-D: one halo tile per task, the CTA's tasks pipelined kSweepStages - 2 deep, in one pass: whether
+// this is a problem's last sweep of the cycle (adding e / s into the FP64 solution) is decided per
+// tile (two passes, one per kind, cost a pipeline wait and a CTA barrier per skipped tile).
+template <typename T, bool DIAG = false>
 __device__ void sweep2(const KernelParams& p, const Phase& ph, int c, SweepStage<T>* st) {
   constexpr int D = kSweepStages;
   const int l = ph.level;
@@ -1520,7 +1538,7 @@ __device__ void sweep2(const KernelParams& p, const Phase& ph, int c, SweepStage
   const int tid = threadIdx.x;
   const int b0 = (2 * (tid / kTX)) * kHX + (tid % kTX);
   auto task = [&](int j) -> const TileTask& { return p.tasks[t0 + j]; };
-  auto mine = [&](const SweepCtl& sc) { return sc.active && sc.last == LAST; };
+  auto mine = [&](const SweepCtl& sc) { return sc.active; };
   auto issue = [&](int j) {
     if (j < J) {
       const TileTask& tk = task(j);
@@ -1543,7 +1561,7 @@ __device__ void sweep2(const KernelParams& p, const Phase& ph, int c, SweepStage
           if (cl.in[r]) {
             cp_async_t(&S.r[tid + r * kThreads], (const T*)p.R + sc.off + cl.off[r]);
             if (P.hetero) cp_async_t(&S.q[tid + r * kThreads], (const T*)p.Q + sc.off + cl.off[r]);
-            if (LAST) cp_async_t(&S.u[tid + r * kThreads], p.U + P.off_full + cl.off[r]);
+            if (sc.last) cp_async_t(&S.u[tid + r * kThreads], p.U + P.off_full + cl.off[r]);
           }
       }
     }
@@ -1567,7 +1585,8 @@ __device__ void sweep2(const KernelParams& p, const Phase& ph, int c, SweepStage
     if (P.hetero) plane_sums2<T, true>(S, b0, sc.zero_in, ps);
     else plane_sums2<T, false>(S, b0, sc.zero_in, ps);
     T* dst = sweep_parity(p, l, ph.sweep) ? (T*)p.E + sc.off : (T*)p.E2 + sc.off;
-    const double inv_scale = LAST ? inv_scale_at(p, tk.b, c & 1) : 0.0;
+    const bool last = sc.last;
+    const double inv_scale = last ? inv_scale_at(p, tk.b, c & 1) : 0.0;
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
       if (!cl.in[r] || cl.fixed_xy[r]) continue;
@@ -1576,8 +1595,8 @@ __device__ void sweep2(const KernelParams& p, const Phase& ph, int c, SweepStage
       const T e_new = P.hetero ? sweep_update<T, true>(kc, S, slot, cc, CSe, rn_fma(kc.w_e, ps[r].sC, ps[r].sF), ps[r].v)
                                : sweep_update<T, false>(kc, S, slot, cc, CSe, (T)0, ps[r].v);
       if (DIAG) dmx = fmax(dmx, diag_term(e_new - ps[r].v, P.hetero ? S.q[slot] : kc.q_const));
-      if (LAST) p.U[P.off_full + cl.off[r]] = __fma_rn((double)e_new, inv_scale, S.u[slot]);
-      if (!LAST || p.mixed) dst[cl.off[r]] = e_new;
+      if (last) p.U[P.off_full + cl.off[r]] = __fma_rn((double)e_new, inv_scale, S.u[slot]);
+      if (!last || p.mixed) dst[cl.off[r]] = e_new;
     }
     if (DIAG) diag_flush<T>(p, tk.b, c, l, dmx, kc.inv_c);
   }
@@ -2070,13 +2089,8 @@ template <typename T, int DIM>
 __device__ void phase_sweep(const KernelParams& p, const Phase& ph, int c, unsigned char* smem) {
   SweepStage<T>* st = (SweepStage<T>*)smem;
   if (DIM == 2) {
-    if (p.diag) {
-      if (ph.flags & kFinalVisit) sweep2<T, true, true>(p, ph, c, st);
-      sweep2<T, false, true>(p, ph, c, st);
-    } else {
-      if (ph.flags & kFinalVisit) sweep2<T, true>(p, ph, c, st);  // problems whose last sweep this is
-      sweep2<T, false>(p, ph, c, st);
-    }
+    if (p.diag) sweep2<T, true>(p, ph, c, st);
+    else sweep2<T>(p, ph, c, st);
     return;
   }
   if constexpr (sizeof(T) == 4) {
