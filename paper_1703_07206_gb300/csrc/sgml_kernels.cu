@@ -415,6 +415,24 @@ __device__ __forceinline__ HaloCells halo_cells(const ProblemDesc& P, int N, int
   return hc;
 }
 
+// 2-D tiles, whose set-up is paid per tile (no z-march to spread it over): a tile whose halo lies
+// inside the level needs no images, clamps or face tests -- each halo offset is one multiply-add.
+__device__ __forceinline__ bool tile_interior(int N, int x0, int y0) {
+  return x0 >= 1 && y0 >= 1 && x0 + kTX <= N - 1 && y0 + kTY <= N - 1;
+}
+
+__device__ __forceinline__ HaloCells halo_cells_2d(const ProblemDesc& P, int N, int x0, int y0, bool interior) {
+  if (!interior) return halo_cells(P, N, x0, y0, false);
+  HaloCells hc;
+#pragma unroll
+  for (int s = 0; s < kCells; ++s) {
+    const int k = threadIdx.x + s * kThreads;
+    hc.off[s] = k < kHalo ? (y0 - 1 + k / kHX) * N + (x0 - 1 + k % kHX) : -1;
+    hc.ghost[s] = 0.0;
+  }
+  return hc;
+}
+
 __device__ __forceinline__ double z_ghost(const ProblemDesc& P, int z, int N) {
   if (z < 0 && P.face_type[4] == 1) return 2.0 * P.h * P.face_value[4];
   if (z > N - 1 && P.face_type[5] == 1) return 2.0 * P.h * P.face_value[5];
@@ -443,6 +461,20 @@ __device__ __forceinline__ Columns own_columns(const ProblemDesc& P, int N, int 
   }
   cl.dz0 = P.face_type[4] == 0;
   cl.dz1 = P.face_type[5] == 0;
+  return cl;
+}
+
+__device__ __forceinline__ Columns own_columns_2d(const ProblemDesc& P, int N, int x0, int y0, bool interior) {
+  if (!interior) return own_columns(P, N, x0, y0);
+  Columns cl;
+  const int x = x0 + (int)(threadIdx.x % kTX), y = y0 + 2 * (int)(threadIdx.x / kTX);
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    cl.in[r] = true;
+    cl.off[r] = (y + r) * N + x;
+    cl.fixed_xy[r] = false;
+  }
+  cl.dz0 = cl.dz1 = false;
   return cl;
 }
 
@@ -985,8 +1017,9 @@ __device__ __forceinline__ void res2_issue(const KernelParams& p, const ProblemD
                                            ResStage<V>& S, const ResSrc<V>& src) {
   const int tid = threadIdx.x;
   const int N = level_side(P.n, 0);
-  const HaloCells hc = halo_cells(P, N, tk.x0, tk.y0, false);
-  const Columns cl = own_columns(P, N, tk.x0, tk.y0);
+  const bool interior = tile_interior(N, tk.x0, tk.y0);
+  const HaloCells hc = halo_cells_2d(P, N, tk.x0, tk.y0, interior);
+  const Columns cl = own_columns_2d(P, N, tk.x0, tk.y0, interior);
 #pragma unroll
   for (int s = 0; s < kCells; ++s)
     if (hc.off[s] >= 0) {
@@ -1014,7 +1047,7 @@ __device__ __forceinline__ void res2_compute(const KernelParams& p, const Proble
       if (hc.off[s] >= 0) S.u[tid + s * kThreads] += (V)hc.ghost[s];
     __syncthreads();
   }
-  const Columns cl = own_columns(P, N, tk.x0, tk.y0);
+  const Columns cl = own_columns_2d(P, N, tk.x0, tk.y0, tile_interior(N, tk.x0, tk.y0));
   V mx = (V)0, s2 = (V)0;
   V uc[2], sc[2], cls[2][3];
 #pragma unroll
@@ -1546,8 +1579,9 @@ __device__ void sweep2(const KernelParams& p, const Phase& ph, int c, SweepStage
       if (mine(sc)) {
         const ProblemDesc& P = prob_at(p, tk.b);
         const int N = sc.N;
-        const HaloCells hc = halo_cells(P, N, tk.x0, tk.y0, false);
-        const Columns cl = own_columns(P, N, tk.x0, tk.y0);
+        const bool interior = tile_interior(N, tk.x0, tk.y0);
+        const HaloCells hc = halo_cells_2d(P, N, tk.x0, tk.y0, interior);
+        const Columns cl = own_columns_2d(P, N, tk.x0, tk.y0, interior);
         SweepStage<T>& S = st[j % D];
         const T* src = sweep_parity(p, l, ph.sweep) ? (const T*)p.E2 + sc.off : (const T*)p.E + sc.off;
 #pragma unroll
@@ -1578,7 +1612,7 @@ __device__ void sweep2(const KernelParams& p, const Phase& ph, int c, SweepStage
     T dmx = (T)0;  // pseudo-residual times inv_c (DIAG)
     const ProblemDesc& P = prob_at(p, tk.b);
     const int N = sc.N;
-    const Columns cl = own_columns(P, N, tk.x0, tk.y0);
+    const Columns cl = own_columns_2d(P, N, tk.x0, tk.y0, tile_interior(N, tk.x0, tk.y0));
     const SweepStage<T>& S = st[j % D];
     const SweepConst<T> kc = sweep_const<T>(p, P, l);
     PlaneSums<T> ps[2];
