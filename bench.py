@@ -630,6 +630,14 @@ def run_ncu_case(args):
     from paper_1703_07206_gb300 import build, inputs, sgml
     build.build()
     torch.cuda.set_device(0)
+    if args.ncu_workload == "curl":  # v = curl psi (Eq. 14) of a random (2^n + 1)^3 potential: two launches
+        N = 2 ** args.n + 1
+        psi = torch.from_numpy(np.random.default_rng(7).standard_normal((3, N, N, N))).cuda()
+        for _ in range(2):
+            v = sgml.curl(psi)
+        torch.cuda.synchronize()
+        print(json.dumps({"ncu_case": True, "workload": "curl", "n": args.n, "checksum": float(v.abs().sum())}))
+        return
     if args.ncu_workload == "batch":  # the 256 uneven 2-D Helmholtz problems
         probs = inputs.helmholtz_batch_2d()
     else:
@@ -764,8 +772,9 @@ def main():
     ap.add_argument("--ncu-case", action="store_true")
     ap.add_argument("--ncu-cycles", type=int, default=2)
     ap.add_argument("--ncu-solve", action="store_true", help="ncu case: one full solve instead of --ncu-cycles")
-    ap.add_argument("--ncu-workload", default="dielectric", choices=["dielectric", "batch"],
-                    help="ncu case: the 3-D dielectric workload (--n) or the 256-problem 2-D Helmholtz batch")
+    ap.add_argument("--ncu-workload", default="dielectric", choices=["dielectric", "batch", "curl"],
+                    help="ncu case: the 3-D dielectric workload (--n), the 256-problem 2-D Helmholtz batch, "
+                         "or two curl launches on a random (2^n + 1)^3 potential")
     ap.add_argument("--phased", action="store_true")
     ap.add_argument("--tile-x", type=int, default=64, choices=[32, 64], help="column tiles 32 x 16 or 64 x 8")
     ap.add_argument("--slab-z", type=int, default=None,

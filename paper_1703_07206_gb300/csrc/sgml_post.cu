@@ -11,6 +11,7 @@
 // integral of f, coordinates clamped to the unit square / cube).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <string>
 
@@ -37,19 +38,45 @@ __device__ __forceinline__ double deriv(const double* __restrict__ f, int N, dou
   return (f[c + s] - f[c - s]) * inv2h;
 }
 
-// One thread per node: x from the block's threads, y and z from the grid (no index divisions).
-__global__ void __launch_bounds__(128) curl_kernel(int N, double inv2h, const double* __restrict__ psi,
-                                                   double* __restrict__ v) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
-  if (i >= N) return;
-  const long long M = (long long)N * N * N;
+// One thread per (x, y) column of a z-chunk, a block of 32 x 8 columns: the thread walks its chunk
+// in z keeping psi_x and psi_y of planes k - 1, k, k + 1 in registers (their z derivatives), while
+// the x and y derivatives read the neighbouring columns, which the block's other threads load in
+// the same plane step (L1 hits).  Every derivative is the same expression as `deriv`.
+constexpr int kCurlBX = 32, kCurlBY = 8;
+
+__global__ void __launch_bounds__(kCurlBX * kCurlBY) curl_kernel(int N, int zlen, double inv2h,
+                                                                 const double* __restrict__ psi,
+                                                                 double* __restrict__ v) {
+  const int i = blockIdx.x * kCurlBX + threadIdx.x, j = blockIdx.y * kCurlBY + threadIdx.y;
+  const int k0 = blockIdx.z * zlen, k1 = min(N, k0 + zlen);
+  if (i >= N || j >= N || k0 >= k1) return;
+  const long long M = (long long)N * N * N, NN = (long long)N * N;
   const double* px = psi;
   const double* py = psi + M;
   const double* pz = psi + 2 * M;
-  const long long c = ((long long)k * N + j) * N + i;
-  v[c] = deriv(pz, N, inv2h, i, j, k, 1) - deriv(py, N, inv2h, i, j, k, 2);
-  v[M + c] = deriv(px, N, inv2h, i, j, k, 2) - deriv(pz, N, inv2h, i, j, k, 0);
-  v[2 * M + c] = deriv(py, N, inv2h, i, j, k, 0) - deriv(px, N, inv2h, i, j, k, 1);
+  const long long col = (long long)j * N + i;
+  // window of psi_x / psi_y at planes k - 1, k, k + 1 (entries outside 0..N-1 are not used)
+  double xm = k0 > 0 ? px[(k0 - 1) * NN + col] : 0.0, x0 = px[k0 * NN + col];
+  double ym = k0 > 0 ? py[(k0 - 1) * NN + col] : 0.0, y0 = py[k0 * NN + col];
+  for (int k = k0; k < k1; ++k) {
+    const long long c = k * NN + col;
+    const double xp = k + 1 < N ? px[c + NN] : 0.0, yp = k + 1 < N ? py[c + NN] : 0.0;
+    double dzx, dzy;  // d psi_x / dz, d psi_y / dz
+    if (k == 0) {
+      dzx = (-3.0 * x0 + 4.0 * xp - px[c + 2 * NN]) * inv2h;
+      dzy = (-3.0 * y0 + 4.0 * yp - py[c + 2 * NN]) * inv2h;
+    } else if (k == N - 1) {
+      dzx = (3.0 * x0 - 4.0 * xm + px[c - 2 * NN]) * inv2h;
+      dzy = (3.0 * y0 - 4.0 * ym + py[c - 2 * NN]) * inv2h;
+    } else {
+      dzx = (xp - xm) * inv2h;
+      dzy = (yp - ym) * inv2h;
+    }
+    v[c] = deriv(pz, N, inv2h, i, j, k, 1) - dzy;
+    v[M + c] = dzx - deriv(pz, N, inv2h, i, j, k, 0);
+    v[2 * M + c] = deriv(py, N, inv2h, i, j, k, 0) - deriv(px, N, inv2h, i, j, k, 1);
+    xm = x0, x0 = xp, ym = y0, y0 = yp;
+  }
 }
 
 __device__ __forceinline__ bool inside(const double x[3]) {
@@ -264,8 +291,12 @@ int sgml_curl(int n, const double* psi, double* v, void* cuda_stream) {
   if (!device_pointer(psi) || !device_pointer(v)) return post_fail(SGML_ERR_ARG, "psi and v must be device arrays");
   const int N = (1 << n) + 1;
   const double h = 1.0 / (double)(N - 1);
-  const dim3 grid((unsigned)((N + 127) / 128), (unsigned)N, (unsigned)N);
-  curl_kernel<<<grid, 128, 0, (cudaStream_t)cuda_stream>>>(N, 1.0 / (2.0 * h), psi, v);
+  // z-chunks: enough blocks for several waves of the GPU, chunks as long as that allows
+  const int bx = (N + kCurlBX - 1) / kCurlBX, by = (N + kCurlBY - 1) / kCurlBY;
+  const int chunks = std::min(N, std::max(1, (4096 + bx * by - 1) / (bx * by)));
+  const int zlen = (N + chunks - 1) / chunks;
+  const dim3 grid((unsigned)bx, (unsigned)by, (unsigned)((N + zlen - 1) / zlen));
+  curl_kernel<<<grid, dim3(kCurlBX, kCurlBY), 0, (cudaStream_t)cuda_stream>>>(N, zlen, 1.0 / (2.0 * h), psi, v);
   const cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? SGML_OK : post_fail(SGML_ERR_CUDA, cudaGetErrorString(e));
 }

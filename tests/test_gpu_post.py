@@ -32,7 +32,7 @@ def smooth_potential(n, seed, modes=4):
     return psi
 
 
-@pytest.mark.parametrize("n", [4, 5])
+@pytest.mark.parametrize("n", [4, 5, 7])  # 129^3: z-chunks of three planes
 def test_curl_matches_oracle(n):
     rng = np.random.default_rng(900 + n)
     N = 2 ** n + 1
