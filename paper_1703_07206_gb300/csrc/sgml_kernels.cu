@@ -1036,7 +1036,7 @@ __device__ __forceinline__ void res2_issue(const KernelParams& p, const ProblemD
 
 template <typename T, typename V>
 __device__ __forceinline__ void res2_compute(const KernelParams& p, const ProblemDesc& P, const TileTask& tk, int c,
-                                             ResStage<V>& S, const ResSrc<V>& src) {
+                                             ResStage<V>& S, const ResSrc<V>& src, V& mx, V& s2) {
   const int tid = threadIdx.x;
   const int b0 = (2 * (tid / kTX)) * kHX + (tid % kTX);
   const int N = level_side(P.n, 0);
@@ -1048,7 +1048,6 @@ __device__ __forceinline__ void res2_compute(const KernelParams& p, const Proble
     __syncthreads();
   }
   const Columns cl = own_columns_2d(P, N, tk.x0, tk.y0, tile_interior(N, tk.x0, tk.y0));
-  V mx = (V)0, s2 = (V)0;
   V uc[2], sc[2], cls[2][3];
 #pragma unroll
   for (int r = 0; r < 2; ++r) {
@@ -1069,7 +1068,6 @@ __device__ __forceinline__ void res2_compute(const KernelParams& p, const Proble
     res_finish<T, V>(src, c0v, sum, uc[r], a, S.f[tid + r * kThreads], scale, scale32, (T*)p.R + P.off_lvl[0],
                      p.RESP ? p.RESP + P.off_full : nullptr, cl.off[r], mx, s2);
   }
-  block_flush((double)mx, (double)s2, &p.accum[tk.b].rmax_bits[c & 1], &p.accum[tk.b].rsum2[c & 1]);
 }
 
 template <typename T>
@@ -1094,6 +1092,21 @@ __device__ void residual2(const KernelParams& p, int c, unsigned char* smem) {
     }
     cp_async_commit();
   };
+  // The norms of a problem's tiles are summed per thread and flushed (one block reduction and two
+  // atomics) when the CTA moves to another problem: a CTA's tasks run problem by problem, and a
+  // flush per tile costs a CTA barrier and FP64 reductions per 512 nodes.
+  int ab = -1;          // problem whose norms are being summed (-1: none)
+  bool a_anchor = false;  // ... through the FP64 anchor (double sums), else the recurrence (V = T)
+  double dmx = 0.0, ds2 = 0.0;
+  T fmx = (T)0, fs2 = (T)0;
+  auto flush = [&]() {  // uniform over the CTA (block_flush holds CTA barriers)
+    if (ab < 0) return;
+    if (a_anchor) block_flush(dmx, ds2, &p.accum[ab].rmax_bits[c & 1], &p.accum[ab].rsum2[c & 1]);
+    else block_flush((double)fmx, (double)fs2, &p.accum[ab].rmax_bits[c & 1], &p.accum[ab].rsum2[c & 1]);
+    dmx = ds2 = 0.0;
+    fmx = fs2 = (T)0;
+    ab = -1;
+  };
   for (int j = 0; j < D - 2; ++j) issue(j);
   for (int j = 0; j < J; ++j) {
     cp_async_wait<D - 3>();
@@ -1101,13 +1114,19 @@ __device__ void residual2(const KernelParams& p, int c, unsigned char* smem) {
     issue(j + D - 2);
     const TileTask& tk = task(j);
     if (done_at(p, tk.b)) continue;  // uniform over the CTA
+    if (tk.b != ab) {
+      flush();
+      ab = tk.b;
+      a_anchor = use_anchor<T>(p, tk.b, c);
+    }
     const ProblemDesc& P = prob_at(p, tk.b);
-    if (use_anchor<T>(p, tk.b, c)) {
-      res2_compute<T, double>(p, P, tk, c, *(ResStage<double>*)slot(j), anchor_src(p, P));
+    if (a_anchor) {
+      res2_compute<T, double>(p, P, tk, c, *(ResStage<double>*)slot(j), anchor_src(p, P), dmx, ds2);
     } else if constexpr (sizeof(T) == 4) {
-      res2_compute<T, T>(p, P, tk, c, *(ResStage<T>*)slot(j), recur_src<T>(p, P, tk.b, c));
+      res2_compute<T, T>(p, P, tk, c, *(ResStage<T>*)slot(j), recur_src<T>(p, P, tk.b, c), fmx, fs2);
     }
   }
+  flush();
   cp_async_wait<0>();
   __syncthreads();
 }
@@ -1570,65 +1589,91 @@ __device__ void sweep2(const KernelParams& p, const Phase& ph, int c, SweepStage
   const int t0 = s_toff[l][0], J = s_toff[l][1] - s_toff[l][0];
   const int tid = threadIdx.x;
   const int b0 = (2 * (tid / kTX)) * kHX + (tid % kTX);
+  const bool odd = sweep_parity(p, l, ph.sweep) != 0;
+  const T* Esrc = odd ? (const T*)p.E2 : (const T*)p.E;
+  T* Edst = odd ? (T*)p.E : (T*)p.E2;
   auto task = [&](int j) -> const TileTask& { return p.tasks[t0 + j]; };
-  auto mine = [&](const SweepCtl& sc) { return sc.active; };
+  // The control of a tile (SweepCtl, sigma per node or not) is its problem's; a CTA's tasks run
+  // problem by problem, so the loads and the update each keep the control of the last problem
+  // they met instead of re-deriving it per tile.
+  int ib = -1;
+  SweepCtl isc{};
+  bool ihet = false;
   auto issue = [&](int j) {
     if (j < J) {
       const TileTask& tk = task(j);
-      const SweepCtl sc = sweep_ctl(p, ph, tk.b);
-      if (mine(sc)) {
-        const ProblemDesc& P = prob_at(p, tk.b);
-        const int N = sc.N;
+      if (tk.b != ib) {
+        ib = tk.b;
+        isc = sweep_ctl(p, ph, ib);
+        ihet = prob_at(p, ib).hetero != 0;
+      }
+      if (isc.active) {
+        const int N = isc.N;
         const bool interior = tile_interior(N, tk.x0, tk.y0);
-        const HaloCells hc = halo_cells_2d(P, N, tk.x0, tk.y0, interior);
-        const Columns cl = own_columns_2d(P, N, tk.x0, tk.y0, interior);
+        HaloCells hc;
+        Columns cl;
+        if (interior) {
+          hc = halo_cells_2d(s_prob0, N, tk.x0, tk.y0, true);  // the descriptor is not read
+          cl = own_columns_2d(s_prob0, N, tk.x0, tk.y0, true);
+        } else {
+          const ProblemDesc& P = prob_at(p, tk.b);
+          hc = halo_cells(P, N, tk.x0, tk.y0, false);
+          cl = own_columns(P, N, tk.x0, tk.y0);
+        }
         SweepStage<T>& S = st[j % D];
-        const T* src = sweep_parity(p, l, ph.sweep) ? (const T*)p.E2 + sc.off : (const T*)p.E + sc.off;
+        const T* src = Esrc + isc.off;
 #pragma unroll
         for (int s = 0; s < kCells; ++s)
           if (hc.off[s] >= 0) {
-            if (!sc.zero_in) cp_async_t(&S.e[tid + s * kThreads], src + hc.off[s]);
-            if (P.hetero) cp_async_t(&S.s[tid + s * kThreads], (const T*)p.SIG + sc.off + hc.off[s]);
+            if (!isc.zero_in) cp_async_t(&S.e[tid + s * kThreads], src + hc.off[s]);
+            if (ihet) cp_async_t(&S.s[tid + s * kThreads], (const T*)p.SIG + isc.off + hc.off[s]);
           }
 #pragma unroll
         for (int r = 0; r < 2; ++r)
           if (cl.in[r]) {
-            cp_async_t(&S.r[tid + r * kThreads], (const T*)p.R + sc.off + cl.off[r]);
-            if (P.hetero) cp_async_t(&S.q[tid + r * kThreads], (const T*)p.Q + sc.off + cl.off[r]);
-            if (sc.last) cp_async_t(&S.u[tid + r * kThreads], p.U + P.off_full + cl.off[r]);
+            cp_async_t(&S.r[tid + r * kThreads], (const T*)p.R + isc.off + cl.off[r]);
+            if (ihet) cp_async_t(&S.q[tid + r * kThreads], (const T*)p.Q + isc.off + cl.off[r]);
+            if (isc.last) cp_async_t(&S.u[tid + r * kThreads], p.U + prob_at(p, tk.b).off_full + cl.off[r]);
           }
       }
     }
     cp_async_commit();
   };
+  int cb = -1;
+  SweepCtl csc{};
+  bool chet = false;
   for (int j = 0; j < D - 2; ++j) issue(j);
   for (int j = 0; j < J; ++j) {
     cp_async_wait<D - 3>();
     __syncthreads();
     issue(j + D - 2);
     const TileTask& tk = task(j);
-    const SweepCtl sc = sweep_ctl(p, ph, tk.b);
-    if (!mine(sc)) continue;
+    if (tk.b != cb) {
+      cb = tk.b;
+      csc = sweep_ctl(p, ph, cb);
+      chet = prob_at(p, cb).hetero != 0;
+    }
+    if (!csc.active) continue;
     T dmx = (T)0;  // pseudo-residual times inv_c (DIAG)
     const ProblemDesc& P = prob_at(p, tk.b);
-    const int N = sc.N;
+    const int N = csc.N;
     const Columns cl = own_columns_2d(P, N, tk.x0, tk.y0, tile_interior(N, tk.x0, tk.y0));
     const SweepStage<T>& S = st[j % D];
     const SweepConst<T> kc = sweep_const<T>(p, P, l);
     PlaneSums<T> ps[2];
-    if (P.hetero) plane_sums2<T, true>(S, b0, sc.zero_in, ps);
-    else plane_sums2<T, false>(S, b0, sc.zero_in, ps);
-    T* dst = sweep_parity(p, l, ph.sweep) ? (T*)p.E + sc.off : (T*)p.E2 + sc.off;
-    const bool last = sc.last;
+    if (chet) plane_sums2<T, true>(S, b0, csc.zero_in, ps);
+    else plane_sums2<T, false>(S, b0, csc.zero_in, ps);
+    T* dst = Edst + csc.off;
+    const bool last = csc.last;
     const double inv_scale = last ? inv_scale_at(p, tk.b, c & 1) : 0.0;
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
       if (!cl.in[r] || cl.fixed_xy[r]) continue;
       const T CSe = rn_fma(kc.w_e, ps[r].C, ps[r].F);
       const int slot = tid + r * kThreads, cc = b0 + (r + 1) * kHX + 1;
-      const T e_new = P.hetero ? sweep_update<T, true>(kc, S, slot, cc, CSe, rn_fma(kc.w_e, ps[r].sC, ps[r].sF), ps[r].v)
-                               : sweep_update<T, false>(kc, S, slot, cc, CSe, (T)0, ps[r].v);
-      if (DIAG) dmx = fmax(dmx, diag_term(e_new - ps[r].v, P.hetero ? S.q[slot] : kc.q_const));
+      const T e_new = chet ? sweep_update<T, true>(kc, S, slot, cc, CSe, rn_fma(kc.w_e, ps[r].sC, ps[r].sF), ps[r].v)
+                           : sweep_update<T, false>(kc, S, slot, cc, CSe, (T)0, ps[r].v);
+      if (DIAG) dmx = fmax(dmx, diag_term(e_new - ps[r].v, chet ? S.q[slot] : kc.q_const));
       if (last) p.U[P.off_full + cl.off[r]] = __fma_rn((double)e_new, inv_scale, S.u[slot]);
       if (!last || p.mixed) dst[cl.off[r]] = e_new;
     }
