@@ -1012,25 +1012,34 @@ __device__ __forceinline__ ResSrc<T> recur_src(const KernelParams& p, const Prob
 // task's problem takes the FP64 anchor or (mixed form) the FP32 recurrence.  The stage slots are
 // sized for the anchor's FP64 layout, so both kinds of tile share the pipeline (two passes over all
 // tiles, one per kind, cost a pipeline wait and a CTA barrier per skipped tile).
-template <typename T, typename V>
-__device__ __forceinline__ void res2_issue(const KernelParams& p, const ProblemDesc& P, const TileTask& tk,
-                                           ResStage<V>& S, const ResSrc<V>& src) {
+// The loads of a 2-D residual tile: the operand and sigma on the halo, the right-hand side and a at
+// the tile's nodes (pointers already offset to the problem's arrays; P is read only on the level's
+// edges).
+template <typename V>
+__device__ __forceinline__ void res2_issue(const KernelParams& p, const TileTask& tk, int N, ResStage<V>& S,
+                                           const V* u, const V* sg, const double* rhs, const V* a) {
   const int tid = threadIdx.x;
-  const int N = level_side(P.n, 0);
-  const bool interior = tile_interior(N, tk.x0, tk.y0);
-  const HaloCells hc = halo_cells_2d(P, N, tk.x0, tk.y0, interior);
-  const Columns cl = own_columns_2d(P, N, tk.x0, tk.y0, interior);
+  HaloCells hc;
+  Columns cl;
+  if (tile_interior(N, tk.x0, tk.y0)) {
+    hc = halo_cells_2d(s_prob0, N, tk.x0, tk.y0, true);  // the descriptor is not read
+    cl = own_columns_2d(s_prob0, N, tk.x0, tk.y0, true);
+  } else {
+    const ProblemDesc& P = prob_at(p, tk.b);
+    hc = halo_cells(P, N, tk.x0, tk.y0, false);
+    cl = own_columns(P, N, tk.x0, tk.y0);
+  }
 #pragma unroll
   for (int s = 0; s < kCells; ++s)
     if (hc.off[s] >= 0) {
-      cp_async_t(&S.u[tid + s * kThreads], src.u + hc.off[s]);
-      if (src.s) cp_async_t(&S.s[tid + s * kThreads], src.s + hc.off[s]);
+      cp_async_t(&S.u[tid + s * kThreads], u + hc.off[s]);
+      if (sg) cp_async_t(&S.s[tid + s * kThreads], sg + hc.off[s]);
     }
 #pragma unroll
   for (int r = 0; r < 2; ++r)
     if (cl.in[r]) {
-      cp_async_t(&S.f[tid + r * kThreads], src.rhs + cl.off[r]);
-      if (src.a) cp_async_t(&S.a[tid + r * kThreads], src.a + cl.off[r]);
+      cp_async_t(&S.f[tid + r * kThreads], rhs + cl.off[r]);
+      if (a) cp_async_t(&S.a[tid + r * kThreads], a + cl.off[r]);
     }
 }
 
@@ -1078,16 +1087,35 @@ __device__ void residual2(const KernelParams& p, int c, unsigned char* smem) {
   const int t0 = s_toff[0][0], J = s_toff[0][1] - s_toff[0][0];  // level 0
   auto task = [&](int j) -> const TileTask& { return p.tasks[t0 + j]; };
   auto slot = [&](int j) { return smem + (size_t)(j % D) * kSlot; };
+  // The loads keep the sources of the last problem they met (a CTA's tasks run problem by problem).
+  int ib = -1, ikind = 0;  // ikind: 0 none (problem done), 1 FP64 anchor, 2 FP32 recurrence
+  int iN = 0;
+  const void *iu = nullptr, *isg = nullptr, *ia = nullptr;
+  const double* irhs = nullptr;
   auto issue = [&](int j) {
     if (j < J) {
-      const TileTask& tk = task(j);
-      if (!done_at(p, tk.b)) {
-        const ProblemDesc& P = prob_at(p, tk.b);
-        if (use_anchor<T>(p, tk.b, c)) {
-          res2_issue<T, double>(p, P, tk, *(ResStage<double>*)slot(j), anchor_src(p, P));
-        } else if constexpr (sizeof(T) == 4) {
-          res2_issue<T, T>(p, P, tk, *(ResStage<T>*)slot(j), recur_src<T>(p, P, tk.b, c));
+      const TileTask tk = task(j);  // by value: the cp.async statements clobber memory
+      if (tk.b != ib) {
+        ib = tk.b;
+        const ProblemDesc& P = prob_at(p, ib);
+        iN = level_side(P.n, 0);
+        ikind = done_at(p, ib) ? 0 : (use_anchor<T>(p, ib, c) ? 1 : 2);
+        if (ikind == 1) {
+          const ResSrc<double> src = anchor_src(p, P);
+          iu = src.u, isg = src.s, irhs = src.rhs, ia = src.a;
+        } else if (ikind == 2) {
+          if constexpr (sizeof(T) == 4) {
+            const ResSrc<T> src = recur_src<T>(p, P, ib, c);
+            iu = src.u, isg = src.s, irhs = src.rhs, ia = src.a;
+          }
         }
+      }
+      if (ikind == 1) {
+        res2_issue<double>(p, tk, iN, *(ResStage<double>*)slot(j), (const double*)iu, (const double*)isg, irhs,
+                           (const double*)ia);
+      } else if (ikind == 2) {
+        if constexpr (sizeof(T) == 4)
+          res2_issue<T>(p, tk, iN, *(ResStage<T>*)slot(j), (const T*)iu, (const T*)isg, irhs, (const T*)ia);
       }
     }
     cp_async_commit();
@@ -1112,7 +1140,7 @@ __device__ void residual2(const KernelParams& p, int c, unsigned char* smem) {
     cp_async_wait<D - 3>();
     __syncthreads();
     issue(j + D - 2);
-    const TileTask& tk = task(j);
+    const TileTask tk = task(j);
     if (done_at(p, tk.b)) continue;  // uniform over the CTA
     if (tk.b != ab) {
       flush();
@@ -1601,7 +1629,7 @@ __device__ void sweep2(const KernelParams& p, const Phase& ph, int c, SweepStage
   bool ihet = false;
   auto issue = [&](int j) {
     if (j < J) {
-      const TileTask& tk = task(j);
+      const TileTask tk = task(j);  // by value: the cp.async statements clobber memory
       if (tk.b != ib) {
         ib = tk.b;
         isc = sweep_ctl(p, ph, ib);
@@ -1642,24 +1670,26 @@ __device__ void sweep2(const KernelParams& p, const Phase& ph, int c, SweepStage
   int cb = -1;
   SweepCtl csc{};
   bool chet = false;
+  SweepConst<T> kc{};
   for (int j = 0; j < D - 2; ++j) issue(j);
   for (int j = 0; j < J; ++j) {
     cp_async_wait<D - 3>();
     __syncthreads();
     issue(j + D - 2);
-    const TileTask& tk = task(j);
+    const TileTask tk = task(j);
     if (tk.b != cb) {
       cb = tk.b;
       csc = sweep_ctl(p, ph, cb);
-      chet = prob_at(p, cb).hetero != 0;
+      const ProblemDesc& P = prob_at(p, cb);
+      chet = P.hetero != 0;
+      kc = sweep_const<T>(p, P, l);
     }
     if (!csc.active) continue;
     T dmx = (T)0;  // pseudo-residual times inv_c (DIAG)
-    const ProblemDesc& P = prob_at(p, tk.b);
     const int N = csc.N;
-    const Columns cl = own_columns_2d(P, N, tk.x0, tk.y0, tile_interior(N, tk.x0, tk.y0));
+    const Columns cl = tile_interior(N, tk.x0, tk.y0) ? own_columns_2d(s_prob0, N, tk.x0, tk.y0, true)
+                                                      : own_columns(prob_at(p, tk.b), N, tk.x0, tk.y0);
     const SweepStage<T>& S = st[j % D];
-    const SweepConst<T> kc = sweep_const<T>(p, P, l);
     PlaneSums<T> ps[2];
     if (chet) plane_sums2<T, true>(S, b0, csc.zero_in, ps);
     else plane_sums2<T, false>(S, b0, csc.zero_in, ps);
@@ -1674,7 +1704,7 @@ __device__ void sweep2(const KernelParams& p, const Phase& ph, int c, SweepStage
       const T e_new = chet ? sweep_update<T, true>(kc, S, slot, cc, CSe, rn_fma(kc.w_e, ps[r].sC, ps[r].sF), ps[r].v)
                            : sweep_update<T, false>(kc, S, slot, cc, CSe, (T)0, ps[r].v);
       if (DIAG) dmx = fmax(dmx, diag_term(e_new - ps[r].v, chet ? S.q[slot] : kc.q_const));
-      if (last) p.U[P.off_full + cl.off[r]] = __fma_rn((double)e_new, inv_scale, S.u[slot]);
+      if (last) p.U[prob_at(p, tk.b).off_full + cl.off[r]] = __fma_rn((double)e_new, inv_scale, S.u[slot]);
       if (!last || p.mixed) dst[cl.off[r]] = e_new;
     }
     if (DIAG) diag_flush<T>(p, tk.b, c, l, dmx, kc.inv_c);

@@ -38,43 +38,71 @@ __device__ __forceinline__ double deriv(const double* __restrict__ f, int N, dou
   return (f[c + s] - f[c - s]) * inv2h;
 }
 
-// One thread per (x, y) column of a z-chunk, a block of 32 x 8 columns: the thread walks its chunk
-// in z keeping psi_x and psi_y of planes k - 1, k, k + 1 in registers (their z derivatives), while
-// the x and y derivatives read the neighbouring columns, which the block's other threads load in
-// the same plane step (L1 hits).  Every derivative is the same expression as `deriv`.
+// Nodes on the faces of the cube (2 N^2 + 4 (N - 1)(N - 2) of them), one thread each: one-sided
+// differences where a neighbour is missing.  Face index t: the planes z = 0 and z = N - 1 first,
+// then, plane by plane, the ring of each inner plane.
+__global__ void curl_faces_kernel(int N, double inv2h, const double* __restrict__ psi, double* __restrict__ v) {
+  const long long NN = (long long)N * N, ring = 4LL * (N - 1), total = 2 * NN + (long long)(N - 2) * ring;
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= total) return;
+  int i, j, k;
+  if (t < 2 * NN) {
+    k = t < NN ? 0 : N - 1;
+    const long long r = t % NN;
+    j = (int)(r / N);
+    i = (int)(r % N);
+  } else {
+    const long long r = t - 2 * NN;
+    k = 1 + (int)(r / ring);
+    const int q = (int)(r % ring);  // ring position: y = 0 row, y = N - 1 row, then x = 0 / x = N - 1 columns
+    if (q < N) {
+      j = 0, i = q;
+    } else if (q < 2 * N) {
+      j = N - 1, i = q - N;
+    } else {
+      const int m = q - 2 * N;  // 0 .. 2 (N - 2) - 1
+      j = 1 + m / 2;
+      i = (m & 1) ? N - 1 : 0;
+    }
+  }
+  const long long M = NN * N;
+  const double* px = psi;
+  const double* py = psi + M;
+  const double* pz = psi + 2 * M;
+  const long long c = ((long long)k * N + j) * N + i;
+  v[c] = deriv(pz, N, inv2h, i, j, k, 1) - deriv(py, N, inv2h, i, j, k, 2);
+  v[M + c] = deriv(px, N, inv2h, i, j, k, 2) - deriv(pz, N, inv2h, i, j, k, 0);
+  v[2 * M + c] = deriv(py, N, inv2h, i, j, k, 0) - deriv(px, N, inv2h, i, j, k, 1);
+}
+
+// Inner nodes (1 <= i, j, k <= N - 2): one thread per (x, y) column of a z-chunk, a block of 32 x 8
+// columns; the thread walks its chunk in z keeping psi_x and psi_y of planes k - 1, k, k + 1 in
+// registers (their z derivatives), while the x and y derivatives read the neighbouring columns,
+// which the block's other threads load in the same plane step (L1 hits).  GB300's FP64 pipe bounds
+// this kernel, so a node takes 12 FP64 instructions: each component is the difference of two
+// central differences, scaled once, ((f_a(+) - f_a(-)) - (f_b(+) - f_b(-))) / 2h; the faces are a
+// kernel of their own, so no warp carries their one-sided arithmetic.
 constexpr int kCurlBX = 32, kCurlBY = 8;
 
 __global__ void __launch_bounds__(kCurlBX * kCurlBY) curl_kernel(int N, int zlen, double inv2h,
                                                                  const double* __restrict__ psi,
                                                                  double* __restrict__ v) {
-  const int i = blockIdx.x * kCurlBX + threadIdx.x, j = blockIdx.y * kCurlBY + threadIdx.y;
-  const int k0 = blockIdx.z * zlen, k1 = min(N, k0 + zlen);
-  if (i >= N || j >= N || k0 >= k1) return;
+  const int i = 1 + blockIdx.x * kCurlBX + threadIdx.x, j = 1 + blockIdx.y * kCurlBY + threadIdx.y;
+  const int k0 = 1 + blockIdx.z * zlen, k1 = min(N - 1, k0 + zlen);
+  if (i >= N - 1 || j >= N - 1 || k0 >= k1) return;
   const long long M = (long long)N * N * N, NN = (long long)N * N;
   const double* px = psi;
   const double* py = psi + M;
   const double* pz = psi + 2 * M;
   const long long col = (long long)j * N + i;
-  // window of psi_x / psi_y at planes k - 1, k, k + 1 (entries outside 0..N-1 are not used)
-  double xm = k0 > 0 ? px[(k0 - 1) * NN + col] : 0.0, x0 = px[k0 * NN + col];
-  double ym = k0 > 0 ? py[(k0 - 1) * NN + col] : 0.0, y0 = py[k0 * NN + col];
+  double xm = px[(k0 - 1) * NN + col], x0 = px[k0 * NN + col];  // psi_x, psi_y at planes k - 1, k
+  double ym = py[(k0 - 1) * NN + col], y0 = py[k0 * NN + col];
   for (int k = k0; k < k1; ++k) {
     const long long c = k * NN + col;
-    const double xp = k + 1 < N ? px[c + NN] : 0.0, yp = k + 1 < N ? py[c + NN] : 0.0;
-    double dzx, dzy;  // d psi_x / dz, d psi_y / dz
-    if (k == 0) {
-      dzx = (-3.0 * x0 + 4.0 * xp - px[c + 2 * NN]) * inv2h;
-      dzy = (-3.0 * y0 + 4.0 * yp - py[c + 2 * NN]) * inv2h;
-    } else if (k == N - 1) {
-      dzx = (3.0 * x0 - 4.0 * xm + px[c - 2 * NN]) * inv2h;
-      dzy = (3.0 * y0 - 4.0 * ym + py[c - 2 * NN]) * inv2h;
-    } else {
-      dzx = (xp - xm) * inv2h;
-      dzy = (yp - ym) * inv2h;
-    }
-    v[c] = deriv(pz, N, inv2h, i, j, k, 1) - dzy;
-    v[M + c] = dzx - deriv(pz, N, inv2h, i, j, k, 0);
-    v[2 * M + c] = deriv(py, N, inv2h, i, j, k, 0) - deriv(px, N, inv2h, i, j, k, 1);
+    const double xp = px[c + NN], yp = py[c + NN];
+    v[c] = ((pz[c + N] - pz[c - N]) - (yp - ym)) * inv2h;
+    v[M + c] = ((xp - xm) - (pz[c + 1] - pz[c - 1])) * inv2h;
+    v[2 * M + c] = ((py[c + 1] - py[c - 1]) - (px[c + N] - px[c - N])) * inv2h;
     xm = x0, x0 = xp, ym = y0, y0 = yp;
   }
 }
@@ -291,12 +319,16 @@ int sgml_curl(int n, const double* psi, double* v, void* cuda_stream) {
   if (!device_pointer(psi) || !device_pointer(v)) return post_fail(SGML_ERR_ARG, "psi and v must be device arrays");
   const int N = (1 << n) + 1;
   const double h = 1.0 / (double)(N - 1);
-  // z-chunks: enough blocks for several waves of the GPU, chunks as long as that allows
-  const int bx = (N + kCurlBX - 1) / kCurlBX, by = (N + kCurlBY - 1) / kCurlBY;
-  const int chunks = std::min(N, std::max(1, (4096 + bx * by - 1) / (bx * by)));
-  const int zlen = (N + chunks - 1) / chunks;
-  const dim3 grid((unsigned)bx, (unsigned)by, (unsigned)((N + zlen - 1) / zlen));
-  curl_kernel<<<grid, dim3(kCurlBX, kCurlBY), 0, (cudaStream_t)cuda_stream>>>(N, zlen, 1.0 / (2.0 * h), psi, v);
+  // inner nodes in z-chunks: enough blocks for several waves of the GPU, chunks as long as that allows
+  const int Ni = N - 2;  // inner nodes per side (N >= 3)
+  const int bx = (Ni + kCurlBX - 1) / kCurlBX, by = (Ni + kCurlBY - 1) / kCurlBY;
+  const int chunks = std::min(Ni, std::max(1, (4096 + bx * by - 1) / (bx * by)));
+  const int zlen = (Ni + chunks - 1) / chunks;
+  const dim3 grid((unsigned)bx, (unsigned)by, (unsigned)((Ni + zlen - 1) / zlen));
+  const double inv2h = 1.0 / (2.0 * h);
+  curl_kernel<<<grid, dim3(kCurlBX, kCurlBY), 0, (cudaStream_t)cuda_stream>>>(N, zlen, inv2h, psi, v);
+  const long long faces = 2LL * N * N + 4LL * (N - 1) * (N - 2);
+  curl_faces_kernel<<<(unsigned)((faces + 255) / 256), 256, 0, (cudaStream_t)cuda_stream>>>(N, inv2h, psi, v);
   const cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? SGML_OK : post_fail(SGML_ERR_CUDA, cudaGetErrorString(e));
 }
