@@ -546,6 +546,10 @@ __device__ __forceinline__ void cp_async_t(T* smem, const T* gmem) {
 #endif
 constexpr int kSweepStages = SGML_SWEEP_STAGES;  // loads issued kSweepStages - 2 planes ahead
 constexpr int kOuterStages = SGML_OUTER_STAGES;  // loads issued kOuterStages - 3 planes ahead (three resident)
+// A z-piece of at most kSweepStages - 1 planes issues all its planes before its first step, whose wait
+// leaves kSweepStages - 3 copy groups pending: plane 0 is then complete only while the piece has more
+// planes than that, which its three-plane minimum guarantees for four or five stages (not six).
+static_assert(kSweepStages >= 4 && kSweepStages <= 5, "sweep pipelines are written for 4 or 5 stages");
 
 template <typename T>
 struct SweepStage {
