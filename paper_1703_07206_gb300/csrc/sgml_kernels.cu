@@ -756,6 +756,56 @@ __device__ __forceinline__ void res_finish(const ResSrc<V>& src, V c0v, V sum, V
   }
 }
 
+// A fresh solve whose lift is zero -- every Dirichlet value and every prescribed flux zero, and not an
+// Eq. 10 problem (whose residuals follow the mean projection) -- starts from u = 0, so its first
+// residual is r = f - delta L 0 = f exactly at every unknown: the anchor's values, bits included
+// (the stencil terms are exact zeros), without reading u and sigma or spending FP64 instructions
+// on the stencil.
+template <int DIM>
+__device__ __forceinline__ bool zero_lift(const ProblemDesc& P) {
+  if (P.project_mean) return false;
+#pragma unroll
+  for (int k = 0; k < 2 * DIM; ++k)
+    if (P.face_value[k] != 0.0) return false;
+  return true;
+}
+
+// The anchor's bookkeeping of one unknown whose residual is r = f: norms and the float pair.
+__device__ __forceinline__ void res_of_source(double f, float2* RES, long long idx, double& mx, double& s2) {
+  mx = nan_max(mx, fabs(f));
+  s2 = fma(f, f, s2);
+  if (RES) {
+    const float hi = (float)f;
+    RES[idx] = make_float2(hi, (float)(f - (double)hi));
+  }
+}
+
+template <typename T>
+__device__ void residual3_zero(const KernelParams& p, const TileTask& tk, int c) {
+  const ProblemDesc& P = prob_at(p, tk.b);
+  const int N = level_side(P.n, 0);
+  const Columns cl = own_columns(P, N, tk.x0, tk.y0);
+  const double scale = outer_scale(p, tk.b, c);
+  T* R0 = (T*)p.R + P.off_lvl[0];
+  float2* RES = p.RESP ? p.RESP + P.off_full : nullptr;
+  const double* F = p.F + P.off_full;
+  const long long NN = (long long)N * N;
+  double mx = 0.0, s2 = 0.0;
+#pragma unroll 4
+  for (int z = tk.z0; z < tk.z0 + tk.nz; ++z) {
+    if (z_fixed(cl, z, N)) continue;
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      if (!cl.in[r] || cl.fixed_xy[r]) continue;
+      const long long idx = (long long)z * NN + cl.off[r];
+      const double f = F[idx];
+      res_of_source(f, RES, idx, mx, s2);
+      R0[idx] = (T)(f * scale);
+    }
+  }
+  block_flush(mx, s2, &p.accum[tk.b].rmax_bits[c & 1], &p.accum[tk.b].rsum2[c & 1]);
+}
+
 template <typename T, typename V, bool HET>
 __device__ void residual3(const KernelParams& p, const TileTask& tk, int c, ResStage<V>* st, const ResSrc<V>& src) {
   constexpr int D = kOuterStages;
@@ -1083,6 +1133,24 @@ __device__ __forceinline__ void res2_compute(const KernelParams& p, const Proble
   }
 }
 
+// 2-D tile of a fresh zero-lift problem's first residual (r = f, see residual3_zero).
+template <typename T>
+__device__ __forceinline__ void res2_zero(const KernelParams& p, const ProblemDesc& P, const TileTask& tk, int c,
+                                          double& mx, double& s2) {
+  const int N = level_side(P.n, 0);
+  const Columns cl = own_columns_2d(P, N, tk.x0, tk.y0, tile_interior(N, tk.x0, tk.y0));
+  const double scale = outer_scale(p, tk.b, c);
+  T* R0 = (T*)p.R + P.off_lvl[0];
+  float2* RES = p.RESP ? p.RESP + P.off_full : nullptr;
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    if (!cl.in[r] || cl.fixed_xy[r]) continue;
+    const double f = p.F[P.off_full + cl.off[r]];
+    res_of_source(f, RES, cl.off[r], mx, s2);
+    R0[cl.off[r]] = (T)(f * scale);
+  }
+}
+
 template <typename T>
 __device__ void residual2(const KernelParams& p, int c, unsigned char* smem) {
   constexpr int D = kOuterStages;
@@ -1103,7 +1171,7 @@ __device__ void residual2(const KernelParams& p, int c, unsigned char* smem) {
         ib = tk.b;
         const ProblemDesc& P = prob_at(p, ib);
         iN = level_side(P.n, 0);
-        ikind = done_at(p, ib) ? 0 : (use_anchor<T>(p, ib, c) ? 1 : 2);
+        ikind = done_at(p, ib) ? 0 : (c == 0 && p.fresh && zero_lift<2>(P) ? 3 : (use_anchor<T>(p, ib, c) ? 1 : 2));
         if (ikind == 1) {
           const ResSrc<double> src = anchor_src(p, P);
           iu = src.u, isg = src.s, irhs = src.rhs, ia = src.a;
@@ -1128,12 +1196,12 @@ __device__ void residual2(const KernelParams& p, int c, unsigned char* smem) {
   // atomics) when the CTA moves to another problem: a CTA's tasks run problem by problem, and a
   // flush per tile costs a CTA barrier and FP64 reductions per 512 nodes.
   int ab = -1;          // problem whose norms are being summed (-1: none)
-  bool a_anchor = false;  // ... through the FP64 anchor (double sums), else the recurrence (V = T)
+  int akind = 0;        // ... through the FP64 anchor (1) or r = f (3): double sums; the recurrence (2): V = T
   double dmx = 0.0, ds2 = 0.0;
   T fmx = (T)0, fs2 = (T)0;
   auto flush = [&]() {  // uniform over the CTA (block_flush holds CTA barriers)
     if (ab < 0) return;
-    if (a_anchor) block_flush(dmx, ds2, &p.accum[ab].rmax_bits[c & 1], &p.accum[ab].rsum2[c & 1]);
+    if (akind != 2) block_flush(dmx, ds2, &p.accum[ab].rmax_bits[c & 1], &p.accum[ab].rsum2[c & 1]);
     else block_flush((double)fmx, (double)fs2, &p.accum[ab].rmax_bits[c & 1], &p.accum[ab].rsum2[c & 1]);
     dmx = ds2 = 0.0;
     fmx = fs2 = (T)0;
@@ -1149,10 +1217,12 @@ __device__ void residual2(const KernelParams& p, int c, unsigned char* smem) {
     if (tk.b != ab) {
       flush();
       ab = tk.b;
-      a_anchor = use_anchor<T>(p, tk.b, c);
+      akind = c == 0 && p.fresh && zero_lift<2>(prob_at(p, ab)) ? 3 : (use_anchor<T>(p, tk.b, c) ? 1 : 2);
     }
     const ProblemDesc& P = prob_at(p, tk.b);
-    if (a_anchor) {
+    if (akind == 3) {
+      res2_zero<T>(p, P, tk, c, dmx, ds2);
+    } else if (akind == 1) {
       res2_compute<T, double>(p, P, tk, c, *(ResStage<double>*)slot(j), anchor_src(p, P), dmx, ds2);
     } else if constexpr (sizeof(T) == 4) {
       res2_compute<T, T>(p, P, tk, c, *(ResStage<T>*)slot(j), recur_src<T>(p, P, tk.b, c), fmx, fs2);
@@ -1172,7 +1242,9 @@ __device__ void phase_outer(const KernelParams& p, int c, unsigned char* smem) {
   for_tasks(p, 0, [&](const TileTask& tk) {
     if (done_at(p, tk.b)) return;
     const ProblemDesc& P = prob_at(p, tk.b);
-    if (use_anchor<T>(p, tk.b, c)) {
+    if (c == 0 && p.fresh && zero_lift<3>(P)) {
+      residual3_zero<T>(p, tk, c);
+    } else if (use_anchor<T>(p, tk.b, c)) {
       const ResSrc<double> src = anchor_src(p, P);
       if (P.hetero) residual3<T, double, true>(p, tk, c, (ResStage<double>*)smem, src);
       else residual3<T, double, false>(p, tk, c, (ResStage<double>*)smem, src);
