@@ -114,6 +114,31 @@ def test_batch_of_uneven_problems_matches_individual_oracle_solves():
         assert rel_l2(g.get_solution(b), u_ref) <= 1e-12, b
 
 
+def test_3d_batch_mixing_zero_and_nonzero_lifts_matches_oracle_per_cycle():
+    """A 3-D batch of uneven problems in which some start from a zero lift (every Dirichlet value and
+    flux zero: the first residual is f itself, taken without the stencil) and others carry Dirichlet
+    values or fluxes (the first residual through the FP64 stencil).  FP64 form: after one and after
+    three cycles each problem equals the oracle's iterate; both forms: converged solutions agree."""
+    probs = [inputs.random_problem(3, 3, seed=300),
+             with_dirichlet_values(inputs.random_problem(3, 4, seed=301, helmholtz=False)),
+             inputs.random_problem(3, 2, seed=302, flux=True),
+             inputs.random_problem(3, 4, seed=303, hetero=False, helmholtz=False, mixed_bc=False),
+             inputs.random_problem(3, 3, seed=304, flux=True)]
+    for k in (1, 3):
+        g = gpu_grid(probs, sgml.FP64)
+        g.run_cycle(k)
+        for b, d in enumerate(probs):
+            u_ref = oracle_cycles(oracle_problem(d), d["f"], k)
+            assert rel_l2(g.get_solution(b), u_ref) <= 1e-12, (k, b)
+    for precision in (sgml.FP64, sgml.MIXED):
+        g = gpu_grid(probs, precision, max_cycles=400)
+        st, cyc, rel = g.solve_to_tol(1e-12)
+        assert st == sgml.OK
+        for b, d in enumerate(probs):
+            u_ref, _, _ = oracle_problem(d).solve(d["f"], tol=1e-12, max_cycles=400)
+            assert rel_l2(g.get_solution(b), u_ref) <= 1e-10, (precision, b)
+
+
 def test_residual_entry_point_matches_oracle():
     d = inputs.random_problem(3, 4, seed=301, flux=True)
     p = oracle_problem(d)
