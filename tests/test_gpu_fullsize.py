@@ -105,3 +105,64 @@ def test_mixed_recurrence_drift_at_257_cubed():
         assert drift <= 0.05, (j, hist[j], exact)
     g.close()
     print(f"largest recurrence drift over the sampled cycles: {worst:.2e}")
+
+
+def sine_symbol(dim, n):
+    """Eigenvalue of the radial stencil (Eq. 5, consistent constant) on the mode
+    sin(pi x) sin(pi y) (sin(pi z)) of a 2^n + 1 grid with Dirichlet faces: the sum over the
+    neighbours o of w_o (prod_d cos(pi h o_d) - 1), times kappa_d / h^2."""
+    import itertools
+    import math
+    h = 1.0 / 2 ** n
+    kappa = (math.sqrt(2.0) - 1.0) if dim == 2 else 2.0 / (2.0 + 8.0 / math.sqrt(2.0) + 8.0 / math.sqrt(3.0))
+    lam = 0.0
+    for o in itertools.product((-1, 0, 1), repeat=dim):
+        nz = sum(1 for v in o if v)
+        if nz:
+            lam += (math.prod(math.cos(math.pi * h * v) for v in o) - 1.0) / math.sqrt(nz)
+    return kappa / h ** 2 * lam
+
+
+def sine_source(dim, n):
+    """f = Lap(prod sin(pi x_d)) = -dim pi^2 prod sin(pi x_d) on the nodes, built from outer
+    products (the 3-D grid at n = 10 holds 1.08e9 nodes)."""
+    s = np.sin(np.pi * np.linspace(0.0, 1.0, 2 ** n + 1))
+    mode = np.multiply.outer(s, s) if dim == 2 else np.multiply.outer(np.multiply.outer(s, s), s)
+    mode *= -dim * np.pi ** 2
+    return mode
+
+
+@pytest.mark.parametrize("dim,n,tol", [(2, 12, 1e-9), (3, 10, 1e-10)], ids=["4097sq", "1025cubed"])
+def test_largest_grids_solve_to_the_closed_form_discrete_solution(dim, n, tol):
+    """The largest grids the library accepts (n = 12 in 2-D, 16.8 M nodes; n = 10 in 3-D, 1.08e9
+    nodes), mixed form, default launch: a sine mode is an eigenvector of the stencil with Dirichlet
+    faces, so the discrete solution is f / lambda_h in closed form; the converged GPU solution must
+    equal it at sampled nodes to within what the residual allows (||delta L^-1|| < 1), and the
+    oracle's residual there must be at the tolerance.  The tolerances sit above the floor that
+    rounding u to FP64 sets on any residual, about 1e-16 ||delta L|| ||u|| / ||f||: 2.4e-10 at 4097^2
+    (measured, in both forms), ~2e-11 at 1025^3."""
+    import torch
+    nodes = (2 ** n + 1) ** dim
+    free_dev, _ = torch.cuda.mem_get_info()
+    if free_dev < 90 * nodes:  # ~72 B per node in the mixed form, with margin
+        pytest.skip(f"needs {90 * nodes / 2**30:.0f} GiB of free device memory")
+    with open("/proc/meminfo") as fh:
+        avail = next(int(l.split()[1]) * 1024 for l in fh if l.startswith("MemAvailable"))
+    if avail < 40 * nodes:  # f, u and temporaries in host memory
+        pytest.skip(f"needs {40 * nodes / 2**30:.0f} GiB of free host memory")
+    f = sine_source(dim, n)
+    d = inputs._problem(dim, n, f)
+    g = sgml.Grid(dim, [n], precision=sgml.MIXED)
+    g.set_params(max_cycles=100)
+    sgml.problem_into_grid(g, 0, d)
+    st, cyc, rel = g.solve_to_tol(tol)
+    assert st == sgml.OK and rel[0] <= tol
+    u = g.get_solution(0)
+    g.close()
+    lam = sine_symbol(dim, n)
+    rng = np.random.default_rng(dim * 100 + n)
+    idx = rng.choice(u.size, size=4000, replace=False)
+    want = f.ravel()[idx] / lam
+    got = u.ravel()[idx]
+    assert np.abs(got - want).max() <= tol * dim * np.pi ** 2  # ||e|| <= ||delta L^-1|| ||r|| <= ||r||
+    assert sampled_rel_residual(d, u, count=2000, seed=3) <= 1.2 * tol
