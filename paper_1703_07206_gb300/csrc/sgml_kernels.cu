@@ -2405,6 +2405,122 @@ __device__ void phase_restrict(const KernelParams& p, int l) {
   });
 }
 
+// The same restriction for a 3-D level l as a z-march over the level-l tiles of the work partition:
+// the level-(l-1) planes 2z - 1, 2z, 2z + 1 of the tile's footprint ((2 kTX + 1) x (2 kTY + 1) cells,
+// images applied) are staged in shared memory once per tile -- an odd plane serves two level-l planes
+// -- and every node forms its in-plane 3 x 3 sums from shared memory, in the operation order of
+// phase_restrict (bit-identical results).  A row phase re-reads the shared rows and planes of the
+// finer level through L2 (2.25x); here each footprint cell is fetched once per tile.  Nodes of tiles
+// the partition leaves out (all on a Dirichlet face) are not written: their values reach only
+// Dirichlet nodes of the coarser levels, which no stencil reads.
+constexpr int kRX = 2 * kTX + 1, kRY = 2 * kTY + 1, kRCells = kRX * kRY;
+constexpr int kRSlots = (kRCells + kThreads - 1) / kThreads;
+constexpr int kRestrictStages = 4;  // loads issued two fine planes ahead
+
+template <typename T>
+struct RestrictStage {
+  T v[kRSlots * kThreads];  // one fine plane of the footprint, row-major (row = kRX cells)
+};
+static_assert(sizeof(RestrictStage<float>) * kRestrictStages <= phase_smem_bytes<float>(), "shared memory");
+static_assert(sizeof(RestrictStage<double>) * kRestrictStages <= phase_smem_bytes<double>(), "shared memory");
+
+// Kept out of line with plain arguments, so that its registers do not enter the allocation of the
+// persistent kernel's other phases.
+template <typename T>
+__device__ __noinline__ void restrict3(const T* __restrict__ src, T* __restrict__ dst, int N, int x0, int y0, int z0,
+                                       int nz, RestrictStage<T>* st) {
+  constexpr int D = kRestrictStages;
+  const int Ns = 2 * N - 1;
+  const long long NNs = (long long)Ns * Ns, NN = (long long)N * N;
+  const int tid = threadIdx.x, tx = tid % kTX, ty = tid / kTX;
+  const int X0 = 2 * x0 - 1, Y0 = 2 * y0 - 1;
+  const int nfine = 2 * nz + 1;  // fine planes 2 z0 - 1 .. 2 (z0 + nz - 1) + 1
+  // footprint cell c of the thread: fine (X, Y) = (X0 + c % kRX, Y0 + c / kRX), images applied;
+  // cells past the image of the far edge serve no node of the level and are not fetched (-1)
+  int coff[kRSlots];
+#pragma unroll
+  for (int s = 0; s < kRSlots; ++s) {
+    const int c = tid + s * kThreads;
+    const int X = X0 + c % kRX, Y = Y0 + c / kRX;
+    coff[s] = (c < kRCells && X <= Ns && Y <= Ns) ? refl(Y, Ns) * Ns + refl(X, Ns) : -1;
+  }
+  auto issue = [&](int k) {
+    if (k < nfine) {
+      const T* plane = src + (long long)refl(2 * z0 - 1 + k, Ns) * NNs;
+      T* v = st[k % D].v;
+#pragma unroll
+      for (int s = 0; s < kRSlots; ++s)
+        if (coff[s] >= 0) cp_async_t(&v[tid + s * kThreads], plane + coff[s]);
+    }
+    cp_async_commit();
+  };
+  const int x = x0 + tx;
+  bool in[2];
+  int off[2];
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    const int y = y0 + 2 * ty + r;
+    in[r] = x < N && y < N;
+    off[r] = y * N + x;
+  }
+  for (int k = 0; k < D - 2; ++k) issue(k);
+  T acc[2] = {(T)0, (T)0};
+  for (int k = 0; k < nfine; ++k) {
+    cp_async_wait<D - 3>();
+    __syncthreads();
+    issue(k + D - 2);
+    const T* v = st[k % D].v;
+    T q[2];
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      T accz = (T)0;
+#pragma unroll
+      for (int dy = 0; dy < 3; ++dy) {
+        const T* row = v + (2 * (2 * ty + r) + dy) * kRX + 2 * tx;
+        accz = rn_fma(dy == 1 ? (T)0.5 : (T)0.25, restrict_line(row[0], row[1], row[2]), accz);
+      }
+      q[r] = accz;
+    }
+    // fine plane k is plane dz = k - 2 j of the level-l plane z0 + j
+    if (k & 1) {
+#pragma unroll
+      for (int r = 0; r < 2; ++r) acc[r] = rn_fma((T)0.5, q[r], acc[r]);
+    } else {
+      if (k >= 2) {
+        const long long zoff = (long long)(z0 + k / 2 - 1) * NN;
+#pragma unroll
+        for (int r = 0; r < 2; ++r)
+          if (in[r]) dst[zoff + off[r]] = rn_fma((T)0.25, q[r], acc[r]);
+      }
+#pragma unroll
+      for (int r = 0; r < 2; ++r) acc[r] = rn_fma((T)0.25, q[r], (T)0);
+    }
+  }
+  cp_async_wait<0>();
+  __syncthreads();
+}
+
+// Restriction passes of 3-D problems into levels 1 .. kTiledRestrictLevels run as tile z-marches;
+// coarser levels (a few thousand nodes or fewer per problem) keep the row phase.
+#ifndef SGML_TILED_RESTRICT_LEVELS
+#define SGML_TILED_RESTRICT_LEVELS 2
+#endif
+constexpr int kTiledRestrictLevels = SGML_TILED_RESTRICT_LEVELS;
+
+template <typename T, int DIM>
+__device__ void phase_restrict_any(const KernelParams& p, int l, unsigned char* smem) {
+  if (DIM == 3 && l <= kTiledRestrictLevels) {
+    for_tasks(p, l, [&](const TileTask& tk) {
+      if (done_at(p, tk.b)) return;
+      const ProblemDesc& P = prob_at(p, tk.b);
+      restrict3<T>((const T*)p.R + P.off_lvl[l - 1], (T*)p.R + P.off_lvl[l], level_side(P.n, l), tk.x0, tk.y0,
+                   tk.z0, tk.nz, (RestrictStage<T>*)smem);
+    });
+    return;
+  }
+  phase_restrict<T, DIM>(p, l);
+}
+
 // Buffer holding the result of a visit of tooth `tooth` at a level (E if the visit flipped the
 // ping-pong buffers an even number of times, E2 otherwise).
 template <typename T>
@@ -2666,7 +2782,7 @@ __device__ void phase_mean_apply(const KernelParams& p) {
 template <typename T, int DIM>
 __device__ __forceinline__ void run_phase(const KernelParams& p, const Phase& ph, int c, unsigned char* sm) {
   switch (ph.op) {
-    case OP_RESTRICT: phase_restrict<T, DIM>(p, ph.level); break;
+    case OP_RESTRICT: phase_restrict_any<T, DIM>(p, ph.level, sm); break;
     case OP_SWEEP: phase_sweep<T, DIM>(p, ph, c, sm); break;
     case OP_PROLONG: phase_prolong<T, DIM>(p, ph, sm); break;
     case OP_INJECT: phase_inject<T, DIM>(p, ph); break;
