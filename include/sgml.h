@@ -185,6 +185,16 @@ int sgml_set_fusion(sgml_grid_t g, int pair_levels);
  * cycle. */
 int sgml_set_quad(sgml_grid_t g, int quad_levels);
 
+/* Coarse tail (3-D, SGML_MIXED, a grid of one problem with n >= 4; on by default).  The phases of
+ * a cycle that touch only the three coarsest levels (9^3, 5^3 and 3^3 nodes: the restriction
+ * passes into them and the visits of the teeth nu1 = n - 1, n - 2 and the start of n - 3 of
+ * Algorithm 3) run in one CTA with all their arrays in shared memory, instead of as grid phases
+ * that each end in a grid barrier.  The same operations in the same order: results are
+ * bit-identical either way.  on: 1 (default) or 0.  Ignored for batches, 2-D grids, the FP64 form,
+ * the one-launch-per-phase mode and while diagnostics are recorded.  Takes effect at the next
+ * launch. */
+int sgml_set_coarse_tail(sgml_grid_t g, int on);
+
 /* The cycle's phase table as the library runs it (Algorithm 3's schedule: restriction passes, then
  * the visits with their interpolation / injection steps).  Writes 4 ints per phase to out
  * (op: 0 restrict, 1 sweep, 2 interpolate to the finer level, 3 inject to the coarser level; the

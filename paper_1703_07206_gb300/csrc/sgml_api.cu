@@ -73,6 +73,9 @@ struct sgml_grid {
   int slab_z = 32;  // slab height of the slab cut of large 3-D levels (0: contiguous runs only)
   int pair_levels = 0;  // levels whose sweeps run in fused pairs (3-D mixed form only; off by default)
   int quad_levels = 0;  // levels whose sweeps run four rows per thread (3-D mixed form only; off by default)
+  bool coarse_tail = true;  // 3-D mixed form, one problem: one CTA runs the three coarsest levels' phases
+  int tail_cta = 0;         // ... the last CTA without tiles on the levels around the tail (its SM's
+                            //     instruction cache then holds the tail's code, not the next phases')
   int mode = 0;  // 0: one persistent cooperative launch per call, 1: one launch per phase
   unsigned long long timeout_ns = 2000000000ull;  // limit of every grid-barrier wait (2 s)
   int withhold_barrier = 0;  // test aid: CTA 0 withholds its arrival at this barrier (0: never)
@@ -144,7 +147,7 @@ static long long round_up(long long x, long long a) { return (x + a - 1) / a * a
 // ------------------------------------------------------------------------------------------------
 // Phase table of one cycle.  On levels below pair_levels the sweeps of a visit run two at a time
 // (kPair; a visit with an odd number of sweeps ends with a single one).
-static std::vector<Phase> build_phases(int n_max, int n_r, int pair_levels, bool any_eq10) {
+static std::vector<Phase> build_phases(int n_max, int n_r, int pair_levels, bool any_eq10, bool tail = false) {
   std::vector<Phase> ph;
   for (int l = 1; l <= n_max - 1; ++l) ph.push_back(Phase{OP_RESTRICT, l, l - 1, 0, 0, 0});
   struct Visit {
@@ -181,7 +184,33 @@ static std::vector<Phase> build_phases(int n_max, int n_r, int pair_levels, bool
     ph.push_back(Phase{OP_MEAN_REDUCE, 0, 0, 0, 0, 0});
     ph.push_back(Phase{OP_MEAN_APPLY, 0, 0, 0, 0, 0});
   }
+  if (tail) {  // coarse tail: from the restriction into level n - 3 up to the first phase below it
+    const int lt = n_max - 3;
+    auto lowest = [](const Phase& f) {  // lowest level a phase reads or writes
+      if (f.op == OP_RESTRICT || f.op == OP_INJECT) return f.level - 1;
+      if (f.op == OP_SWEEP || f.op == OP_PROLONG) return f.level;
+      return 0;
+    };
+    for (size_t q0 = 0; q0 < ph.size(); ++q0)
+      if (ph[q0].op == OP_RESTRICT && ph[q0].level == lt) {
+        size_t q1 = q0 + 1;
+        while (q1 < ph.size() && lowest(ph[q1]) >= lt) ++q1;
+        ph[q0].flags |= kTailStart;
+        ph[q0].prev_tooth = (int)q1;
+        break;
+      }
+  }
   return ph;
+}
+
+// Coarse tail (see kTailStart): 3-D mixed form, one problem of at least four levels, persistent
+// launch, no diagnostics, and no fused pairs or four-row tiles on the tail levels.
+static int effective_pair_levels(const sgml_grid* g);
+static int effective_quad_levels(const sgml_grid* g);
+static bool uses_tail(const sgml_grid* g) {
+  const int lt = g->n_max - 3;
+  return g->coarse_tail && g->dim == 3 && g->mixed && g->batch == 1 && g->n_max >= 4 && !g->d_diag && g->mode == 0 &&
+         effective_pair_levels(g) <= lt && effective_quad_levels(g) <= lt;
 }
 
 // Eq. 10 problems: every face Neumann and a >= 0 constant (a < 0 everywhere is well posed as is).
@@ -207,7 +236,7 @@ static int effective_quad_levels(const sgml_grid* g) {
 }
 
 static int upload_phases(sgml_grid* g) {
-  std::vector<Phase> ph = build_phases(g->n_max, g->n_r, effective_pair_levels(g), any_projects_mean(g));
+  std::vector<Phase> ph = build_phases(g->n_max, g->n_r, effective_pair_levels(g), any_projects_mean(g), uses_tail(g));
   const bool same = g->d_phases && ph.size() == g->h_phases.size() &&
                     std::memcmp(ph.data(), g->h_phases.data(), sizeof(Phase) * ph.size()) == 0;
   if (!same) {  // (re)upload only a changed table, reallocating only when it grew
@@ -275,6 +304,16 @@ static int upload_tiles(sgml_grid* g) {
   std::vector<TileTask> tasks, tasks4;
   std::vector<int> toff, toff4;
   partition(g->tile_x, 2 * kThreads / g->tile_x, tasks, toff);
+  g->tail_cta = 0;
+  for (int c = G - 1; c >= 0 && g->n_max >= 4; --c) {
+    bool idle = true;
+    for (int l = std::max(0, g->n_max - 5); l <= g->n_max - 1; ++l)
+      idle = idle && toff[(size_t)l * (G + 1) + c + 1] == toff[(size_t)l * (G + 1) + c];
+    if (idle) {
+      g->tail_cta = c;
+      break;
+    }
+  }
   if (effective_quad_levels(g) > 0) partition(g->tile_x, 4 * kThreads / g->tile_x, tasks4, toff4);
   if (g->d_rows) SGML_CUDA(cudaFree(g->d_rows));
   if (g->d_tasks) SGML_CUDA(cudaFree(g->d_tasks));
@@ -496,6 +535,7 @@ static int launch(sgml_grid* g, int max_cycles, double tol) {
   p.one_m_omega_f = (float)(1.0 - p.omega);
   p.n_r = g->n_r;
   p.pair_levels = effective_pair_levels(g);
+  p.tail_cta = g->tail_cta;
   p.sync = g->d_sync;
   p.timeout_ns = g->timeout_ns;
   p.withhold_barrier = g->withhold_barrier;
@@ -904,6 +944,14 @@ int sgml_set_launch(sgml_grid_t g, int ctas_per_sm, int z_waves, int mode, int t
   g->tile_x = tile_x;
   g->slab_z = slab_z;
   g->dirty_tiles = true;
+  g->dirty_phases = true;  // the coarse tail runs in the persistent launch only
+  return SGML_OK;
+}
+
+int sgml_set_coarse_tail(sgml_grid_t g, int on) {
+  if (!valid(g) || (on != 0 && on != 1)) return fail(SGML_ERR_ARG, "invalid grid, or on not 0 / 1");
+  g->coarse_tail = on != 0;
+  g->dirty_phases = true;
   return SGML_OK;
 }
 
@@ -929,6 +977,7 @@ int sgml_set_quad(sgml_grid_t g, int quad_levels) {
   if (quad_levels < 0 || quad_levels > kMaxLevels) return fail(SGML_ERR_ARG, "quad_levels must be in 0..13");
   g->quad_levels = quad_levels;
   g->dirty_tiles = true;
+  g->dirty_phases = true;  // the coarse tail needs single sweeps on its levels
   return SGML_OK;
 }
 

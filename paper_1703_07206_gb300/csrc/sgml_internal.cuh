@@ -35,6 +35,9 @@ constexpr int kFinalVisit = 1;   // SWEEP: merged last level-0 visit (tooth 0 an
 constexpr int kFirstOfTooth = 2; // SWEEP: first visit of its tooth
 constexpr int kInit = 4;         // PROLONG: first arrival at the target level in this cycle
 constexpr int kPair = 8;         // SWEEP: sweeps `sweep` and `sweep + 1` of the visit, fused
+constexpr int kTailStart = 16;   // RESTRICT into level n - 3 (3-D mixed form, one problem): one CTA runs
+                                 //   this and the following phases up to prev_tooth (exclusive), which
+                                 //   touch only the three coarsest levels, in shared memory (coarse tail)
 
 // One step of the cycle's schedule; a grid-wide barrier follows each phase.
 struct Phase {
@@ -137,6 +140,7 @@ struct KernelParams {
   float w_edge_f, w_corner_f, one_m_omega_f;  // FP32 copies of w_edge, w_corner and 1 - omega
   int n_r;
   int pair_levels;               // levels 0 .. pair_levels - 1 run their sweeps in fused pairs (kPair)
+  int tail_cta;                  // CTA that runs the coarse tail (kTailStart)
   GridSync* sync;
   unsigned long long timeout_ns;  // limit of every grid-barrier wait
   int withhold_barrier;          // test aid: CTA 0 withholds its arrival at this barrier (1-based; 0: never)

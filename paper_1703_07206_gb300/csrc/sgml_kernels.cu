@@ -577,10 +577,12 @@ constexpr size_t sweep_smem_bytes() {
 }
 constexpr size_t outer_smem_bytes() { return sizeof(ResStage<double>) * kOuterStages; }
 // ProlongStage<T> (defined with the interpolation phase): (kTX/2+1)(kTY/2+1) coarse cells x 2 plus
-// 2 x 2 x kThreads fine values, 4 stages.
+// 2 x 2 x kThreads fine values; 6 stages in FP32 (loads four coarse planes ahead), 4 in FP64.
+template <typename T>
+__host__ __device__ constexpr int prolong_stages() { return sizeof(T) == 4 ? 6 : 4; }
 template <typename T>
 constexpr size_t prolong_smem_bytes() {
-  return 4 * (sizeof(T) * 2 * (kTX / 2 + 1) * (kTY / 2 + 1) + sizeof(T) * 4 * kThreads);
+  return prolong_stages<T>() * (sizeof(T) * 2 * (kTX / 2 + 1) * (kTY / 2 + 1) + sizeof(T) * 4 * kThreads);
 }
 
 
@@ -2535,7 +2537,6 @@ __device__ __forceinline__ T* visit_result(const KernelParams& p, const ProblemD
 // change formed once per coarse node) and the previous values of the two fine planes it completes
 // (2 cz - 1 from coarse planes cz - 1 and cz, 2 cz from cz alone).
 constexpr int kCX = kTX / 2 + 1, kCY = kTY / 2 + 1, kCoarse = kCX * kCY;
-constexpr int kProlongStages = 4;
 static_assert(kCoarse <= kThreads, "one coarse cell per thread");
 
 template <typename T>
@@ -2545,8 +2546,8 @@ struct ProlongStage {
   T base[2][2 * kThreads];  // previous fine values of planes 2 cz - 1 and 2 cz at the tile's nodes
 };
 
-static_assert(sizeof(ProlongStage<float>) * kProlongStages <= phase_smem_bytes<float>(), "shared memory");
-static_assert(sizeof(ProlongStage<double>) * kProlongStages <= phase_smem_bytes<double>(), "shared memory");
+static_assert(sizeof(ProlongStage<float>) * prolong_stages<float>() <= phase_smem_bytes<float>(), "shared memory");
+static_assert(sizeof(ProlongStage<double>) * prolong_stages<double>() <= phase_smem_bytes<double>(), "shared memory");
 
 // (a + b) / 2, explicitly rounded.
 template <typename T>
@@ -2556,7 +2557,7 @@ __device__ __forceinline__ T half_sum(T a, T b) {
 
 template <typename T>
 __device__ void prolong3(const KernelParams& p, const Phase& ph, const TileTask& tk, ProlongStage<T>* st) {
-  constexpr int D = kProlongStages;
+  constexpr int D = prolong_stages<T>();
   const int l = ph.level;
   const bool init = (ph.flags & kInit) != 0;
   const ProblemDesc& P = prob_at(p, tk.b);
@@ -2603,10 +2604,12 @@ __device__ void prolong3(const KernelParams& p, const Phase& ph, const TileTask&
     }
     cp_async_commit();
   };
-  // interpolated change at the thread's two nodes from one coarse plane
+  // interpolated change at the thread's two nodes from one coarse plane (the change of a coarse node,
+  // value - B, is formed by every thread that reads it: no barrier between forming and reading)
+  auto delta = [&](const ProlongStage<T>& S, int i) { return init ? S.d[i] : rn_add(S.d[i], -S.b[i]); };
   auto plane_val = [&](const ProlongStage<T>& S, T out[2]) {
-    const T a0 = S.d[ty * kCX + lx0], a1 = S.d[ty * kCX + lx1];
-    const T b0 = S.d[(ty + 1) * kCX + lx0], b1 = S.d[(ty + 1) * kCX + lx1];
+    const T a0 = delta(S, ty * kCX + lx0), a1 = delta(S, ty * kCX + lx1);
+    const T b0 = delta(S, (ty + 1) * kCX + lx0), b1 = delta(S, (ty + 1) * kCX + lx1);
     const T ra = (x & 1) ? half_sum(a0, a1) : a0;
     const T rb = (x & 1) ? half_sum(b0, b1) : b0;
     out[0] = ra;                // y even: the coarse row itself
@@ -2618,9 +2621,7 @@ __device__ void prolong3(const KernelParams& p, const Phase& ph, const TileTask&
     cp_async_wait<D - 3>();
     __syncthreads();
     issue(k + D - 2);
-    ProlongStage<T>& S = st[k % D];
-    if (!init && has_cell) S.d[tid] = rn_add(S.d[tid], -S.b[tid]);
-    __syncthreads();
+    const ProlongStage<T>& S = st[k % D];
     T cur[2];
     plane_val(S, cur);
     const int cz = zc_first + k;
@@ -2777,6 +2778,206 @@ __device__ void phase_mean_apply(const KernelParams& p) {
 }
 
 // ---------------------------------------------------------------------------------------------
+// Coarse tail (3-D mixed form, one problem): the phases of a cycle that touch only the three
+// coarsest levels (9^3, 5^3 and 3^3 nodes: the restriction passes into them, the visits of teeth
+// n - 1 and n - 2 and the start of tooth n - 3) are about a quarter of a cycle's phases, and on the
+// whole grid each costs a grid barrier and an L2 round trip for a few hundred nodes.  CTA 0 runs
+// them instead with all their arrays in shared memory and CTA barriers between them, while the
+// other CTAs wait at one grid barrier.  Every operation is the grid phase's own arithmetic in the
+// same order (restriction: phase_restrict; sweep: sweep3's plane sums and update; interpolation:
+// prolong3; injection: phase_inject), so results are bit-identical.  In: the restricted residual of
+// level n - 4 (17^3), sigma and the step factor of the tail levels; out: E, E2, B and R of the tail
+// levels.  Kept out of line with plain arguments, so that the persistent kernel's other phases keep
+// their register allocation.
+// ---------------------------------------------------------------------------------------------
+constexpr int kTailLevels = 3;
+// nodes of tail level j (9^3, 5^3, 3^3) and its offset in shared memory (E, E2, B, R, S, Q per level)
+__host__ __device__ constexpr int tail_nodes(int j) { return j == 0 ? 729 : (j == 1 ? 125 : 27); }
+__host__ __device__ constexpr int tail_off(int j) { return j == 0 ? 0 : (j == 1 ? 6 * 729 : 6 * 729 + 6 * 125); }
+constexpr int kTailRf = 6 * (729 + 125 + 27);                           // staged residual of level n - 4
+constexpr int kTailFloats = kTailRf + 17 * 17 * 17;
+static_assert(sizeof(float) * kTailFloats <= phase_smem_bytes<float>(), "shared memory");
+enum TailArr { kTE = 0, kTE2 = 1, kTB = 2, kTR = 3, kTS = 4, kTQ = 5 };
+
+struct TailPlane {
+  float v, F, C, sv, sF, sC;
+};
+
+// The tail's operations on one level of N nodes per side (9, 5 or 3), one node per thread and pass;
+// each is the grid phase's arithmetic in the same order.  One instance per operation (the tail's code
+// is fetched cold once per cycle: fewer instances, fewer misses).  Node i of a level decodes with a
+// float reciprocal, exact here: (i + 1/2) / N lies at least 1/(2N) from an integer and i < 2^13.
+__device__ __forceinline__ void tail_decode(int i, int N, float inv_n, int& x, int& y, int& z) {
+  const int q = __float2int_rz(((float)i + 0.5f) * inv_n);
+  z = __float2int_rz(((float)q + 0.5f) * inv_n);
+  x = i - q * N;
+  y = q - z * N;
+}
+
+__device__ __forceinline__ void tail_restrict(int N, const float* src, float* dst) {
+  const int Ns = 2 * N - 1, M = N * N * N;
+  const float inv_n = 1.0f / (float)N;
+  for (int i = threadIdx.x; i < M; i += blockDim.x) {
+    int x, y, z;
+    tail_decode(i, N, inv_n, x, y, z);
+    const int xm = refl(2 * x - 1, Ns), x0 = 2 * x, xp = refl(2 * x + 1, Ns);
+    float acc = 0.0f;
+#pragma unroll
+    for (int dz = 0; dz < 3; ++dz) {
+      float accz = 0.0f;
+#pragma unroll
+      for (int dy = 0; dy < 3; ++dy) {
+        const float* row = src + (refl(2 * z + dz - 1, Ns) * Ns + refl(2 * y + dy - 1, Ns)) * Ns;
+        accz = rn_fma(dy == 1 ? 0.5f : 0.25f, restrict_line(row[xm], row[x0], row[xp]), accz);
+      }
+      acc = rn_fma(dz == 1 ? 0.5f : 0.25f, accz, acc);
+    }
+    dst[i] = acc;
+  }
+}
+
+__device__ __forceinline__ void tail_sweep(int N, const ProblemDesc& P, const float* src, float* dst, const float* S,
+                                           const float* Qv, const float* Rl, bool het, bool zero_in, float inv_c,
+                                           float q_const, float one_m_omega, float w_e, float w_c) {
+  const int M = N * N * N;
+  const float inv_n = 1.0f / (float)N;
+  for (int i = threadIdx.x; i < M; i += blockDim.x) {
+    int x, y, z;
+    tail_decode(i, N, inv_n, x, y, z);
+    if (is_fixed<3>(P, N, x, y, z)) continue;
+    const int xs[3] = {refl(x - 1, N), x, refl(x + 1, N)};
+    const int ys[3] = {refl(y - 1, N), y, refl(y + 1, N)};
+    TailPlane pl[3];  // planes z - 1, z, z + 1: sweep3's in-plane sums
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const int zz = refl(z - 1 + k, N);
+      float a[3][3], se[3][3];
+#pragma unroll
+      for (int ii = 0; ii < 3; ++ii)
+#pragma unroll
+        for (int jj = 0; jj < 3; ++jj) {
+          const int idx = (zz * N + ys[ii]) * N + xs[jj];
+          a[ii][jj] = zero_in ? 0.0f : src[idx];
+          se[ii][jj] = het ? rn_mul(S[idx], a[ii][jj]) : 0.0f;
+        }
+      pl[k].v = a[1][1];
+      pl[k].F = (a[1][0] + a[1][2]) + (a[0][1] + a[2][1]);
+      pl[k].C = (a[0][0] + a[0][2]) + (a[2][0] + a[2][2]);
+      pl[k].sv = se[1][1];
+      pl[k].sF = (se[1][0] + se[1][2]) + (se[0][1] + se[2][1]);
+      pl[k].sC = (se[0][0] + se[0][2]) + (se[2][0] + se[2][2]);
+    }
+    const TailPlane &m = pl[0], &o = pl[1], &nw = pl[2];
+    const float CSe = rn_fma(w_c, m.C + nw.C, rn_fma(w_e, (o.C + m.F) + nw.F, (o.F + m.v) + nw.v));
+    if (het) {
+      const float CSse = rn_fma(w_c, m.sC + nw.sC, rn_fma(w_e, (o.sC + m.sF) + nw.sF, (o.sF + m.sv) + nw.sv));
+      dst[i] = rn_fma(Qv[i], rn_fma(-Rl[i], inv_c, rn_fma(S[i], CSe, CSse)), rn_mul(one_m_omega, o.v));
+    } else {
+      dst[i] = rn_fma(q_const, rn_fma(-Rl[i], inv_c, rn_mul(2.0f, CSe)), rn_mul(one_m_omega, o.v));
+    }
+  }
+}
+
+__device__ __forceinline__ void tail_prolong(int N, const float* src, const float* Bc, const float* base, float* El,
+                                             bool init) {
+  const int Nc = (N + 1) / 2, M = N * N * N;
+  const float inv_n = 1.0f / (float)N;
+  auto delta = [&](int cx, int cy, int cz) {
+    const int c = (cz * Nc + cy) * Nc + cx;
+    return init ? src[c] : rn_add(src[c], -Bc[c]);
+  };
+  for (int i = threadIdx.x; i < M; i += blockDim.x) {
+    int x, y, z;
+    tail_decode(i, N, inv_n, x, y, z);
+    const int cx = x >> 1, cy = y >> 1;
+    auto plane = [&](int cz) {  // prolong3's in-plane interpolation from coarse plane cz
+      const float a0 = delta(cx, cy, cz), a1 = delta(cx + (x & 1), cy, cz);
+      const float ra = (x & 1) ? half_sum(a0, a1) : a0;
+      if (!(y & 1)) return ra;
+      const float b0 = delta(cx, cy + 1, cz), b1 = delta(cx + (x & 1), cy + 1, cz);
+      const float rb = (x & 1) ? half_sum(b0, b1) : b0;
+      return half_sum(ra, rb);
+    };
+    const float v = (z & 1) ? half_sum(plane(z >> 1), plane((z >> 1) + 1)) : plane(z >> 1);
+    El[i] = rn_add(init ? 0.0f : base[i], v);
+  }
+}
+
+__device__ __forceinline__ void tail_inject(int N, const float* src, float* El, float* Bl) {
+  const int Nf = 2 * N - 1, M = N * N * N;
+  const float inv_n = 1.0f / (float)N;
+  for (int i = threadIdx.x; i < M; i += blockDim.x) {
+    int x, y, z;
+    tail_decode(i, N, inv_n, x, y, z);
+    const float v = src[((2 * z) * Nf + 2 * y) * Nf + 2 * x];
+    El[i] = v;
+    Bl[i] = v;
+  }
+}
+
+__device__ __noinline__ void coarse_tail(const Phase* phases, int q0, int q1, float* E, float* E2, float* Bg,
+                                         float* R, const float* SIG, const float* Q, float one_m_omega, float w_e,
+                                         float w_c, int n_r, unsigned long long* stamps) {
+  extern __shared__ __align__(16) unsigned char tail_smem[];  // the kernel's dynamic shared memory
+  float* sm = reinterpret_cast<float*>(tail_smem);
+  const ProblemDesc& P = s_prob0;
+  const int n = P.n, lt = n - kTailLevels;
+  const bool het = P.hetero != 0;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  auto arr = [&](int l, int which) { return sm + tail_off(l - lt) + which * tail_nodes(l - lt); };
+  auto result = [&](int tooth, int l) {  // buffer holding the visit result of tooth `tooth` at level l
+    return arr(l, (visit_sweeps(n_r, n, tooth, false) & 1) ? kTE2 : kTE);
+  };
+  // in (asynchronous copies, one wait): sigma and q of the tail levels, R of level lt - 1; E, E2
+  // zeroed meanwhile (fixed nodes stay 0)
+  for (int j = 0; j < kTailLevels; ++j) {
+    const int l = lt + j, M = tail_nodes(j);
+    if (het)
+      for (int i = tid; i < M; i += nt) {
+        cp_async_t(&arr(l, kTS)[i], &SIG[P.off_lvl[l] + i]);
+        cp_async_t(&arr(l, kTQ)[i], &Q[P.off_lvl[l] + i]);
+      }
+  }
+  for (int i = tid; i < 17 * 17 * 17; i += nt) cp_async_t(&sm[kTailRf + i], &R[P.off_lvl[lt - 1] + i]);
+  cp_async_commit();
+  for (int j = 0; j < kTailLevels; ++j)
+    for (int i = tid; i < 2 * tail_nodes(j); i += nt) arr(lt + j, kTE)[i] = 0.0f;
+  cp_async_wait<0>();
+  __syncthreads();
+  for (int q = q0; q < q1; ++q) {
+    const Phase ph = q < kPhaseCache ? s_phase[q] : phases[q];
+    const int l = ph.level, N = level_side(n, l);
+    if (ph.op == OP_RESTRICT) {
+      tail_restrict(N, l == lt ? sm + kTailRf : arr(l - 1, kTR), arr(l, kTR));
+    } else if (ph.op == OP_SWEEP) {
+      const bool odd = (ph.sweep & 1) != 0;
+      const bool zero_in = ph.sweep == 0 && (ph.flags & kFirstOfTooth) && ph.tooth == n - 1;
+      tail_sweep(N, P, arr(l, odd ? kTE2 : kTE), arr(l, odd ? kTE : kTE2), arr(l, kTS), arr(l, kTQ), arr(l, kTR), het,
+                 zero_in, P.inv_c_f[l], P.q_const_f[l], one_m_omega, w_e, w_c);
+    } else if (ph.op == OP_PROLONG) {
+      const bool init = (ph.flags & kInit) != 0;
+      tail_prolong(N, result(ph.tooth, l + 1), arr(l + 1, kTB), init ? nullptr : result(ph.prev_tooth, l), arr(l, kTE),
+                   init);
+    } else {  // OP_INJECT
+      tail_inject(N, result(ph.tooth, l - 1), arr(l, kTE), arr(l, kTB));
+    }
+    __syncthreads();
+    if (stamps && tid == 0) stamps[3 + q] = globaltimer();
+  }
+  // out: the tail levels' E, E2, B and R (read by the phases after the tail and by the next cycle)
+  for (int j = 0; j < kTailLevels; ++j) {
+    const int l = lt + j, M = tail_nodes(j);
+    const long long o = P.off_lvl[l];
+    for (int i = tid; i < M; i += nt) {
+      E[o + i] = arr(l, kTE)[i];
+      E2[o + i] = arr(l, kTE2)[i];
+      Bg[o + i] = arr(l, kTB)[i];
+      R[o + i] = arr(l, kTR)[i];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
 // The persistent cycle kernel
 // ---------------------------------------------------------------------------------------------
 template <typename T, int DIM>
@@ -2818,6 +3019,17 @@ __global__ void __launch_bounds__(kThreads, SGML_MIN_CTAS) cycle_kernel(const Ke
     load_done(p);
     for (int q = 0; q < p.nphases; ++q) {
       const Phase ph = phase_at(p, q);
+      if (DIM == 3 && sizeof(T) == 4 && (ph.flags & kTailStart)) {
+        // coarse tail: one CTA runs phases q .. ph.prev_tooth - 1 in shared memory, one grid barrier
+        if ((int)blockIdx.x == p.tail_cta)
+          coarse_tail(p.phases, q, ph.prev_tooth, (float*)p.E, (float*)p.E2, (float*)p.B, (float*)p.R,
+                      (const float*)p.SIG, (const float*)p.Q, p.one_m_omega_f, p.w_edge_f, p.w_corner_f, p.n_r,
+                      (p.trace && c < p.trace_cycles) ? p.trace + (long long)c * (p.nphases + 3) : nullptr);
+        q = ph.prev_tooth - 1;
+        if (!grid_sync(p.sync, p.timeout_ns, p.withhold_barrier)) return;
+        stamp(c, 3 + q);
+        continue;
+      }
       run_phase<T, DIM>(p, ph, c, sm);
       if (!grid_sync(p.sync, p.timeout_ns, p.withhold_barrier)) return;
       stamp(c, 3 + q);

@@ -59,6 +59,7 @@ _SIGNATURES = {
     "sgml_get_diagnostics": [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.c_int,
                              ctypes.POINTER(ctypes.c_int)],
     "sgml_set_quad": [ctypes.c_void_p, ctypes.c_int],
+    "sgml_set_coarse_tail": [ctypes.c_void_p, ctypes.c_int],
     "sgml_get_phases": [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.POINTER(ctypes.c_int)],
     "sgml_set_launch": [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int],
     "sgml_launch_count": [ctypes.c_void_p, ctypes.POINTER(ctypes.c_longlong)],
@@ -268,6 +269,10 @@ class Grid:
     def set_quad(self, quad_levels=1):
         """Levels 0 .. quad_levels - 1 sweep with four rows per thread (3-D mixed form; 0: off)."""
         _check(load().sgml_set_quad(self._h, quad_levels))
+
+    def set_coarse_tail(self, on=True):
+        """Run the three coarsest levels' phases in one CTA's shared memory (3-D mixed form, one problem)."""
+        _check(load().sgml_set_coarse_tail(self._h, 1 if on else 0))
 
     def get_phases(self):
         """The cycle's phase table: list of (op, level, first sweep, sweeps performed)."""
