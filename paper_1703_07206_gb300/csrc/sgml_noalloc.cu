@@ -127,7 +127,7 @@ extern "C" int sgml_solve_noalloc(int dim, int n, int precision, const double* f
     bool all_neumann = true;
     for (int k = 0; k < 2 * dim; ++k) all_neumann = all_neumann && P.face_type[k] == SGML_NEUMANN;
     if (all_neumann && a_scalar >= 0.0)
-      return fail(SGML_ERR_ARG, "all-Neumann problems with a >= 0 (Eq. 10 projection) need the grid API");
+      return fail(SGML_ERR_ARG, "all-Neumann problems with a >= 0 need the mean projection of the grid API");
   }
   long long lvl = 0;
   for (int l = 0; l <= n - 1; ++l) {
